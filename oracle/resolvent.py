@@ -1,0 +1,171 @@
+"""Resolvents (tau L - alpha)^{-1} through the elliptic reformulation
+(Section 2.1) on the global collocation system B u = f (Section 2.2), and the
+rational time step u <- sum_m b_m (tau L - alpha_m)^{-1} u (Section 1.1).
+
+TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
+
+Two problem kinds (state layout [field][node], real, on the public node order):
+
+wave  u_t = v, v_t = div(c^2 grad u) on the unit square, u = 0 on the boundary.
+      (tau L - alpha)(U, V) = (f_u, f_v) gives V = (alpha U + f_u) / tau and
+      [div(c^2 grad .) - (alpha/tau)^2] U = (tau f_v + alpha f_u) / tau^2, U = 0
+      on the boundary.  This is the two-field (u, v) form of Example 2 of
+      Section 2.1 (the paper writes a three-field form); the derivation is the
+      same elimination of all but one unknown.
+
+sw    linearised rotating shallow water u_t = f v - g h_x, v_t = -f u - g h_y,
+      h_t = -H (u_x + v_y), no normal flow at the walls (Example 1 of
+      Section 2.1, eqs. "inverse oper, RSW" to "elliptic solve, RSW", with
+      gravity g and depth H written out).  With K = [[-alpha, tau f],
+      [-tau f, -alpha]] and D = alpha^2 + tau^2 f^2:
+        (U, V) = K^{-1} (F + tau g grad h),
+        (Delta - D/(tau^2 g H)) h = D/(tau^2 g H alpha) r
+                                    - (alpha div F + tau f curl F)/(tau g alpha),
+      and U = 0 (x-walls) / V = 0 (y-walls) become the oblique conditions
+        alpha h_x + tau f h_y = -(alpha F1 + tau f F2)/(tau g)   (x = 0, 1)
+        alpha h_y - tau f h_x = (tau f F1 - alpha F2)/(tau g)    (y = 0, 1).
+
+Every solve is a sparse direct solve (scipy splu) of the full global system.
+"""
+from __future__ import annotations
+
+import numpy as np
+import scipy.sparse as sp
+import scipy.sparse.linalg as spla
+
+from . import sem
+
+
+class Problem:
+    """A discretised problem: grid, kind and coefficients."""
+
+    def __init__(self, grid: sem.Grid, kind: str, tau: float, c2=None,
+                 f: float = 0.0, g: float = 1.0, H: float = 1.0):
+        if kind not in ("wave", "sw"):
+            raise ValueError(kind)
+        self.grid, self.kind, self.tau = grid, kind, float(tau)
+        self.f, self.g, self.H = float(f), float(g), float(H)
+        self.cls, self.side = grid.classify()
+        n = grid.n_nodes
+        if kind == "wave":
+            self.a = np.asarray(c2, dtype=np.float64)
+            self.n_fields = 2
+        else:
+            self.a = np.ones(n)
+            self.n_fields = 3
+        self.Lap = sem.divgrad_operator(grid, self.a)
+        self.Flux = sem.flux_continuity_rows(grid, self.a)
+        if kind == "sw":
+            self.Gx, self.Gy = sem.wall_gradient_rows(grid)
+        self.P_int = sp.diags((self.cls == 0).astype(float))
+        self.P_ifc = sp.diags((self.cls == 1).astype(float))
+        self.P_bnd = sp.diags((self.cls == 2).astype(float))
+
+    # -------------------------------------------------------------- system
+    def kappa2(self, alpha: complex) -> complex:
+        if self.kind == "wave":
+            return (alpha / self.tau) ** 2
+        D = alpha * alpha + (self.tau * self.f) ** 2
+        return D / (self.tau ** 2 * self.g * self.H)
+
+    def system(self, alpha: complex) -> sp.csc_matrix:
+        """Global matrix: interior collocation rows, interface flux rows,
+        boundary rows (Dirichlet identity for wave, oblique condition for sw)."""
+        k2 = self.kappa2(alpha)
+        n = self.grid.n_nodes
+        B = self.P_int @ (self.Lap - k2 * sp.identity(n)) + self.Flux.astype(np.complex128)
+        if self.kind == "wave":
+            B = B + self.P_bnd
+        else:
+            xw = sp.diags(((self.side == 1) | (self.side == 3)).astype(float))
+            yw = sp.diags(((self.side == 0) | (self.side == 2)).astype(float))
+            tf = self.tau * self.f
+            B = B + xw @ (alpha * self.Gx + tf * self.Gy) + yw @ (alpha * self.Gy - tf * self.Gx)
+        return sp.csc_matrix(B)
+
+    def rhs(self, alpha: complex, state: np.ndarray) -> np.ndarray:
+        """Right-hand side of the elliptic system for input state (the pre-map)."""
+        tau = self.tau
+        if self.kind == "wave":
+            fu, fv = state
+            s = (tau * fv + alpha * fu) / tau ** 2
+            return np.where(self.cls == 0, s, 0.0).astype(np.complex128)
+        F1, F2, r = state
+        f, g, H = self.f, self.g, self.H
+        D = alpha * alpha + (tau * f) ** 2
+        div, curl = sem.interior_div_curl(self.grid, F1, F2)
+        s = D / (tau ** 2 * g * H * alpha) * r - (alpha * div + tau * f * curl) / (tau * g * alpha)
+        out = np.where(self.cls == 0, s, 0.0).astype(np.complex128)
+        xw = (self.side == 1) | (self.side == 3)
+        yw = (self.side == 0) | (self.side == 2)
+        out[xw] = -(alpha * F1[xw] + tau * f * F2[xw]) / (tau * g)
+        out[yw] = (tau * f * F1[yw] - alpha * F2[yw]) / (tau * g)
+        return out
+
+    def post(self, alpha: complex, w: np.ndarray, state: np.ndarray) -> np.ndarray:
+        """Recover all fields of (tau L - alpha)^{-1} state from the elliptic solution w."""
+        tau = self.tau
+        if self.kind == "wave":
+            fu = state[0]
+            return np.stack([w, (alpha * w + fu) / tau])
+        F1, F2, _ = state
+        f, g = self.f, self.g
+        D = alpha * alpha + (tau * f) ** 2
+        hx, hy = sem.gradient(self.grid, w)
+        a1 = F1 + tau * g * hx
+        a2 = F2 + tau * g * hy
+        U = (-alpha * a1 - tau * f * a2) / D
+        V = (tau * f * a1 - alpha * a2) / D
+        return np.stack([U, V, w])
+
+
+class Stepper:
+    """u_{n+1} = sum_m b_m (tau L - alpha_m)^{-1} u_n, factorisations cached."""
+
+    def __init__(self, prob: Problem, alpha, b):
+        self.prob = prob
+        self.alpha = np.asarray(alpha, dtype=np.complex128)
+        self.b = np.asarray(b, dtype=np.complex128)
+        self._lu = {}
+
+    def _solver(self, i):
+        if i not in self._lu:
+            self._lu[i] = spla.splu(self.prob.system(self.alpha[i]))
+        return self._lu[i]
+
+    def resolvent(self, i: int, state: np.ndarray) -> np.ndarray:
+        """(tau L - alpha_i)^{-1} state (complex, all fields)."""
+        a = self.alpha[i]
+        w = self._solver(i).solve(self.prob.rhs(a, state))
+        return self.prob.post(a, w, state)
+
+    def step_full(self, state: np.ndarray) -> np.ndarray:
+        """sum over every pole (eq. def_RM applied to tau L); complex result."""
+        out = np.zeros(state.shape, dtype=np.complex128)
+        for i in range(self.alpha.size):
+            out += self.b[i] * self.resolvent(i, state)
+        return out
+
+    def step(self, state: np.ndarray) -> np.ndarray:
+        """Real step using eq. "conjugate, matrix inverses" (Section 3.3): for a
+        real state and conjugate-closed (alpha, b) only one pole of each pair is
+        solved, out = Re(b_0 x_0) + 2 Re sum_{Im alpha_m > 0} b_m x_m."""
+        out = np.zeros(state.shape)
+        for i in range(self.alpha.size):
+            im = self.alpha[i].imag
+            if im < 0:
+                continue
+            w = 1.0 if im == 0 else 2.0
+            out += w * (self.b[i] * self.resolvent(i, state)).real
+        return out
+
+
+def conjugate_closed(alpha, b, tol=0.0) -> bool:
+    """True when the multiset {(alpha, b)} is closed under conjugation."""
+    alpha = np.asarray(alpha)
+    b = np.asarray(b)
+    for i in range(alpha.size):
+        j = np.argmin(np.abs(alpha - np.conj(alpha[i])))
+        if abs(alpha[j] - np.conj(alpha[i])) > tol or abs(b[j] - np.conj(b[i])) > tol:
+            return False
+    return True

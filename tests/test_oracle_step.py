@@ -1,0 +1,174 @@
+"""Pins of oracle.resolvent and oracle.reference: closed-form modes of the
+continuous problems, the dense exponential of the semi-discrete operator, RK4,
+conservation, and the conjugate-pole identity (Sections 1.2, 2.1, 3.3)."""
+import numpy as np
+import pytest
+
+from oracle import rational, sem
+from oracle.reference import WaveLh
+from oracle.resolvent import Problem, Stepper, conjugate_closed
+
+
+@pytest.fixture(scope="module")
+def poles21():
+    return rational.fit(21, 1e-10, s_grid=[1.3, 1.4, 1.5], ratio_grid=(3.75, 4.0))
+
+
+def test_wave_resolvent_of_standing_mode():
+    # c = 1: phi = sin(k pi x) sin(l pi y) satisfies Delta phi = -w^2 phi, w = pi sqrt(k^2+l^2),
+    # so (phi, +-i w phi) are eigenvectors of L with eigenvalues +-i w and
+    # (tau L - alpha)^{-1}(phi, 0) = 1/2 sum_{+-} (phi, +-i w phi) / (+-i tau w - alpha).
+    g = sem.Grid(4, 4, 12)
+    tau, alpha = 0.05, 3.0 + 2.0j
+    prob = Problem(g, "wave", tau, c2=np.ones(g.n_nodes))
+    st = Stepper(prob, np.array([alpha]), np.array([1.0]))
+    k, l = 1, 2
+    w = np.pi * np.hypot(k, l)
+    phi = np.sin(k * np.pi * g.x) * np.sin(l * np.pi * g.y)
+    x = st.resolvent(0, np.stack([phi, 0 * phi]))
+    up, um = 1 / (1j * tau * w - alpha), 1 / (-1j * tau * w - alpha)
+    assert np.abs(x[0] - 0.5 * (up + um) * phi).max() < 1e-10
+    assert np.abs(x[1] - 0.5j * w * (up - um) * phi).max() < 1e-8
+
+
+def test_conjugate_pole_form_equals_full_sum(poles21):
+    alpha, b, X = poles21
+    assert conjugate_closed(alpha, b)
+    g = sem.Grid(2, 2, 8)
+    c2 = (1 + 0.3 * np.sin(3 * g.x) * np.cos(2 * g.y)) ** 2
+    prob = Problem(g, "wave", 0.02, c2=c2)
+    st = Stepper(prob, alpha, b)
+    rng = np.random.default_rng(1)
+    u = rng.standard_normal((2, g.n_nodes))
+    full = st.step_full(u)
+    assert np.abs(full.imag).max() < 1e-10 * np.abs(full.real).max()
+    assert np.abs(st.step(u) - full.real).max() < 1e-12 * np.abs(full.real).max()
+
+
+@pytest.fixture(scope="module")
+def small_wave(poles21):
+    alpha, b, X = poles21
+    g = sem.Grid(2, 2, 12)
+    c2 = (1 + 0.25 * np.sin(2 * np.pi * g.x) * np.cos(2 * np.pi * g.y)) ** 2
+    prob1 = Problem(g, "wave", 1.0, c2=c2)
+    Lh = WaveLh(prob1)
+    lam, _, _ = Lh.eig()
+    u0 = np.exp(-((g.x - 0.45) ** 2 + (g.y - 0.55) ** 2) / (2 * 0.08 ** 2))
+    z0 = Lh.restrict(np.stack([u0, 0 * u0]))
+    # band: smallest eigenvalue modulus beyond which the content of z0 is < 1e-11
+    for Lam in np.sort(np.abs(lam)):
+        if np.linalg.norm(Lh.project_out(Lam, z0)) <= 1e-11 * np.linalg.norm(z0):
+            break
+    tau = X / Lam
+    prob = Problem(g, "wave", tau, c2=c2)
+    return g, prob, Lh, Stepper(prob, alpha, b), z0, tau, Lam
+
+
+def test_step_matches_dense_exponential_within_eq_error_bound(small_wave):
+    # eq. "error in exp(t*L)" bounds |R(tau L)u - exp(tau L)u| by
+    # delta|u| + 2|u - P_Lambda u| for skew L.  L_h is only nearly skew
+    # (Section 1.3), so the bound is taken in its eigenvector form:
+    # sum_k |R(tau lam_k) - e^{tau lam_k}| |c_k| |v_k|, with u = sum_k c_k v_k.
+    g, prob, Lh, st, z0, tau, Lam = small_wave
+    n = z0.size // 2
+    s = Lh.lift(z0[:n], z0[n:])
+    got = Lh.restrict(st.step(s))
+    lam, V, Vi = Lh.eig()
+    c = Vi @ z0
+    R = rational.R_eval(tau * lam, st.alpha, st.b)
+    E = np.exp(tau * lam)
+    # (a) the stepper applies R(tau L_h): spectral calculus of the same matrix.
+    # Each sparse resolvent carries ~1e-10 relative rounding here (condition
+    # ~1e5 with |alpha/tau|^2 ~ 5e5 against the Laplacian's spread) and the pole
+    # sum cancels terms ~30x larger than the result, hence 5e-8.
+    spectral = (V @ (R * c)).real
+    assert np.linalg.norm(got - spectral) < 5e-8 * np.linalg.norm(z0)
+    # (b) per resolved mode R(tau lam) = e^{tau lam} to about delta
+    inband = np.abs(lam) <= Lam
+    assert np.abs(R - E)[inband].max() < 3e-10
+    # (c) the eigenvector form of the bound
+    bound = (np.abs(R - E) * np.abs(c) * np.linalg.norm(V, axis=0)).sum()
+    want = Lh.expm_apply(tau, z0)
+    assert np.linalg.norm(got - want) <= bound + 5e-8 * np.linalg.norm(z0)
+    assert np.linalg.norm(got - want) < 1e-7 * np.linalg.norm(z0)
+
+
+def test_rk4_tiny_step_matches_dense_exponential(small_wave):
+    g, prob, Lh, st, z0, tau, Lam = small_wave
+    want = Lh.expm_apply(tau, z0)
+    got = Lh.rk4(tau, z0, 400)
+    assert np.linalg.norm(got - want) < 1e-9 * np.linalg.norm(z0)
+
+
+def test_wave_energy_conserved_over_steps(small_wave):
+    g, prob, Lh, st, z0, tau, Lam = small_wave
+    wq = sem.leaf_weights(g)
+
+    def energy(s):
+        ux, uy = sem.gradient(g, s[0])
+        return wq @ (prob.a * (ux ** 2 + uy ** 2) + s[1] ** 2)
+
+    n = z0.size // 2
+    s = Lh.lift(z0[:n], z0[n:])
+    e0 = energy(s)
+    for _ in range(5):
+        s = st.step(s)
+    # L_h is only approximately skew (Section 1.3) and the quadrature drops the
+    # corner nodes, so the measured energy moves at the discretisation level
+    assert abs(energy(s) - e0) < 2e-3 * e0
+
+
+def _sw_problem(f, tau, nl=2, p=16):
+    g = sem.Grid(nl, nl, p)
+    return g, Problem(g, "sw", tau, f=f, g=1.0, H=1.0)
+
+
+def test_sw_geostrophic_mode_is_steady(poles21):
+    # f != 0: h = sin(pi x) sin(pi y), (u, v) = (g/f)(-h_y, h_x) satisfies every
+    # equation of the rotating shallow-water system with zero time derivative and
+    # has zero normal flow on the walls, so exp(tau L) leaves it unchanged.
+    alpha, b, X = poles21
+    f = 10.0
+    g, prob = _sw_problem(f, tau=0.25)
+    h = np.sin(np.pi * g.x) * np.sin(np.pi * g.y)
+    u = -(1.0 / f) * np.pi * np.sin(np.pi * g.x) * np.cos(np.pi * g.y)
+    v = (1.0 / f) * np.pi * np.cos(np.pi * g.x) * np.sin(np.pi * g.y)
+    s0 = np.stack([u, v, h])
+    s1 = Stepper(prob, alpha, b).step(s0)
+    assert np.abs(s1 - s0).max() < 1e-8
+
+
+def test_sw_standing_mode_without_rotation(poles21):
+    # f = 0, gH = 1: h = cos(w t) phi, (u, v) = -(g/w) sin(w t) grad phi with
+    # phi = cos(k pi x) cos(l pi y), w^2 = g H pi^2 (k^2 + l^2).
+    alpha, b, X = poles21
+    k, l = 1, 2
+    w = np.pi * np.hypot(k, l)
+    tau = 0.6 * X / w
+    g, prob = _sw_problem(0.0, tau=tau)
+    phi = np.cos(k * np.pi * g.x) * np.cos(l * np.pi * g.y)
+    px = -k * np.pi * np.sin(k * np.pi * g.x) * np.cos(l * np.pi * g.y)
+    py = -l * np.pi * np.cos(k * np.pi * g.x) * np.sin(l * np.pi * g.y)
+    s0 = np.stack([0 * phi, 0 * phi, phi])
+    s1 = Stepper(prob, alpha, b).step(s0)
+    want = np.stack([-(1 / w) * np.sin(w * tau) * px, -(1 / w) * np.sin(w * tau) * py,
+                     np.cos(w * tau) * phi])
+    assert np.abs(s1 - want).max() < 1e-10
+
+
+def test_sw_rotating_energy_conserved(poles21):
+    alpha, b, X = poles21
+    f = 3.0
+    g, prob = _sw_problem(f, tau=0.3)
+    wq = sem.leaf_weights(g)
+    h = np.exp(-((g.x - 0.5) ** 2 + (g.y - 0.45) ** 2) / (2 * 0.15 ** 2))
+    s = np.stack([0 * h, 0 * h, h])
+
+    def energy(s):
+        return wq @ (s[0] ** 2 + s[1] ** 2 + s[2] ** 2)     # g = H = 1
+
+    e0 = energy(s)
+    st = Stepper(prob, alpha, b)
+    for _ in range(4):
+        s = st.step(s)
+    assert abs(energy(s) - e0) < 3e-4 * e0

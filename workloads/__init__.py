@@ -1,0 +1,189 @@
+"""Seeded synthetic workloads for the rational time stepper.
+
+This module holds only workload definitions and seeded input generators:
+grid sizes, PDE coefficients sampled at caller-given coordinates, and initial
+conditions.  It contains none of the method's arithmetic (no rational fit, no
+discretisation, no solve), so both the FP64 CPU oracle and the GPU path can use
+it without sharing any computation.
+
+The workloads follow the paper's two PDE families (rotating shallow water,
+Section 4.1; variable-coefficient wave equation, Section 4.2), with the sizes,
+coefficients and initial-condition recipes of the five benchmark
+configurations.  Every random draw comes from ``numpy.random.default_rng`` with
+a fixed seed (config index * 1000 + instance).
+"""
+from __future__ import annotations
+
+import math
+from dataclasses import dataclass, field
+
+import numpy as np
+
+# ln(1/delta) based spectral cut-off of a Gaussian exp(-r^2 / (2 s^2)):
+# its Fourier transform exp(-k^2 s^2 / 2) drops below delta at
+# k = sqrt(2 ln(1/delta)) / s.
+
+
+def gaussian_kmax(sigma: float, delta: float) -> float:
+    """Wavenumber above which a Gaussian of std ``sigma`` has relative content < delta."""
+    return math.sqrt(2.0 * math.log(1.0 / delta)) / sigma
+
+
+@dataclass(frozen=True)
+class Workload:
+    name: str
+    kind: str                 # "wave" (Dirichlet) or "sw" (no-normal-flow walls)
+    nlx: int
+    nly: int
+    p: int
+    delta: float
+    n_poles: int = 0          # 2M+1 fixed by the workload (0: chosen from the band)
+    tau: float = 0.0          # fixed step (0: chosen from the pole count and band)
+    steps: int = 1
+    n_rhs: int = 1
+    seed: int = 0
+    params: dict = field(default_factory=dict)
+
+    @property
+    def q(self) -> int:
+        return self.p - 2
+
+
+# Configuration 0: variable-coefficient wave equation, Dirichlet walls,
+# 4x4 leaves, p = 12, 21 poles, Gaussian bump (sigma 0.05) at (0.4, 0.6).
+WAVE_4X4_P12 = Workload(
+    name="wave_dirichlet_4x4_p12_N21", kind="wave", nlx=4, nly=4, p=12,
+    delta=1e-10, n_poles=21, steps=10, seed=0,
+    params=dict(c_kind="sincos", ic="bump", bump_sigma=0.05, bump_centre=(0.4, 0.6),
+                c_max=1.25),
+)
+
+# Configuration 1: linearised rotating shallow water, walls, gH = 1, f = 10,
+# 16x16 leaves, p = 16, tau = 20 inertial periods, 3 seeded Gaussians.
+SW_16X16_P16 = Workload(
+    name="sw_walls_16x16_p16_tau20T", kind="sw", nlx=16, nly=16, p=16,
+    delta=1e-10, tau=20.0 * 2.0 * math.pi / 10.0, steps=100, seed=1000,
+    params=dict(f=10.0, g=1.0, H=1.0, n_gauss=3, sigma_range=(0.03, 0.08),
+                amp_range=(0.1, 1.0), centre_range=(0.2, 0.8)),
+)
+
+# Configuration 2: wave equation with c = clip(exp(GRF), 0.5, 2), 32x32 leaves,
+# p = 16, 61 poles, 256 initial conditions of 5 Gaussians each, 50 steps.
+WAVE_32X32_P16 = Workload(
+    name="wave_dirichlet_32x32_p16_N61", kind="wave", nlx=32, nly=32, p=16,
+    delta=1e-10, n_poles=61, steps=50, n_rhs=256, seed=2000,
+    params=dict(c_kind="grf", grf_corr=0.1, grf_std=0.3, c_clip=(0.5, 2.0), c_max=2.0,
+                ic="gauss5", n_gauss=5, sigma_range=(0.03, 0.08),
+                amp_range=(0.1, 1.0), centre_range=(0.2, 0.8)),
+)
+
+WORKLOADS = {w.name: w for w in (WAVE_4X4_P12, SW_16X16_P16, WAVE_32X32_P16)}
+
+
+def sw_band(w: Workload) -> float:
+    """Band Lambda for the shallow-water workload: sqrt(f^2 + gH k_max^2),
+    k_max from the narrowest Gaussian the recipe can draw."""
+    pr = w.params
+    k = gaussian_kmax(pr["sigma_range"][0], w.delta)
+    return math.sqrt(pr["f"] ** 2 + pr["g"] * pr["H"] * k * k)
+
+
+def wave_band(w: Workload) -> float:
+    """Band Lambda for the wave workloads: c_max * k_max of the initial data."""
+    pr = w.params
+    s = pr.get("bump_sigma", pr.get("sigma_range", (0.05,))[0])
+    return pr["c_max"] * gaussian_kmax(s, w.delta)
+
+
+# ---------------------------------------------------------------- coefficients
+
+def wave_c_sincos(x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """c(x, y) = 1 + 0.25 sin(2 pi x) cos(2 pi y)."""
+    return 1.0 + 0.25 * np.sin(2 * np.pi * x) * np.cos(2 * np.pi * y)
+
+
+def grf(x: np.ndarray, y: np.ndarray, seed: int, corr: float, std: float,
+        period: float = 2.0) -> np.ndarray:
+    """Smooth Gaussian random field with covariance std^2 exp(-r^2 / (2 corr^2)).
+
+    Spectral synthesis on a periodic box of side ``period`` (larger than the
+    unit square so no periodicity is imposed on [0,1]^2): random Fourier modes
+    k = 2 pi n / period, |k| <= 7 / corr, amplitude sqrt(S(k) dk^2) with the
+    Gaussian spectral density S(k) = std^2 corr^2 / (2 pi) exp(-k^2 corr^2 / 2).
+    """
+    rng = np.random.default_rng(seed)
+    dk = 2 * np.pi / period
+    nmax = int(math.ceil(7.0 / corr / dk))
+    n = np.arange(-nmax, nmax + 1)
+    kx, ky = np.meshgrid(n * dk, n * dk, indexing="ij")
+    kx = kx.ravel(); ky = ky.ravel()
+    kk = kx * kx + ky * ky
+    sel = kk <= (7.0 / corr) ** 2
+    kx, ky, kk = kx[sel], ky[sel], kk[sel]
+    dens = std * std * corr * corr / (2 * np.pi) * np.exp(-0.5 * kk * corr * corr)
+    amp = np.sqrt(dens * dk * dk)
+    a = rng.standard_normal(kx.size) * amp
+    b = rng.standard_normal(kx.size) * amp
+    xf = np.asarray(x, dtype=np.float64).ravel()
+    yf = np.asarray(y, dtype=np.float64).ravel()
+    out = np.zeros(xf.size)
+    for i in range(0, xf.size, 8192):
+        ph = np.outer(xf[i:i + 8192], kx) + np.outer(yf[i:i + 8192], ky)
+        out[i:i + 8192] = np.cos(ph) @ a + np.sin(ph) @ b
+    return out.reshape(np.shape(x))
+
+
+def wave_c(w: Workload, x: np.ndarray, y: np.ndarray) -> np.ndarray:
+    """Wave speed c at the given coordinates for workload ``w``."""
+    pr = w.params
+    if pr["c_kind"] == "sincos":
+        return wave_c_sincos(x, y)
+    if pr["c_kind"] == "grf":
+        g = grf(x, y, w.seed + 999, pr["grf_corr"], pr["grf_std"])
+        lo, hi = pr["c_clip"]
+        return np.clip(np.exp(g), lo, hi)
+    if pr["c_kind"] == "const":
+        return np.ones_like(np.asarray(x, dtype=np.float64))
+    raise ValueError(pr["c_kind"])
+
+
+# ---------------------------------------------------------- initial conditions
+
+def draw_gaussians(seed: int, n: int, sigma_range, amp_range, centre_range):
+    """Seeded parameters of ``n`` Gaussians: (centres [n,2], sigmas [n], amps [n])."""
+    rng = np.random.default_rng(seed)
+    c = rng.uniform(centre_range[0], centre_range[1], size=(n, 2))
+    s = rng.uniform(sigma_range[0], sigma_range[1], size=n)
+    a = rng.uniform(amp_range[0], amp_range[1], size=n)
+    return c, s, a
+
+
+def gaussian_sum(x, y, centres, sigmas, amps) -> np.ndarray:
+    """Sum_j a_j exp(-|x - c_j|^2 / (2 s_j^2))."""
+    x = np.asarray(x, dtype=np.float64)
+    y = np.asarray(y, dtype=np.float64)
+    out = np.zeros(np.broadcast(x, y).shape)
+    for (cx, cy), s, a in zip(centres, sigmas, amps):
+        out += a * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * s * s))
+    return out
+
+
+def initial_fields(w: Workload, x: np.ndarray, y: np.ndarray, rhs: int = 0) -> list:
+    """Initial fields at the given coordinates, as a list of arrays.
+
+    wave: [u, v] with v = 0.  sw: [u, v, h] with u = v = 0.
+    """
+    pr = w.params
+    if w.kind == "wave":
+        if pr.get("ic") == "bump":
+            cx, cy = pr["bump_centre"]
+            u = gaussian_sum(x, y, [(cx, cy)], [pr["bump_sigma"]], [1.0])
+        else:
+            c, s, a = draw_gaussians(w.seed + rhs, pr["n_gauss"], pr["sigma_range"],
+                                     pr["amp_range"], pr["centre_range"])
+            u = gaussian_sum(x, y, c, s, a)
+        return [u, np.zeros_like(u)]
+    c, s, a = draw_gaussians(w.seed + rhs, pr["n_gauss"], pr["sigma_range"],
+                             pr["amp_range"], pr["centre_range"])
+    h = gaussian_sum(x, y, c, s, a)
+    return [np.zeros_like(h), np.zeros_like(h), h]
