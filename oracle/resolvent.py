@@ -7,11 +7,12 @@ TEST INFRASTRUCTURE ONLY (see ``oracle/__init__.py``).
 Two problem kinds (state layout [field][node], real, on the public node order):
 
 wave  u_t = v, v_t = div(c^2 grad u) on the unit square, u = 0 on the boundary.
-      (tau L - alpha)(U, V) = (f_u, f_v) gives V = (alpha U + f_u) / tau and
-      [div(c^2 grad .) - (alpha/tau)^2] U = (tau f_v + alpha f_u) / tau^2, U = 0
-      on the boundary.  This is the two-field (u, v) form of Example 2 of
-      Section 2.1 (the paper writes a three-field form); the derivation is the
-      same elimination of all but one unknown.
+      (tau L - alpha)(U, V) = (f_u, f_v) gives U = (tau V - f_u) / alpha and
+      [div(c^2 grad .) - (alpha/tau)^2] V = (alpha f_v + tau A f_u) / tau^2 with
+      A = div(c^2 grad .), V = 0 on the boundary (u = 0 there for all time).
+      As in Example 2 of Section 2.1 (eq. "v for inhomog, inverse") the elliptic
+      unknown is the time derivative; the paper writes a three-field form, this
+      is the same elimination in the two-field (u, v) form.
 
 sw    linearised rotating shallow water u_t = f v - g h_x, v_t = -f u - g h_y,
       h_t = -H (u_x + v_y), no normal flow at the walls (Example 1 of
@@ -88,7 +89,7 @@ class Problem:
         tau = self.tau
         if self.kind == "wave":
             fu, fv = state
-            s = (tau * fv + alpha * fu) / tau ** 2
+            s = (alpha * fv + tau * (self.Lap @ fu)) / tau ** 2
             return np.where(self.cls == 0, s, 0.0).astype(np.complex128)
         F1, F2, r = state
         f, g, H = self.f, self.g, self.H
@@ -107,7 +108,7 @@ class Problem:
         tau = self.tau
         if self.kind == "wave":
             fu = state[0]
-            return np.stack([w, (alpha * w + fu) / tau])
+            return np.stack([(tau * w - fu) / alpha, w])
         F1, F2, _ = state
         f, g = self.f, self.g
         D = alpha * alpha + (tau * f) ** 2

@@ -148,6 +148,8 @@ class Grid:
 # ------------------------------------------------------------------ operators
 
 def _coo(rows, cols, vals, n):
+    if not rows:                       # e.g. no interfaces on a single-leaf grid
+        return sp.csr_matrix((n, n))
     return sp.csr_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
                          shape=(n, n))
 

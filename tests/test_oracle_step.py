@@ -77,19 +77,16 @@ def test_step_matches_dense_exponential_within_eq_error_bound(small_wave):
     c = Vi @ z0
     R = rational.R_eval(tau * lam, st.alpha, st.b)
     E = np.exp(tau * lam)
-    # (a) the stepper applies R(tau L_h): spectral calculus of the same matrix.
-    # Each sparse resolvent carries ~1e-10 relative rounding here (condition
-    # ~1e5 with |alpha/tau|^2 ~ 5e5 against the Laplacian's spread) and the pole
-    # sum cancels terms ~30x larger than the result, hence 5e-8.
+    # (a) the stepper applies R(tau L_h): spectral calculus of the same matrix
     spectral = (V @ (R * c)).real
-    assert np.linalg.norm(got - spectral) < 5e-8 * np.linalg.norm(z0)
+    assert np.linalg.norm(got - spectral) < 1e-10 * np.linalg.norm(z0)
     # (b) per resolved mode R(tau lam) = e^{tau lam} to about delta
     inband = np.abs(lam) <= Lam
     assert np.abs(R - E)[inband].max() < 3e-10
     # (c) the eigenvector form of the bound
     bound = (np.abs(R - E) * np.abs(c) * np.linalg.norm(V, axis=0)).sum()
     want = Lh.expm_apply(tau, z0)
-    assert np.linalg.norm(got - want) <= bound + 5e-8 * np.linalg.norm(z0)
+    assert np.linalg.norm(got - want) <= bound + 1e-10 * np.linalg.norm(z0)
     assert np.linalg.norm(got - want) < 1e-7 * np.linalg.norm(z0)
 
 
