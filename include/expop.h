@@ -1,0 +1,163 @@
+/*
+ * expop.h -- C ABI of the GB300 apply engine for the rational time-evolution
+ * operator of Haut, Babb, Martinsson and Wingate:
+ *
+ *     exp(tau L) u  ~  R(tau L) u = sum_{m=-M..M} b_m (tau L - alpha_m)^{-1} u
+ *
+ * (Section 1.1 and eq. def_RM of Section 1.2), for a skew-Hermitian L.  Each
+ * resolvent is reduced to one scalar elliptic solve (Section 2.1), discretised by
+ * multidomain Chebyshev collocation (Section 2.2) and solved with precomputed
+ * nested-dissection (HPS) solution operators (Section 2.3 and Section 1.3).
+ *
+ * Conventions shared by every call:
+ *  - All functions return eo_status; they never print, abort or throw.  On error
+ *    eo_last_error() returns a message for the calling thread.
+ *  - Floating point data are IEEE FP64.  Complex numbers are interleaved
+ *    (re, im) pairs.
+ *  - A state is real, laid out [rhs][field][node] with the node order given by
+ *    eo_grid_nodes.  Fields: EO_WAVE_DIRICHLET (u, v); EO_SW_WALLS (u, v, h).
+ *  - Node order (the "public numbering"): the leaf square [x0,x1]x[y0,y1] is cut
+ *    into nlx x nly leaves with p x p Chebyshev-Lobatto nodes each; the four corner
+ *    nodes of every leaf are dropped (no equation references them).  Then
+ *      interior nodes, leaf l = b*nlx + a, local (k, j), k,j = 1..p-2:
+ *          id = l*q*q + (j-1)*q + (k-1),                       q = p - 2
+ *      horizontal edge nodes, line e = 0..nly, leaf column a, k = 1..q:
+ *          id = n_int + (e*nlx + a)*q + (k-1)
+ *      vertical edge nodes, line e = 0..nlx, leaf row b, j = 1..q:
+ *          id = n_int + n_h + (b*(nlx+1) + e)*q + (j-1)
+ *    with n_int = nlx*nly*q*q and n_h = nlx*(nly+1)*q.
+ *  - Handles are not thread-safe; distinct handles may be used concurrently.
+ *  - "stream" arguments are cudaStream_t passed as void* (NULL = legacy default).
+ */
+#ifndef EXPOP_H
+#define EXPOP_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+  EO_OK = 0,
+  EO_ERR_INVALID_ARG = 1, /* bad size, pointer or option                        */
+  EO_ERR_FIT = 2,         /* no rational approximant meets delta for the request */
+  EO_ERR_SINGULAR = 3,    /* a leaf, merge or root system is numerically singular */
+  EO_ERR_OOM = 4,         /* device or host allocation failed                   */
+  EO_ERR_BUDGET = 5,      /* operators would exceed opts.mem_budget_gb          */
+  EO_ERR_CUDA = 6,        /* a CUDA runtime / cuBLAS call failed                */
+  EO_ERR_TIMEOUT = 7,     /* a bounded device wait gave up                       */
+  EO_ERR_UNSUPPORTED = 8  /* request outside what this build implements          */
+} eo_status;
+
+typedef enum {
+  EO_WAVE_DIRICHLET = 0, /* u_t = v, v_t = div(c^2 grad u), u = 0 on the walls
+                            (two-field form of Example 2, Section 2.1)          */
+  EO_SW_WALLS = 1        /* u_t = f v - g h_x, v_t = -f u - g h_y,
+                            h_t = -H (u_x + v_y), no normal flow at the walls
+                            (Example 1, Section 2.1, constant f, g, H)          */
+} eo_kind;
+
+typedef enum {
+  EO_PREC_FP64 = 0 /* operators stored and applied in FP64 */
+} eo_precision;
+
+typedef struct eo_grid_s *eo_grid_t;
+typedef struct eo_handle_s *eo_handle_t;
+
+/* Options of eo_build_operator.  Zero-initialise and set what you need. */
+typedef struct {
+  int n_poles;         /* 2M+1 (odd) requested; the fitter then maximises the band
+                          X it covers and tau = X / band.  0: tau is given and the
+                          pole count is the smallest that covers tau * band.      */
+  double band;         /* Lambda of eq. RM_prop1: largest |eigenvalue| resolved   */
+  double tau;          /* time step (used when n_poles == 0)                      */
+  double delta;        /* accuracy of eq. RM_prop1 (0: 1e-10)                     */
+  double sw_f, sw_g, sw_H; /* shallow-water Coriolis, gravity, depth            */
+  int precision;       /* eo_precision                                           */
+  int shared_ops;      /* 1: one operator set per tree level (valid only for
+                          constant coefficients; EO_SW_WALLS); 0: one per box     */
+  int max_rhs;         /* largest n_rhs that eo_apply will be called with (>=1)   */
+  double mem_budget_gb;/* cap on operator storage in GB (0: no cap)               */
+} eo_opts;
+
+/* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.
+ * Errors: EO_ERR_INVALID_ARG.  The grid is owned by the library until
+ * eo_grid_destroy; handles built from it keep their own copy. */
+eo_status eo_grid_create(int nlx, int nly, int p, double x0, double x1, double y0,
+                         double y1, eo_grid_t *out);
+/* Sizes: total nodes, interior nodes, edge nodes.  Any pointer may be NULL. */
+eo_status eo_grid_info(eo_grid_t grid, int64_t *n_nodes, int64_t *n_interior,
+                       int64_t *n_edge);
+/* Coordinates of every node in the public order, into caller-owned HOST arrays
+ * of n_nodes doubles. */
+eo_status eo_grid_nodes(eo_grid_t grid, double *x, double *y);
+eo_status eo_grid_destroy(eo_grid_t grid);
+
+/* Build phase (Section 1.3): fit {alpha_m, b_m} (eqs. RM_prop1, RM_prop2), then
+ * on the device, in FP64, for each distinct pole (the conjugate pairs of
+ * eq. "conjugate, matrix inverses", Section 3.3): leaf collocation, leaf solution
+ * operators, merge-level Schur complements, and for EO_SW_WALLS the root
+ * oblique-boundary solve.  Operators stay resident in device memory until
+ * eo_destroy.
+ *   coeff: HOST array of n_nodes doubles with c^2 at the nodes (EO_WAVE_DIRICHLET);
+ *          ignored (may be NULL) for EO_SW_WALLS.
+ * Synchronous: returns when the operators are built.
+ * Errors: EO_ERR_INVALID_ARG, EO_ERR_FIT, EO_ERR_SINGULAR, EO_ERR_OOM,
+ *         EO_ERR_BUDGET, EO_ERR_CUDA, EO_ERR_UNSUPPORTED. */
+eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double *coeff,
+                            const eo_opts *opts, void *stream, eo_handle_t *out);
+
+/* The approximant in use: n = 2M+1 poles alpha (2n doubles, interleaved),
+ * residues b (2n doubles), the step tau and the band X = tau*Lambda it covers.
+ * Pass alpha = b = NULL to query n only.  Poles are ordered m = -M..M. */
+eo_status eo_get_poles(eo_handle_t h, double *alpha, double *b, int *n, double *tau,
+                       double *X);
+
+/* Bytes of device memory held for operators and for the apply workspace. */
+eo_status eo_memory(eo_handle_t h, int64_t *operator_bytes, int64_t *workspace_bytes);
+
+/* Apply phase: u <- R(tau L)^n_steps u for n_rhs states in DEVICE memory
+ * (u_dev: [n_rhs][fields][n_nodes] FP64, caller-owned, updated in place).
+ * Stream-ordered and asynchronous with respect to the host; n_rhs <= max_rhs.
+ * Each step runs two tree sweeps per distinct pole and the b_m-weighted sum.
+ * Errors: EO_ERR_INVALID_ARG, EO_ERR_CUDA (launch errors only; asynchronous
+ * faults surface at the caller's next synchronisation). */
+eo_status eo_apply(eo_handle_t h, double *u_dev, int n_rhs, int n_steps, void *stream);
+
+/* Same as eo_apply for a state in HOST memory (pinned or pageable): copies in,
+ * applies, copies back and synchronises the stream before returning. */
+eo_status eo_apply_host(eo_handle_t h, double *u_host, int n_rhs, int n_steps,
+                        void *stream);
+
+/* One resolvent: x = (tau L - alpha_j)^{-1} u for the pole of index j in the
+ * eo_get_poles order with Im(alpha_j) >= 0, for one state (n_rhs = 1).
+ * u_dev: DEVICE [fields][n_nodes] FP64.  x_dev: DEVICE [fields][n_nodes]
+ * complex (2 doubles each).  Asynchronous like eo_apply. */
+eo_status eo_apply_resolvent(eo_handle_t h, int j, const double *u_dev, double *x_dev,
+                             void *stream);
+
+/* Kernel tracing.  While on, every launch made by eo_apply / eo_apply_host /
+ * eo_apply_resolvent is bracketed by CUDA events recorded on the launching stream.
+ * eo_get_timing synchronises on those events and returns, per kernel class, the
+ * number of launches and their summed device time in milliseconds since the
+ * previous eo_get_timing (then resets).  Classes, in order: pre_map, up_leaf,
+ * up_merge, root, down_merge, down_leaf, edge_sum, post_map.
+ *   n_classes: in: capacity of the arrays; out: number of classes (8).
+ *   names: array of n_classes C strings owned by the library (may be NULL). */
+eo_status eo_set_timing(eo_handle_t h, int on);
+eo_status eo_get_timing(eo_handle_t h, int *n_classes, const char **names, int64_t *launches,
+                        double *ms);
+
+/* Release device memory.  Idempotent on NULL. */
+eo_status eo_destroy(eo_handle_t h);
+
+/* Message of the last error on this thread ("" if none).  Valid until the next
+ * library call on the same thread. */
+const char *eo_last_error(void);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* EXPOP_H */

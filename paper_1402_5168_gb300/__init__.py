@@ -1,0 +1,135 @@
+"""GB300 engine for repeated application of the rational time-evolution operator
+exp(tau L) ~ sum_m b_m (tau L - alpha_m)^{-1} (Haut, Babb, Martinsson, Wingate).
+
+Thin Python binding over the C ABI in ``include/expop.h``: it marshals
+arguments (device pointers of torch tensors, host numpy arrays, the CUDA
+stream) and does no arithmetic of its own.  Every step of the build and apply
+phases runs in the compiled library ``_build/libexpop.so``; if the library is
+missing the calls raise.
+"""
+from __future__ import annotations
+
+import ctypes as C
+
+import numpy as np
+
+from . import _capi
+from ._capi import SW_WALLS, WAVE_DIRICHLET, ExpopError, Opts, check
+
+__all__ = ["Grid", "Operator", "WAVE_DIRICHLET", "SW_WALLS", "ExpopError"]
+
+
+def _stream_ptr(stream):
+    if stream is None:
+        import torch
+        return C.c_void_p(torch.cuda.current_stream().cuda_stream)
+    if isinstance(stream, int):
+        return C.c_void_p(stream)
+    return C.c_void_p(stream.cuda_stream)
+
+
+class Grid:
+    """nlx x nly leaves of p x p Chebyshev nodes on [x0,x1] x [y0,y1]."""
+
+    def __init__(self, nlx, nly, p, x0=0.0, x1=1.0, y0=0.0, y1=1.0):
+        L = _capi.lib()
+        self._h = C.c_void_p()
+        check(L.eo_grid_create(nlx, nly, p, x0, x1, y0, y1, C.byref(self._h)))
+        n, ni, ne = C.c_int64(), C.c_int64(), C.c_int64()
+        check(L.eo_grid_info(self._h, C.byref(n), C.byref(ni), C.byref(ne)))
+        self.nlx, self.nly, self.p = nlx, nly, p
+        self.n_nodes, self.n_interior, self.n_edge = n.value, ni.value, ne.value
+
+    def nodes(self):
+        x = np.zeros(self.n_nodes)
+        y = np.zeros(self.n_nodes)
+        check(_capi.lib().eo_grid_nodes(self._h, x.ctypes.data_as(C.POINTER(C.c_double)),
+                                        y.ctypes.data_as(C.POINTER(C.c_double))))
+        return x, y
+
+    def __del__(self):
+        if getattr(self, "_h", None) and _capi._lib is not None:
+            _capi._lib.eo_grid_destroy(self._h)
+            self._h = None
+
+
+class Operator:
+    """Built operator R(tau L) = sum_m b_m (tau L - alpha_m)^{-1} on one GPU."""
+
+    def __init__(self, grid: Grid, kind: int, band: float, n_poles: int = 0, tau: float = 0.0,
+                 c2=None, f=0.0, g=1.0, H=1.0, delta=1e-10, shared_ops=False, max_rhs=1,
+                 mem_budget_gb=0.0, stream=None):
+        L = _capi.lib()
+        o = Opts(n_poles=n_poles, band=band, tau=tau, delta=delta, sw_f=f, sw_g=g, sw_H=H, precision=0,
+                 shared_ops=int(shared_ops), max_rhs=max_rhs, mem_budget_gb=mem_budget_gb)
+        coeff = None
+        if c2 is not None:
+            self._c2 = np.ascontiguousarray(c2, dtype=np.float64)
+            coeff = self._c2.ctypes.data_as(C.POINTER(C.c_double))
+        self._h = C.c_void_p()
+        self.grid = grid
+        self.kind = kind
+        self.fields = 2 if kind == WAVE_DIRICHLET else 3
+        self.max_rhs = max_rhs
+        check(L.eo_build_operator(grid._h, kind, coeff, C.byref(o), _stream_ptr(stream), C.byref(self._h)))
+        n, tau_, X = C.c_int(), C.c_double(), C.c_double()
+        check(L.eo_get_poles(self._h, None, None, C.byref(n), C.byref(tau_), C.byref(X)))
+        a = np.zeros(2 * n.value)
+        b = np.zeros(2 * n.value)
+        dp = C.POINTER(C.c_double)
+        check(L.eo_get_poles(self._h, a.ctypes.data_as(dp), b.ctypes.data_as(dp), C.byref(n), None, None))
+        self.alpha = a[0::2] + 1j * a[1::2]
+        self.b = b[0::2] + 1j * b[1::2]
+        self.tau, self.X = tau_.value, X.value
+
+    def memory(self):
+        ob, wb = C.c_int64(), C.c_int64()
+        check(_capi.lib().eo_memory(self._h, C.byref(ob), C.byref(wb)))
+        return ob.value, wb.value
+
+    def apply(self, u, n_steps=1, stream=None):
+        """u <- R(tau L)^n_steps u in place; u: CUDA float64 tensor [n_rhs, fields, n_nodes]
+        (or [fields, n_nodes] for one state)."""
+        if not (u.is_cuda and u.dtype.is_floating_point and u.element_size() == 8 and u.is_contiguous()):
+            raise ValueError("u must be a contiguous CUDA float64 tensor")
+        n_rhs = 1 if u.dim() == 2 else u.shape[0]
+        if u.shape[-2:] != (self.fields, self.grid.n_nodes):
+            raise ValueError(f"state shape must end with ({self.fields}, {self.grid.n_nodes})")
+        check(_capi.lib().eo_apply(self._h, C.c_void_p(u.data_ptr()), n_rhs, n_steps, _stream_ptr(stream)))
+        return u
+
+    def apply_host(self, u: np.ndarray, n_steps=1, stream=None):
+        """Same as apply for a host float64 array (copies in and out inside the call)."""
+        if u.dtype != np.float64 or not u.flags["C_CONTIGUOUS"]:
+            raise ValueError("u must be a C-contiguous float64 array")
+        n_rhs = 1 if u.ndim == 2 else u.shape[0]
+        check(_capi.lib().eo_apply_host(self._h, u.ctypes.data_as(C.POINTER(C.c_double)), n_rhs, n_steps,
+                                        _stream_ptr(stream)))
+        return u
+
+    def resolvent(self, j, u, x, stream=None):
+        """x <- (tau L - alpha_j)^{-1} u for pole index j (Im alpha_j >= 0); u float64
+        [fields, n_nodes], x complex128 [fields, n_nodes], both CUDA tensors."""
+        check(_capi.lib().eo_apply_resolvent(self._h, j, C.c_void_p(u.data_ptr()), C.c_void_p(x.data_ptr()),
+                                             _stream_ptr(stream)))
+        return x
+
+    def set_timing(self, on: bool):
+        check(_capi.lib().eo_set_timing(self._h, int(on)))
+
+    def timing(self):
+        """{kernel class: (launches, device ms)} since the previous call."""
+        n = C.c_int(16)
+        names = (C.c_char_p * 16)()
+        launches = (C.c_int64 * 16)()
+        ms = (C.c_double * 16)()
+        check(_capi.lib().eo_get_timing(self._h, C.byref(n), names, launches, ms))
+        return {names[i].decode(): (launches[i], ms[i]) for i in range(n.value)}
+
+    def close(self):
+        if getattr(self, "_h", None) and _capi._lib is not None:
+            _capi._lib.eo_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()

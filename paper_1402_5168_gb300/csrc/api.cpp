@@ -1,0 +1,394 @@
+// C ABI of include/expop.h: argument checks, handle set-up (fit, pole tables,
+// device allocations) and dispatch to the build and apply phases.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstring>
+#include <new>
+
+#include "handle.h"
+
+namespace eo {
+const char* last_error_cstr();
+}
+
+using namespace eo;
+typedef std::complex<double> cx;
+
+struct eo_grid_s {
+  Grid g;
+};
+struct eo_handle_s {
+  Handle h;
+  double* host_stage = nullptr;   // device state used by eo_apply_host
+};
+
+namespace eo {
+
+Handle::~Handle() {
+  for (void* p : allocs) cudaFree(p);
+  for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+}
+
+eo_status Handle::alloc(void** p, size_t bytes, bool op) {
+  if (bytes == 0) bytes = 16;
+  if (cudaMalloc(p, bytes) != cudaSuccess) {
+    cudaGetLastError();
+    *p = nullptr;
+    return fail(EO_ERR_OOM, "device allocation of " + std::to_string(bytes) + " bytes failed");
+  }
+  allocs.push_back(*p);
+  (op ? op_bytes : ws_bytes) += (int64_t)bytes;
+  return EO_OK;
+}
+
+}  // namespace eo
+
+namespace {
+
+template <typename T>
+eo_status upload(Handle& h, T** dst, const std::vector<T>& v, cudaStream_t st) {
+  eo_status rc = h.alloc((void**)dst, sizeof(T) * std::max<size_t>(1, v.size()), false);
+  if (rc) return rc;
+  if (!v.empty())
+    EO_CUDA_TRY(cudaMemcpyAsync(*dst, v.data(), sizeof(T) * v.size(), cudaMemcpyHostToDevice, st));
+  return EO_OK;
+}
+
+eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
+  const Grid& g = h.g;
+  const int p = g.p, q = g.q, ni = q * q, nb = 4 * q;
+  const int nleaf = g.nlx * g.nly;
+  // ---- approximant and time step
+  const double delta = o.delta > 0 ? o.delta : 1e-10;
+  if (!(o.band > 0)) return fail(EO_ERR_INVALID_ARG, "opts.band must be positive");
+  eo_status rc;
+  if (o.n_poles > 0) {
+    if ((rc = fit_for_poles(o.n_poles, delta, h.fit))) return rc;
+    h.tau = h.fit.X / o.band;
+  } else {
+    if (!(o.tau > 0)) return fail(EO_ERR_INVALID_ARG, "opts.tau must be positive when n_poles == 0");
+    if ((rc = fit_for_band(o.tau * o.band, delta, 301, h.fit))) return rc;
+    h.tau = o.tau;
+  }
+  const int N = h.fit.N(), M = (N - 1) / 2;
+  h.P = M + 1;
+  h.alpha.resize(h.P);
+  h.cw.resize(h.P);
+  h.pole_index.resize(h.P);
+  for (int j = 0; j < h.P; ++j) {
+    const int i = M + j;
+    h.pole_index[j] = i;
+    h.alpha[j] = cx(h.fit.are[i], h.fit.aim[i]);
+    h.cw[j] = (j == 0 ? 1.0 : 2.0) * cx(h.fit.bre[i], h.fit.bim[i]);
+  }
+  h.R = std::max(1, o.max_rhs);
+  h.shared = o.shared_ops ? 1 : 0;
+  const double tau = h.tau;
+  // ---- per-pole tables
+  std::vector<cd> coef, wgt, bcoef, nu;
+  double C[4] = {0, 0, 0, 0};
+  if (h.kind == EO_WAVE_DIRICHLET) {
+    h.K = 2; h.F = 2;
+    // elliptic unknown V: (A - (alpha/tau)^2) V = (alpha/tau^2) f_v + (1/tau) A f_u,
+    // U = (tau V - f_u) / alpha; sums: V = Re sum c V_p, U = Re sum (c tau/alpha) V_p - C0 f_u
+    for (int j = 0; j < h.P; ++j) {
+      const cx a = h.alpha[j], c = h.cw[j];
+      const cx c0 = a / (tau * tau), c1 = 1.0 / tau, w0 = c, w1 = c * tau / a;
+      coef.push_back(make_double2(c0.real(), c0.imag()));
+      coef.push_back(make_double2(c1.real(), c1.imag()));
+      wgt.push_back(make_double2(w0.real(), w0.imag()));
+      wgt.push_back(make_double2(w1.real(), w1.imag()));
+      C[0] += (c / a).real();
+    }
+  } else {
+    h.K = 3; h.F = 3;
+    const double f = o.sw_f, gg = o.sw_g, H = o.sw_H, tf = tau * f;
+    if (!(gg > 0) || !(H > 0)) return fail(EO_ERR_INVALID_ARG, "sw_g and sw_H must be positive");
+    for (int j = 0; j < h.P; ++j) {
+      const cx a = h.alpha[j], c = h.cw[j];
+      const cx D = a * a + tf * tf;
+      const cx c0 = D / (tau * tau * gg * H * a), c1 = -1.0 / (tau * gg), c2 = -f / (gg * a);
+      const cx w0 = c, w1 = c * (-a / D), w2 = c * (-tf / D);
+      for (cx v : {c0, c1, c2}) coef.push_back(make_double2(v.real(), v.imag()));
+      for (cx v : {w0, w1, w2}) wgt.push_back(make_double2(v.real(), v.imag()));
+      C[0] += w1.real();
+      C[1] += w2.real();
+      // wall right-hand sides per side S, E, N, W: coefficients of (F1, F2)
+      const cx xw0 = -a / (tau * gg), xw1 = -f / gg;       // x-walls: -(a F1 + tau f F2)/(tau g)
+      const cx yw0 = f / gg, yw1 = -a / (tau * gg);         // y-walls: (tau f F1 - a F2)/(tau g)
+      const cx sides[4][2] = {{yw0, yw1}, {xw0, xw1}, {yw0, yw1}, {xw0, xw1}};
+      for (int sd = 0; sd < 4; ++sd)
+        for (int t = 0; t < 2; ++t) bcoef.push_back(make_double2(sides[sd][t].real(), sides[sd][t].imag()));
+      const double sg[4] = {-1.0, 1.0, 1.0, -1.0};
+      for (int sd = 0; sd < 4; ++sd) nu.push_back(make_double2(sg[sd] * a.real(), sg[sd] * a.imag()));
+    }
+  }
+  std::memcpy(h.C, C, sizeof(C));
+  // scaled differentiation matrices
+  for (int i = 0; i < p * p; ++i) {
+    h.Dx[i] = g.D[i] * 2.0 / g.hx;
+    h.Dy[i] = g.D[i] * 2.0 / g.hy;
+  }
+  for (int i = 0; i < q * q; ++i) {
+    h.Ex[i] = g.Ed[i] * 2.0 / g.hx;
+    h.Ey[i] = g.Ed[i] * 2.0 / g.hy;
+  }
+  // ---- operator sizes and budget
+  const Plan& plan = h.plan;
+  const int L = plan.L();
+  const int nlo = h.shared ? 1 : nleaf;
+  const int64_t P = h.P;
+  int64_t ops = P * nlo * ((int64_t)nb * ni + (int64_t)ni * (ni + nb));
+  h.lv.resize(L + 1);
+  for (int l = 1; l <= L; ++l) {
+    const Level& lv = plan.lv[l];
+    LevelDev& ld = h.lv[l];
+    const bool root = l == L;
+    const bool need_par = !(root && h.kind == EO_WAVE_DIRICHLET);
+    const int nbo = h.shared ? 1 : lv.nbox;
+    ld.zu_rows = lv.n3 + (need_par ? lv.nbd : 0);
+    ld.zu_bstride = h.shared ? 0 : (int64_t)ld.zu_rows * lv.n3;
+    ld.zu_pstride = (int64_t)nbo * ld.zu_rows * lv.n3;
+    ops += P * ld.zu_pstride;
+    if (need_par) {
+      ld.s_bstride = h.shared ? 0 : (int64_t)lv.n3 * lv.nbd;
+      ld.s_pstride = (int64_t)nbo * lv.n3 * lv.nbd;
+      ops += P * ld.s_pstride;
+    }
+  }
+  if (h.kind == EO_SW_WALLS) {
+    h.nroot = plan.lv[L].nbd;
+    ops += P * (int64_t)h.nroot * h.nroot;
+  }
+  const double op_gb = (double)ops * sizeof(cd) / 1e9;
+  if (o.mem_budget_gb > 0 && op_gb > o.mem_budget_gb)
+    return fail(EO_ERR_BUDGET, "operators need " + std::to_string(op_gb) + " GB, over the budget");
+  // ---- allocations: operators
+  h.h_bstride = h.shared ? 0 : (int64_t)nb * ni;
+  h.h_pstride = (int64_t)nlo * nb * ni;
+  h.xy_bstride = h.shared ? 0 : (int64_t)ni * (ni + nb);
+  h.xy_pstride = (int64_t)nlo * ni * (ni + nb);
+  if ((rc = h.alloc((void**)&h.H, sizeof(cd) * P * h.h_pstride, true))) return rc;
+  if ((rc = h.alloc((void**)&h.XY, sizeof(cd) * P * h.xy_pstride, true))) return rc;
+  for (int l = 1; l <= L; ++l) {
+    LevelDev& ld = h.lv[l];
+    if ((rc = h.alloc((void**)&ld.ZU, sizeof(cd) * P * ld.zu_pstride, true))) return rc;
+    if (ld.s_pstride && (rc = h.alloc((void**)&ld.S, sizeof(cd) * P * ld.s_pstride, true))) return rc;
+  }
+  if (h.kind == EO_SW_WALLS && (rc = h.alloc((void**)&h.Binv, sizeof(cd) * P * h.nroot * h.nroot, true)))
+    return rc;
+  // ---- index maps
+  for (int l = 0; l <= L; ++l) {
+    const Level& lv = plan.lv[l];
+    LevelDev& ld = h.lv[l];
+    ld.nbox = lv.nbox; ld.nbx = lv.nbx; ld.nby = lv.nby; ld.nbd = lv.nbd; ld.nseg = lv.nseg;
+    ld.n3 = lv.n3; ld.dir = lv.dir;
+    if ((rc = upload(h, &ld.bseg, lv.bseg, st))) return rc;
+    if (l >= 1) {
+      ld.nbx_child = plan.lv[l - 1].nbx;
+      if ((rc = upload(h, &ld.par_child, lv.par_child, st))) return rc;
+      if ((rc = upload(h, &ld.par_idx, lv.par_idx, st))) return rc;
+      if ((rc = upload(h, &ld.a3, lv.a3, st))) return rc;
+      if ((rc = upload(h, &ld.b3, lv.b3, st))) return rc;
+      if ((rc = upload(h, &ld.iseg, lv.iseg, st))) return rc;
+    }
+  }
+  if ((rc = upload(h, &h.coef, coef, st))) return rc;
+  if ((rc = upload(h, &h.wgt, wgt, st))) return rc;
+  if (h.kind == EO_SW_WALLS) {
+    if ((rc = upload(h, &h.bcoef, bcoef, st))) return rc;
+    if ((rc = upload(h, &h.nu, nu, st))) return rc;
+  }
+  if ((rc = h.alloc((void**)&h.dDx, sizeof(double) * (2 * p * p + 2 * q * q), false))) return rc;
+  // ---- apply workspace
+  const int64_t R = h.R;
+  int64_t hmax = 0;
+  for (int l = 0; l <= L; ++l) hmax = std::max<int64_t>(hmax, (int64_t)plan.lv[l].nbox * plan.lv[l].nbd);
+  if ((rc = h.alloc((void**)&h.hA, sizeof(cd) * P * R * hmax, false))) return rc;
+  if ((rc = h.alloc((void**)&h.hB, sizeof(cd) * P * R * hmax, false))) return rc;
+  if ((rc = h.alloc((void**)&h.E, sizeof(cd) * P * R * g.n_edge, false))) return rc;
+  EO_CUDA_TRY(cudaMemsetAsync(h.E, 0, sizeof(cd) * P * R * g.n_edge, st));
+  for (int l = 1; l <= L; ++l) {
+    LevelDev& ld = h.lv[l];
+    if ((rc = h.alloc((void**)&ld.w3, sizeof(cd) * P * R * ld.nbox * ld.n3, false))) return rc;
+  }
+  h.nchunk = (int)std::min<int64_t>(P, 64);
+  if ((rc = h.alloc((void**)&h.part, sizeof(double) * h.nchunk * R * h.K * g.n_int, false))) return rc;
+  if ((rc = h.alloc((void**)&h.eacc, sizeof(double) * R * h.K * g.n_edge, false))) return rc;
+  if ((rc = h.alloc((void**)&h.ustate, sizeof(double) * R * h.F * g.n_nodes, false))) return rc;
+  if ((rc = h.alloc((void**)&h.pre, sizeof(double) * R * 2 * g.n_int, false))) return rc;
+  if (h.kind == EO_SW_WALLS) {
+    if ((rc = h.alloc((void**)&h.afull, sizeof(double) * R * h.K * g.n_nodes, false))) return rc;
+  } else {
+    if ((rc = h.alloc((void**)&h.acoef, sizeof(double) * g.n_nodes, false))) return rc;
+  }
+  return EO_OK;
+}
+
+}  // namespace
+
+extern "C" {
+
+eo_status eo_grid_create(int nlx, int nly, int p, double x0, double x1, double y0, double y1,
+                         eo_grid_t* out) {
+  if (!out) return fail(EO_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  eo_grid_s* gs = new (std::nothrow) eo_grid_s;
+  if (!gs) return fail(EO_ERR_OOM, "host allocation failed");
+  eo_status rc = make_grid(nlx, nly, p, x0, x1, y0, y1, gs->g);
+  if (rc) { delete gs; return rc; }
+  *out = gs;
+  set_error("");
+  return EO_OK;
+}
+
+eo_status eo_grid_info(eo_grid_t grid, int64_t* n_nodes, int64_t* n_interior, int64_t* n_edge) {
+  if (!grid) return fail(EO_ERR_INVALID_ARG, "null grid");
+  if (n_nodes) *n_nodes = grid->g.n_nodes;
+  if (n_interior) *n_interior = grid->g.n_int;
+  if (n_edge) *n_edge = grid->g.n_edge;
+  return EO_OK;
+}
+
+eo_status eo_grid_nodes(eo_grid_t grid, double* x, double* y) {
+  if (!grid || !x || !y) return fail(EO_ERR_INVALID_ARG, "null argument");
+  std::vector<double> vx, vy;
+  grid->g.coords(vx, vy);
+  std::memcpy(x, vx.data(), sizeof(double) * vx.size());
+  std::memcpy(y, vy.data(), sizeof(double) * vy.size());
+  return EO_OK;
+}
+
+eo_status eo_grid_destroy(eo_grid_t grid) {
+  delete grid;
+  return EO_OK;
+}
+
+eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double* coeff, const eo_opts* opts,
+                            void* stream, eo_handle_t* out) {
+  if (!grid || !opts || !out) return fail(EO_ERR_INVALID_ARG, "null argument");
+  *out = nullptr;
+  if (kind != EO_WAVE_DIRICHLET && kind != EO_SW_WALLS) return fail(EO_ERR_INVALID_ARG, "unknown kind");
+  if (kind == EO_WAVE_DIRICHLET && !coeff) return fail(EO_ERR_INVALID_ARG, "wave kind needs c^2 at the nodes");
+  if (kind == EO_WAVE_DIRICHLET && opts->shared_ops)
+    return fail(EO_ERR_INVALID_ARG, "shared operators need constant coefficients (EO_SW_WALLS)");
+  if (opts->precision != EO_PREC_FP64) return fail(EO_ERR_UNSUPPORTED, "only FP64 operators are built");
+  if (opts->max_rhs < 0) return fail(EO_ERR_INVALID_ARG, "max_rhs must be >= 1");
+  if (kind == EO_WAVE_DIRICHLET)
+    for (int64_t i = 0; i < grid->g.n_nodes; ++i)
+      if (!(coeff[i] > 0) || !std::isfinite(coeff[i]))
+        return fail(EO_ERR_INVALID_ARG, "c^2 must be positive and finite at every node");
+  eo_handle_s* hs = new (std::nothrow) eo_handle_s;
+  if (!hs) return fail(EO_ERR_OOM, "host allocation failed");
+  Handle& h = hs->h;
+  h.g = grid->g;
+  h.kind = kind;
+  h.opts = *opts;
+  make_plan(h.g, h.plan);
+  cudaStream_t st = (cudaStream_t)stream;
+  eo_status rc = setup(h, *opts, st);
+  if (!rc) rc = build(h, coeff, st);
+  if (rc) {
+    delete hs;
+    return rc;
+  }
+  *out = hs;
+  set_error("");
+  return EO_OK;
+}
+
+eo_status eo_get_poles(eo_handle_t hd, double* alpha, double* b, int* n, double* tau, double* X) {
+  if (!hd) return fail(EO_ERR_INVALID_ARG, "null handle");
+  const Fit& f = hd->h.fit;
+  if (n) *n = f.N();
+  if (tau) *tau = hd->h.tau;
+  if (X) *X = f.X;
+  if (alpha)
+    for (int i = 0; i < f.N(); ++i) { alpha[2 * i] = f.are[i]; alpha[2 * i + 1] = f.aim[i]; }
+  if (b)
+    for (int i = 0; i < f.N(); ++i) { b[2 * i] = f.bre[i]; b[2 * i + 1] = f.bim[i]; }
+  return EO_OK;
+}
+
+eo_status eo_memory(eo_handle_t hd, int64_t* operator_bytes, int64_t* workspace_bytes) {
+  if (!hd) return fail(EO_ERR_INVALID_ARG, "null handle");
+  if (operator_bytes) *operator_bytes = hd->h.op_bytes;
+  if (workspace_bytes) *workspace_bytes = hd->h.ws_bytes;
+  return EO_OK;
+}
+
+eo_status eo_apply(eo_handle_t hd, double* u_dev, int n_rhs, int n_steps, void* stream) {
+  if (!hd) return fail(EO_ERR_INVALID_ARG, "null handle");
+  return apply(hd->h, u_dev, n_rhs, n_steps, (cudaStream_t)stream);
+}
+
+eo_status eo_apply_host(eo_handle_t hd, double* u_host, int n_rhs, int n_steps, void* stream) {
+  if (!hd || !u_host) return fail(EO_ERR_INVALID_ARG, "null argument");
+  Handle& h = hd->h;
+  if (n_rhs < 1 || n_rhs > h.R) return fail(EO_ERR_INVALID_ARG, "n_rhs out of range [1, max_rhs]");
+  cudaStream_t st = (cudaStream_t)stream;
+  const size_t bytes = sizeof(double) * (size_t)n_rhs * h.F * h.g.n_nodes;
+  if (!hd->host_stage) {
+    eo_status rc = h.alloc((void**)&hd->host_stage, sizeof(double) * (size_t)h.R * h.F * h.g.n_nodes, false);
+    if (rc) return rc;
+  }
+  EO_CUDA_TRY(cudaMemcpyAsync(hd->host_stage, u_host, bytes, cudaMemcpyHostToDevice, st));
+  eo_status rc = apply(h, hd->host_stage, n_rhs, n_steps, st);
+  if (rc) return rc;
+  EO_CUDA_TRY(cudaMemcpyAsync(u_host, hd->host_stage, bytes, cudaMemcpyDeviceToHost, st));
+  EO_CUDA_TRY(cudaStreamSynchronize(st));
+  return EO_OK;
+}
+
+eo_status eo_apply_resolvent(eo_handle_t hd, int j, const double* u_dev, double* x_dev, void* stream) {
+  if (!hd || !u_dev || !x_dev) return fail(EO_ERR_INVALID_ARG, "null argument");
+  // j is an index of eo_get_poles' order; map to the distinct pole list (Im >= 0)
+  const Handle& h = hd->h;
+  const int M = (h.fit.N() - 1) / 2;
+  if (j < M || j >= h.fit.N()) return fail(EO_ERR_INVALID_ARG, "pole index must have Im(alpha) >= 0");
+  return apply_resolvent(hd->h, j - M, u_dev, x_dev, (cudaStream_t)stream);
+}
+
+eo_status eo_set_timing(eo_handle_t hd, int on) {
+  if (!hd) return fail(EO_ERR_INVALID_ARG, "null handle");
+  hd->h.timing = on != 0;
+  hd->h.ev_used = 0;
+  return EO_OK;
+}
+
+eo_status eo_get_timing(eo_handle_t hd, int* n_classes, const char** names, int64_t* launches, double* ms) {
+  static const char* kNames[TR_N] = {"pre_map", "up_leaf", "up_merge", "root", "down_merge", "down_leaf",
+                                     "edge_sum", "post_map"};
+  if (!hd || !n_classes) return fail(EO_ERR_INVALID_ARG, "null argument");
+  const int cap = *n_classes;
+  *n_classes = TR_N;
+  if (cap < TR_N) return fail(EO_ERR_INVALID_ARG, "arrays need room for 8 classes");
+  Handle& h = hd->h;
+  for (int c = 0; c < TR_N; ++c) {
+    if (names) names[c] = kNames[c];
+    if (launches) launches[c] = 0;
+    if (ms) ms[c] = 0.0;
+  }
+  for (int i = 0; i < h.ev_used; ++i) {
+    EO_CUDA_TRY(cudaEventSynchronize(h.ev_pool[2 * i + 1]));
+    float t = 0;
+    EO_CUDA_TRY(cudaEventElapsedTime(&t, h.ev_pool[2 * i], h.ev_pool[2 * i + 1]));
+    const int c = h.ev_class[i];
+    if (launches) launches[c] += 1;
+    if (ms) ms[c] += t;
+  }
+  h.ev_used = 0;
+  return EO_OK;
+}
+
+eo_status eo_destroy(eo_handle_t hd) {
+  delete hd;
+  return EO_OK;
+}
+
+const char* eo_last_error(void) { return last_error_cstr(); }
+
+}  // extern "C"

@@ -1,0 +1,914 @@
+// Apply phase: u <- sum_m b_m (tau L - alpha_m)^{-1} u  (Section 1.1, eq. def_RM),
+// with the conjugate-pole form of Section 3.3 (one solve per pair), each
+// resolvent through the precomputed nested-dissection operators of the build
+// (Section 2.3): an upward sweep (leaf particular fluxes, merge-level interface
+// corrections) and a downward sweep (interface values, then leaf interiors),
+// followed by the weighted pole sum and the recovery of every field from the
+// elliptic solution (Section 2.1).
+//
+// Every level is one launch over (poles x boxes x right-hand sides).  The
+// per-box products are complex matrix times (multi-)vector products in FP64:
+// operator blocks are column-major and read once per block with coalesced
+// 16-byte loads (consecutive threads take consecutive rows), the vectors sit
+// in shared memory, and when several columns share a block (shared per-level
+// operators, or several right-hand sides) each loaded entry feeds up to 8 of
+// them.  The pole sum is accumulated in FP64 in shared memory across the poles
+// a block owns and reduced in a fixed order, so results are deterministic.
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "handle.h"
+
+namespace eo {
+
+__device__ __forceinline__ cd cmul(cd a, cd b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void cfma(cd& acc, cd a, cd b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+
+// C[c][r] = sum_{j<k} A[r + j*lda] B[c][j]  for r < rows, c < NC.
+// Bs: shared [NC][kb]; Cs: shared [NC][rows]; red: shared [blockDim * NC].
+template <int NC>
+__device__ void cmv(const cd* __restrict__ A, int lda, int rows, int k, const cd* Bs, int kb,
+                    cd* Cs, cd* red) {
+  const int nt = blockDim.x, t = threadIdx.x;
+  int rp = (rows + 31) & ~31;
+  if (rp > nt) rp = nt;
+  const int ks = nt / rp;
+  const int ri = t % rp, kg = t / rp;
+  for (int r0 = 0; r0 < rows; r0 += rp) {
+    const int r = r0 + ri;
+    cd acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = make_double2(0.0, 0.0);
+    if (kg < ks && r < rows) {
+      const cd* Ar = A + r;
+      int j = kg;
+      for (; j + 3 * ks < k; j += 4 * ks) {
+        const cd a0 = __ldg(Ar + (size_t)j * lda);
+        const cd a1 = __ldg(Ar + (size_t)(j + ks) * lda);
+        const cd a2 = __ldg(Ar + (size_t)(j + 2 * ks) * lda);
+        const cd a3 = __ldg(Ar + (size_t)(j + 3 * ks) * lda);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          cfma(acc[c], a0, Bs[c * kb + j]);
+          cfma(acc[c], a1, Bs[c * kb + j + ks]);
+          cfma(acc[c], a2, Bs[c * kb + j + 2 * ks]);
+          cfma(acc[c], a3, Bs[c * kb + j + 3 * ks]);
+        }
+      }
+      for (; j < k; j += ks) {
+        const cd a = __ldg(Ar + (size_t)j * lda);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) cfma(acc[c], a, Bs[c * kb + j]);
+      }
+    }
+    if (ks == 1) {
+      if (r < rows)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Cs[c * rows + r] = acc[c];
+    } else {
+      if (kg < ks)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) red[(kg * NC + c) * rp + ri] = acc[c];
+      __syncthreads();
+      if (kg == 0 && r < rows) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          cd s = red[c * rp + ri];
+          for (int g = 1; g < ks; ++g) {
+            const cd v = red[(g * NC + c) * rp + ri];
+            s.x += v.x;
+            s.y += v.y;
+          }
+          Cs[c * rows + r] = s;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Kernel arguments shared by the sweep kernels.
+struct Sweep {
+  int R;                 // right-hand sides in this call
+  int P;                 // poles in this call (local index pl, operator index p0 + pl)
+  int p0;
+  int q, ni, nb;
+  long long n_int, n_edge, n_nodes;
+  int shared;
+  // pre-map sources (real, per rhs stride), K of them, and coefficients [P][K]
+  int K;
+  const double* src[3];
+  long long src_rs[3];
+  const cd* coef;
+  const cd* wgt;
+};
+
+__device__ __forceinline__ void col_box(int c, int R, int& box, int& r) {
+  box = c / R;
+  r = c - box * R;
+}
+
+// ---------------------------------------------------------------- up: leaves
+template <int NC>
+__global__ void __launch_bounds__(256) k_up_leaf(Sweep s, const cd* __restrict__ H, long long hps,
+                                                 long long hbs, int nleaf, cd* __restrict__ h0) {
+  extern __shared__ cd smem[];
+  const int pl = blockIdx.y, p = s.p0 + pl;
+  const int ncols = nleaf * s.R;
+  const int c0 = blockIdx.x * NC;
+  cd* Bs = smem;
+  cd* Cs = Bs + NC * s.ni;
+  cd* red = Cs + NC * s.nb;
+  int box0, r0;
+  col_box(c0, s.R, box0, r0);
+  cd cf[3];
+  for (int kk = 0; kk < s.K; ++kk) cf[kk] = s.coef[p * s.K + kk];
+  for (int e = threadIdx.x; e < NC * s.ni; e += blockDim.x) {
+    const int c = e / s.ni, j = e - c * s.ni;
+    cd g = make_double2(0.0, 0.0);
+    if (c0 + c < ncols) {
+      int box, r;
+      col_box(c0 + c, s.R, box, r);
+      for (int kk = 0; kk < s.K; ++kk) {
+        const double v = s.src[kk][r * s.src_rs[kk] + (long long)box * s.ni + j];
+        g.x += cf[kk].x * v;
+        g.y += cf[kk].y * v;
+      }
+    }
+    Bs[e] = g;
+  }
+  __syncthreads();
+  const cd* A = H + (long long)p * hps + (s.shared ? 0 : (long long)box0 * hbs);
+  cmv<NC>(A, s.nb, s.nb, s.ni, Bs, s.ni, Cs, red);
+  for (int e = threadIdx.x; e < NC * s.nb; e += blockDim.x) {
+    const int c = e / s.nb, row = e - c * s.nb;
+    if (c0 + c >= ncols) continue;
+    int box, r;
+    col_box(c0 + c, s.R, box, r);
+    h0[(((long long)pl * s.R + r) * nleaf + box) * s.nb + row] = Cs[e];
+  }
+}
+
+// ---------------------------------------------------------------- up: merges
+struct MergeArgs {
+  int nbox, nbx, nbx_c, nbox_c, dir, nbd, nbd_c, n3, zu_rows;
+  const int* par_child;
+  const int* par_idx;
+  const int* a3;
+  const int* b3;
+  const cd* ZU;
+  long long zps, zbs;
+  const cd* S;
+  long long sps, sbs;
+  const int* bseg;
+  const int* iseg;
+  int nseg;
+  cd* w3;
+};
+
+__device__ __forceinline__ void children(const MergeArgs& m, int box, int& ca, int& cb) {
+  const int bx = box % m.nbx, by = box / m.nbx;
+  if (m.dir == 0) { ca = by * m.nbx_c + 2 * bx; cb = ca + 1; }
+  else { ca = (2 * by) * m.nbx_c + bx; cb = ca + m.nbx_c; }
+}
+
+template <int NC>
+__global__ void __launch_bounds__(256) k_up_merge(Sweep s, MergeArgs m, const cd* __restrict__ hin,
+                                                  cd* __restrict__ hout) {
+  extern __shared__ cd smem[];
+  const int pl = blockIdx.y, p = s.p0 + pl;
+  const int ncols = m.nbox * s.R;
+  const int c0 = blockIdx.x * NC;
+  cd* Bs = smem;
+  cd* Cs = Bs + NC * m.n3;
+  cd* red = Cs + NC * m.zu_rows;
+  for (int e = threadIdx.x; e < NC * m.n3; e += blockDim.x) {
+    const int c = e / m.n3, t = e - c * m.n3;
+    cd v = make_double2(0.0, 0.0);
+    if (c0 + c < ncols) {
+      int box, r, ca, cb;
+      col_box(c0 + c, s.R, box, r);
+      children(m, box, ca, cb);
+      const cd* hr = hin + ((long long)pl * s.R + r) * m.nbox_c * m.nbd_c;
+      const cd x = hr[(long long)ca * m.nbd_c + m.a3[t]], y = hr[(long long)cb * m.nbd_c + m.b3[t]];
+      v = make_double2(x.x + y.x, x.y + y.y);
+    }
+    Bs[e] = v;
+  }
+  __syncthreads();
+  int box0, r0;
+  col_box(c0, s.R, box0, r0);
+  const cd* A = m.ZU + (long long)p * m.zps + (s.shared ? 0 : (long long)box0 * m.zbs);
+  cmv<NC>(A, m.zu_rows, m.zu_rows, m.n3, Bs, m.n3, Cs, red);
+  for (int e = threadIdx.x; e < NC * m.zu_rows; e += blockDim.x) {
+    const int c = e / m.zu_rows, row = e - c * m.zu_rows;
+    if (c0 + c >= ncols) continue;
+    int box, r;
+    col_box(c0 + c, s.R, box, r);
+    const cd v = Cs[e];
+    if (row < m.n3) {
+      m.w3[(((long long)pl * s.R + r) * m.nbox + box) * m.n3 + row] = v;
+    } else {
+      const int i = row - m.n3;
+      int ca, cb;
+      children(m, box, ca, cb);
+      const cd* hr = hin + ((long long)pl * s.R + r) * m.nbox_c * m.nbd_c;
+      const cd x = hr[(long long)(m.par_child[i] ? cb : ca) * m.nbd_c + m.par_idx[i]];
+      hout[(((long long)pl * s.R + r) * m.nbox + box) * m.nbd + i] = make_double2(x.x + v.x, x.y + v.y);
+    }
+  }
+}
+
+// ---------------------------------------------------------------- root (walls)
+struct RootArgs {
+  int n, q, sxq, syq;
+  const int* bseg;
+  const cd* Binv;
+  const cd* bcoef;   // [P][4][2]
+  const cd* nu;      // [P][4]
+  const double* state;
+  int F;
+};
+
+template <int NC>
+__global__ void __launch_bounds__(256) k_root_sw(Sweep s, RootArgs ra, const cd* __restrict__ hroot,
+                                                 cd* __restrict__ E) {
+  extern __shared__ cd smem[];
+  const int pl = blockIdx.y, p = s.p0 + pl;
+  const int c0 = blockIdx.x * NC;
+  const int n = ra.n;
+  cd* Bs = smem;
+  cd* Cs = Bs + NC * n;
+  cd* red = Cs + NC * n;
+  for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
+    const int c = e / n, i = e - c * n;
+    cd v = make_double2(0.0, 0.0);
+    const int r = c0 + c;
+    if (r < s.R) {
+      int side;
+      if (i < ra.sxq) side = 0;
+      else if (i < ra.sxq + ra.syq) side = 1;
+      else if (i < 2 * ra.sxq + ra.syq) side = 2;
+      else side = 3;
+      const long long node = s.n_int + (long long)ra.bseg[i / ra.q] * ra.q + (i % ra.q);
+      const double F1 = ra.state[(long long)r * ra.F * s.n_nodes + node];
+      const double F2 = ra.state[((long long)r * ra.F + 1) * s.n_nodes + node];
+      const cd b0 = ra.bcoef[(p * 4 + side) * 2], b1 = ra.bcoef[(p * 4 + side) * 2 + 1];
+      const cd nu = ra.nu[p * 4 + side];
+      const cd hr = hroot[((long long)pl * s.R + r) * n + i];
+      const cd nh = cmul(nu, hr);
+      v = make_double2(b0.x * F1 + b1.x * F2 - nh.x, b0.y * F1 + b1.y * F2 - nh.y);
+    }
+    Bs[e] = v;
+  }
+  __syncthreads();
+  cmv<NC>(ra.Binv + (long long)p * n * n, n, n, n, Bs, n, Cs, red);
+  for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
+    const int c = e / n, i = e - c * n;
+    const int r = c0 + c;
+    if (r >= s.R) continue;
+    E[((long long)pl * s.R + r) * s.n_edge + (long long)ra.bseg[i / ra.q] * ra.q + (i % ra.q)] = Cs[e];
+  }
+}
+
+// ---------------------------------------------------------------- down: merges
+template <int NC>
+__global__ void __launch_bounds__(256) k_down_merge(Sweep s, MergeArgs m, cd* __restrict__ E) {
+  extern __shared__ cd smem[];
+  const int pl = blockIdx.y, p = s.p0 + pl;
+  const int ncols = m.nbox * s.R;
+  const int c0 = blockIdx.x * NC;
+  cd* Bs = smem;
+  cd* Cs = Bs + NC * m.nbd;
+  cd* red = Cs + NC * m.n3;
+  const int q = s.q;
+  if (m.S) {
+    for (int e = threadIdx.x; e < NC * m.nbd; e += blockDim.x) {
+      const int c = e / m.nbd, i = e - c * m.nbd;
+      cd v = make_double2(0.0, 0.0);
+      if (c0 + c < ncols) {
+        int box, r;
+        col_box(c0 + c, s.R, box, r);
+        v = E[((long long)pl * s.R + r) * s.n_edge + (long long)m.bseg[box * m.nseg + i / q] * q + (i % q)];
+      }
+      Bs[e] = v;
+    }
+    __syncthreads();
+    int box0, r0;
+    col_box(c0, s.R, box0, r0);
+    const cd* A = m.S + (long long)p * m.sps + (s.shared ? 0 : (long long)box0 * m.sbs);
+    cmv<NC>(A, m.n3, m.n3, m.nbd, Bs, m.nbd, Cs, red);
+  }
+  const int n3s = m.n3 / q;
+  for (int e = threadIdx.x; e < NC * m.n3; e += blockDim.x) {
+    const int c = e / m.n3, row = e - c * m.n3;
+    if (c0 + c >= ncols) continue;
+    int box, r;
+    col_box(c0 + c, s.R, box, r);
+    cd v = m.w3[(((long long)pl * s.R + r) * m.nbox + box) * m.n3 + row];
+    if (m.S) {
+      v.x += Cs[e].x;
+      v.y += Cs[e].y;
+    }
+    E[((long long)pl * s.R + r) * s.n_edge + (long long)m.iseg[box * n3s + row / q] * q + (row % q)] = v;
+  }
+}
+
+// ---------------------------------------------------------------- down: leaves + pole sum
+template <int NC>
+__global__ void __launch_bounds__(256) k_down_leaf(Sweep s, const cd* __restrict__ XY, long long xps,
+                                                   long long xbs, const int* __restrict__ bseg, int nleaf,
+                                                   int ppc, const cd* __restrict__ E,
+                                                   double* __restrict__ part) {
+  extern __shared__ cd smem[];
+  const int ni = s.ni, nb = s.nb, k = ni + nb, q = s.q;
+  const int ncols = nleaf * s.R;
+  const int c0 = blockIdx.x * NC;
+  const int chunk = blockIdx.y;
+  cd* Bs = smem;
+  cd* Cs = Bs + NC * k;
+  cd* red = Cs + NC * ni;
+  double* acc = (double*)(red + blockDim.x * NC);   // [NC][K][ni]
+  for (int e = threadIdx.x; e < NC * s.K * ni; e += blockDim.x) acc[e] = 0.0;
+  int box0, r0;
+  col_box(c0, s.R, box0, r0);
+  const int pbeg = chunk * ppc, pend = min(s.P, pbeg + ppc);
+  for (int pl = pbeg; pl < pend; ++pl) {
+    const int p = s.p0 + pl;
+    cd cf[3];
+    for (int kk = 0; kk < s.K; ++kk) cf[kk] = s.coef[p * s.K + kk];
+    __syncthreads();
+    for (int e = threadIdx.x; e < NC * k; e += blockDim.x) {
+      const int c = e / k, j = e - c * k;
+      cd v = make_double2(0.0, 0.0);
+      if (c0 + c < ncols) {
+        int box, r;
+        col_box(c0 + c, s.R, box, r);
+        if (j < ni) {
+          for (int kk = 0; kk < s.K; ++kk) {
+            const double x = s.src[kk][r * s.src_rs[kk] + (long long)box * ni + j];
+            v.x += cf[kk].x * x;
+            v.y += cf[kk].y * x;
+          }
+        } else {
+          const int i = j - ni;
+          v = E[((long long)pl * s.R + r) * s.n_edge + (long long)bseg[box * 4 + i / q] * q + (i % q)];
+        }
+      }
+      Bs[e] = v;
+    }
+    __syncthreads();
+    const cd* A = XY + (long long)p * xps + (s.shared ? 0 : (long long)box0 * xbs);
+    cmv<NC>(A, ni, ni, k, Bs, k, Cs, red);
+    cd w[3];
+    for (int kk = 0; kk < s.K; ++kk) w[kk] = s.wgt[p * s.K + kk];
+    for (int e = threadIdx.x; e < NC * ni; e += blockDim.x) {
+      const int c = e / ni, row = e - c * ni;
+      const cd x = Cs[e];
+      for (int kk = 0; kk < s.K; ++kk) acc[(c * s.K + kk) * ni + row] += w[kk].x * x.x - w[kk].y * x.y;
+    }
+  }
+  __syncthreads();
+  for (int e = threadIdx.x; e < NC * s.K * ni; e += blockDim.x) {
+    const int c = e / (s.K * ni), rem = e - c * s.K * ni, kk = rem / ni, row = rem - kk * ni;
+    if (c0 + c >= ncols) continue;
+    int box, r;
+    col_box(c0 + c, s.R, box, r);
+    part[(((long long)chunk * s.R + r) * s.K + kk) * s.n_int + (long long)box * ni + row] = acc[e];
+  }
+}
+
+// edge-node pole sums: eacc[r][k][e] = sum_p Re(w[p][k] E_p[r][e])
+__global__ void k_edge_acc(Sweep s, const cd* __restrict__ E, double* __restrict__ eacc) {
+  const long long tot = (long long)s.R * s.n_edge;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / s.n_edge);
+    const long long e = t - (long long)r * s.n_edge;
+    double a[3] = {0, 0, 0};
+    for (int pl = 0; pl < s.P; ++pl) {
+      const cd x = E[((long long)pl * s.R + r) * s.n_edge + e];
+      for (int kk = 0; kk < s.K; ++kk) {
+        const cd w = s.wgt[(s.p0 + pl) * s.K + kk];
+        a[kk] += w.x * x.x - w.y * x.y;
+      }
+    }
+    for (int kk = 0; kk < s.K; ++kk) eacc[((long long)r * s.K + kk) * s.n_edge + e] = a[kk];
+  }
+}
+
+// accumulated field kk at node (r) from the chunk partials / edge sums
+__device__ __forceinline__ double accum(const Sweep& s, int nchunk, const double* part,
+                                        const double* eacc, int r, int kk, long long node) {
+  if (node < s.n_int) {
+    double v = 0;
+    for (int c = 0; c < nchunk; ++c) v += part[(((long long)c * s.R + r) * s.K + kk) * s.n_int + node];
+    return v;
+  }
+  return eacc[((long long)r * s.K + kk) * s.n_edge + (node - s.n_int)];
+}
+
+// wave post-map: v = A0, u = A1 - C0 u_in
+__global__ void k_post_wave(Sweep s, int nchunk, const double* __restrict__ part,
+                            const double* __restrict__ eacc, const double* __restrict__ uin,
+                            double* __restrict__ uout, double C0) {
+  const long long tot = (long long)s.R * s.n_nodes;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / s.n_nodes);
+    const long long node = t - (long long)r * s.n_nodes;
+    const double a0 = accum(s, nchunk, part, eacc, r, 0, node);
+    const double a1 = accum(s, nchunk, part, eacc, r, 1, node);
+    const double u = uin[(long long)r * 2 * s.n_nodes + node];
+    uout[(long long)r * 2 * s.n_nodes + node] = a1 - C0 * u;
+    uout[((long long)r * 2 + 1) * s.n_nodes + node] = a0;
+  }
+}
+
+// shallow water: accumulated fields at every node, afull[r][k][node]
+__global__ void k_reduce_full(Sweep s, int nchunk, const double* __restrict__ part,
+                              const double* __restrict__ eacc, double* __restrict__ afull) {
+  const long long tot = (long long)s.R * s.K * s.n_nodes;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long rk = t / s.n_nodes;
+    const long long node = t - rk * s.n_nodes;
+    const int r = (int)(rk / s.K), kk = (int)(rk % s.K);
+    afull[t] = accum(s, nchunk, part, eacc, r, kk, node);
+  }
+}
+
+struct LeafGeo {
+  int nlx, nly, p, q;
+  long long n_int, n_hseg;
+  const double* Dx;   // p x p row-major (scaled)
+  const double* Dy;
+  const double* Ex;   // q x q
+  const double* Ey;
+};
+
+__device__ __forceinline__ long long gnode(const LeafGeo& g, int a, int b, int k, int j) {
+  const int p = g.p, q = g.q;
+  const bool kin = k > 0 && k < p - 1, jin = j > 0 && j < p - 1;
+  if (kin && jin) return ((long long)b * g.nlx + a) * q * q + (long long)(j - 1) * q + (k - 1);
+  if (kin) return g.n_int + ((long long)(j == 0 ? b : b + 1) * g.nlx + a) * q + (k - 1);
+  if (jin) return g.n_int + (g.n_hseg + (long long)b * (g.nlx + 1) + (k == 0 ? a : a + 1)) * q + (j - 1);
+  return -1;
+}
+
+// derivatives of a leaf-local field f[j*p+k] (corners unused)
+__device__ __forceinline__ double ddx(const LeafGeo& g, const double* f, int k, int j) {
+  double s = 0;
+  for (int m = 0; m < g.p; ++m) s += g.Dx[k * g.p + m] * f[j * g.p + m];
+  return s;
+}
+__device__ __forceinline__ double ddy(const LeafGeo& g, const double* f, int k, int j) {
+  double s = 0;
+  for (int m = 0; m < g.p; ++m) s += g.Dy[j * g.p + m] * f[m * g.p + k];
+  return s;
+}
+
+// wave pre-map: A u = d/dx(c^2 du/dx) + d/dy(c^2 du/dy) at interior nodes by
+// nested leaf differentiation (the collocation rows of Section 2.2), pre[r][n_int]
+__global__ void k_pre_wave(LeafGeo g, int R, long long n_nodes, const double* __restrict__ acoef,
+                           const double* __restrict__ state, double* __restrict__ pre) {
+  const int leaf = blockIdx.x, r = blockIdx.y;
+  const int a = leaf % g.nlx, b = leaf / g.nlx, p = g.p, q = g.q;
+  extern __shared__ double sd[];
+  double* u = sd;
+  double* al = sd + p * p;
+  double* fx = sd + 2 * p * p;   // a * du/dx at (l, j)
+  double* fy = sd + 3 * p * p;   // a * du/dy at (k, l)
+  const double* U = state + (long long)r * 2 * n_nodes;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const long long id = gnode(g, a, b, t % p, t / p);
+    u[t] = id < 0 ? 0.0 : U[id];
+    al[t] = id < 0 ? 0.0 : acoef[id];
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int k = t % p, j = t / p;
+    double sx = 0, sy = 0;
+    for (int m = 0; m < p; ++m) {
+      sx += g.Dx[k * p + m] * u[j * p + m];
+      sy += g.Dy[j * p + m] * u[m * p + k];
+    }
+    fx[t] = al[t] * sx;
+    fy[t] = al[t] * sy;
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < q * q; t += blockDim.x) {
+    const int k = t % q + 1, j = t / q + 1;
+    double s = 0;
+    for (int l = 0; l < p; ++l) s += g.Dx[k * p + l] * fx[j * p + l] + g.Dy[j * p + l] * fy[l * p + k];
+    pre[(long long)r * g.n_int + (long long)leaf * q * q + t] = s;
+  }
+}
+
+// shallow-water pre-map: div F and curl F at interior nodes, pre[r][0|1][n_int]
+__global__ void k_pre_sw(LeafGeo g, int R, long long n_nodes, const double* __restrict__ state,
+                         double* __restrict__ pre) {
+  const int leaf = blockIdx.x, r = blockIdx.y;
+  const int a = leaf % g.nlx, b = leaf / g.nlx, p = g.p, q = g.q;
+  extern __shared__ double sd[];
+  double* f1 = sd;
+  double* f2 = sd + p * p;
+  const double* F1 = state + (long long)r * 3 * n_nodes;
+  const double* F2 = F1 + n_nodes;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const long long id = gnode(g, a, b, t % p, t / p);
+    f1[t] = id < 0 ? 0.0 : F1[id];
+    f2[t] = id < 0 ? 0.0 : F2[id];
+  }
+  __syncthreads();
+  const long long ni = (long long)q * q;
+  for (int t = threadIdx.x; t < q * q; t += blockDim.x) {
+    const int k = t % q + 1, j = t / q + 1;
+    const long long o = (long long)leaf * ni + t;
+    pre[((long long)r * 2) * g.n_int + o] = ddx(g, f1, k, j) + ddy(g, f2, k, j);
+    pre[((long long)r * 2 + 1) * g.n_int + o] = ddx(g, f2, k, j) - ddy(g, f1, k, j);
+  }
+}
+
+// shallow-water post-map: h = A0,
+//   U = C1 F1 + C2 F2 + tau g (dA1/dx + dA2/dy), V = -C2 F1 + C1 F2 + tau g (-dA2/dx + dA1/dy)
+// Interior nodes by leaf differentiation; edge nodes owned by this leaf (S and W,
+// plus E / N on the domain boundary): normal derivative = mean of the one-sided
+// derivatives of the leaves that touch the edge, tangential = edge interpolant.
+__global__ void k_post_sw(LeafGeo g, int R, long long n_nodes, int K, const double* __restrict__ afull,
+                          const double* __restrict__ uin, double* __restrict__ uout, double C1, double C2,
+                          double taug) {
+  const int leaf = blockIdx.x, r = blockIdx.y;
+  const int a = leaf % g.nlx, b = leaf / g.nlx, p = g.p, q = g.q;
+  extern __shared__ double sd[];
+  double* A1 = sd;              // this leaf, p x p
+  double* A2 = sd + p * p;
+  double* W1 = sd + 2 * p * p;  // west neighbour, p x p
+  double* W2 = sd + 3 * p * p;
+  double* S1 = sd + 4 * p * p;  // south neighbour, p x p
+  double* S2 = sd + 5 * p * p;
+  const double* a1g = afull + ((long long)r * K + 1) * n_nodes;
+  const double* a2g = afull + ((long long)r * K + 2) * n_nodes;
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int k = t % p, j = t / p;
+    long long id = gnode(g, a, b, k, j);
+    A1[t] = id < 0 ? 0.0 : a1g[id];
+    A2[t] = id < 0 ? 0.0 : a2g[id];
+    id = a > 0 ? gnode(g, a - 1, b, k, j) : -1;
+    W1[t] = id < 0 ? 0.0 : a1g[id];
+    W2[t] = id < 0 ? 0.0 : a2g[id];
+    id = b > 0 ? gnode(g, a, b - 1, k, j) : -1;
+    S1[t] = id < 0 ? 0.0 : a1g[id];
+    S2[t] = id < 0 ? 0.0 : a2g[id];
+  }
+  __syncthreads();
+  const double* in = uin + (long long)r * 3 * n_nodes;
+  double* out = uout + (long long)r * 3 * n_nodes;
+  const double* a0g = afull + ((long long)r * K) * n_nodes;
+  auto emit = [&](long long id, double d1x, double d1y, double d2x, double d2y) {
+    const double F1 = in[id], F2 = in[n_nodes + id];
+    out[id] = C1 * F1 + C2 * F2 + taug * (d1x + d2y);
+    out[n_nodes + id] = -C2 * F1 + C1 * F2 + taug * (-d2x + d1y);
+    out[2 * n_nodes + id] = a0g[id];
+  };
+  // interior
+  for (int t = threadIdx.x; t < q * q; t += blockDim.x) {
+    const int k = t % q + 1, j = t / q + 1;
+    emit(gnode(g, a, b, k, j), ddx(g, A1, k, j), ddy(g, A1, k, j), ddx(g, A2, k, j), ddy(g, A2, k, j));
+  }
+  // owned edges
+  for (int t = threadIdx.x; t < 4 * q; t += blockDim.x) {
+    const int side = t / q, o = t % q + 1;
+    if (side == 1 && a != g.nlx - 1) continue;   // E edge owned by the east neighbour
+    if (side == 2 && b != g.nly - 1) continue;   // N edge owned by the north neighbour
+    double d1x, d1y, d2x, d2y;
+    long long id;
+    if (side == 0 || side == 2) {                // horizontal edge: normal y, tangential x
+      const int j = side == 0 ? 0 : p - 1, k = o;
+      id = gnode(g, a, b, k, j);
+      d1y = ddy(g, A1, k, j);
+      d2y = ddy(g, A2, k, j);
+      if (side == 0 && b > 0) {
+        d1y = 0.5 * (d1y + ddy(g, S1, k, p - 1));
+        d2y = 0.5 * (d2y + ddy(g, S2, k, p - 1));
+      }
+      d1x = 0; d2x = 0;
+      for (int m = 1; m <= q; ++m) {
+        d1x += g.Ex[(k - 1) * q + (m - 1)] * A1[j * p + m];
+        d2x += g.Ex[(k - 1) * q + (m - 1)] * A2[j * p + m];
+      }
+    } else {                                     // vertical edge: normal x, tangential y
+      const int k = side == 3 ? 0 : p - 1, j = o;
+      id = gnode(g, a, b, k, j);
+      d1x = ddx(g, A1, k, j);
+      d2x = ddx(g, A2, k, j);
+      if (side == 3 && a > 0) {
+        d1x = 0.5 * (d1x + ddx(g, W1, p - 1, j));
+        d2x = 0.5 * (d2x + ddx(g, W2, p - 1, j));
+      }
+      d1y = 0; d2y = 0;
+      for (int m = 1; m <= q; ++m) {
+        d1y += g.Ey[(j - 1) * q + (m - 1)] * A1[m * p + k];
+        d2y += g.Ey[(j - 1) * q + (m - 1)] * A2[m * p + k];
+      }
+    }
+    emit(id, d1x, d1y, d2x, d2y);
+  }
+}
+
+// ---------------------------------------------------------------- host driver
+namespace {
+
+int pick_nc(int shared, int R, int k, int rows) {
+  int nc = 1;
+  if (shared) nc = 8;
+  else {
+    while (nc < 8 && R % (nc * 2) == 0) nc *= 2;
+  }
+  // keep the shared-memory footprint under ~200 KB
+  while (nc > 1 && (size_t)nc * (k + rows + 256) * sizeof(cd) > 200 * 1024) nc /= 2;
+  return nc;
+}
+
+template <template <int> class Launcher, typename... Args>
+eo_status dispatch(int nc, Args&&... args) {
+  switch (nc) {
+    case 1: return Launcher<1>::run(args...);
+    case 2: return Launcher<2>::run(args...);
+    case 4: return Launcher<4>::run(args...);
+    default: return Launcher<8>::run(args...);
+  }
+}
+
+#define EO_SET_SMEM(kern, bytes)                                                              \
+  do {                                                                                        \
+    if ((bytes) > 48 * 1024)                                                                  \
+      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes))); \
+  } while (0)
+
+template <int NC>
+struct UpLeaf {
+  static eo_status run(const Sweep& s, const Handle& h, int nleaf, cd* h0, cudaStream_t st) {
+    const int ncols = nleaf * s.R;
+    dim3 grid((ncols + NC - 1) / NC, s.P);
+    const size_t smem = sizeof(cd) * ((size_t)NC * (s.ni + s.nb) + 256 * NC);
+    EO_SET_SMEM(k_up_leaf<NC>, smem);
+    k_up_leaf<NC><<<grid, 256, smem, st>>>(s, h.H, h.h_pstride, h.h_bstride, nleaf, h0);
+    EO_CUDA_TRY(cudaGetLastError());
+    return EO_OK;
+  }
+};
+
+template <int NC>
+struct UpMerge {
+  static eo_status run(const Sweep& s, const MergeArgs& m, const cd* hin, cd* hout, cudaStream_t st) {
+    dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
+    const size_t smem = sizeof(cd) * ((size_t)NC * (m.n3 + m.zu_rows) + 256 * NC);
+    EO_SET_SMEM(k_up_merge<NC>, smem);
+    k_up_merge<NC><<<grid, 256, smem, st>>>(s, m, hin, hout);
+    EO_CUDA_TRY(cudaGetLastError());
+    return EO_OK;
+  }
+};
+
+template <int NC>
+struct DownMerge {
+  static eo_status run(const Sweep& s, const MergeArgs& m, cd* E, cudaStream_t st) {
+    dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
+    const size_t smem = sizeof(cd) * ((size_t)NC * (m.nbd + m.n3) + 256 * NC);
+    EO_SET_SMEM(k_down_merge<NC>, smem);
+    k_down_merge<NC><<<grid, 256, smem, st>>>(s, m, E);
+    EO_CUDA_TRY(cudaGetLastError());
+    return EO_OK;
+  }
+};
+
+template <int NC>
+struct RootSW {
+  static eo_status run(const Sweep& s, const RootArgs& ra, const cd* hroot, cd* E, cudaStream_t st) {
+    dim3 grid((s.R + NC - 1) / NC, s.P);
+    const size_t smem = sizeof(cd) * ((size_t)NC * 2 * ra.n + 256 * NC);
+    EO_SET_SMEM(k_root_sw<NC>, smem);
+    k_root_sw<NC><<<grid, 256, smem, st>>>(s, ra, hroot, E);
+    EO_CUDA_TRY(cudaGetLastError());
+    return EO_OK;
+  }
+};
+
+template <int NC>
+struct DownLeaf {
+  static eo_status run(const Sweep& s, const Handle& h, int nleaf, int nchunk, int ppc, const cd* E,
+                       double* part, cudaStream_t st) {
+    dim3 grid((nleaf * s.R + NC - 1) / NC, nchunk);
+    const size_t smem = sizeof(cd) * ((size_t)NC * (s.ni + s.nb + s.ni) + 256 * NC) +
+                        sizeof(double) * NC * s.K * s.ni;
+    EO_SET_SMEM(k_down_leaf<NC>, smem);
+    k_down_leaf<NC><<<grid, 256, smem, st>>>(s, h.XY, h.xy_pstride, h.xy_bstride, h.lv[0].bseg, nleaf, ppc,
+                                            E, part);
+    EO_CUDA_TRY(cudaGetLastError());
+    return EO_OK;
+  }
+};
+
+MergeArgs merge_args(const Handle& h, int l) {
+  const LevelDev& ld = h.lv[l];
+  const LevelDev& lc = h.lv[l - 1];
+  MergeArgs m;
+  m.nbox = ld.nbox; m.nbx = ld.nbx; m.nbx_c = lc.nbx; m.nbox_c = lc.nbox; m.dir = ld.dir;
+  m.nbd = ld.nbd; m.nbd_c = lc.nbd; m.n3 = ld.n3; m.zu_rows = ld.zu_rows;
+  m.par_child = ld.par_child; m.par_idx = ld.par_idx; m.a3 = ld.a3; m.b3 = ld.b3;
+  m.ZU = ld.ZU; m.zps = ld.zu_pstride; m.zbs = ld.zu_bstride;
+  m.S = ld.S; m.sps = ld.s_pstride; m.sbs = ld.s_bstride;
+  m.bseg = ld.bseg; m.iseg = ld.iseg; m.nseg = ld.nseg; m.w3 = ld.w3;
+  return m;
+}
+
+// One application of sum_p c_p (tau L - alpha_p)^{-1} restricted to poles
+// [p0, p0 + np) with accumulation weights wgt (device [P][K]) and post constants C.
+eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, int np, const cd* wgt,
+                   const double* C, cudaStream_t st) {
+  const Grid& g = h.g;
+  const int q = g.q, ni = q * q, nb = 4 * q;
+  const int nleaf = g.nlx * g.nly;
+  const int L = h.plan.L();
+  eo_status rc;
+  Sweep s;
+  s.R = R; s.P = np; s.p0 = p0; s.q = q; s.ni = ni; s.nb = nb;
+  s.n_int = g.n_int; s.n_edge = g.n_edge; s.n_nodes = g.n_nodes; s.shared = h.shared;
+  s.K = h.K; s.coef = h.coef; s.wgt = wgt;
+  LeafGeo geo{g.nlx, g.nly, g.p, q, g.n_int, g.n_hseg, h.dDx, h.dDx + g.p * g.p, h.dDx + 2 * g.p * g.p,
+              h.dDx + 2 * g.p * g.p + q * q};
+  if (h.kind == EO_WAVE_DIRICHLET) {
+    // s = (alpha / tau^2) v + (1 / tau) A u: sources v (field 1) and A u (pre-map)
+    if ((rc = h.trace_begin(st))) return rc;
+    k_pre_wave<<<dim3(nleaf, R), 128, sizeof(double) * 4 * g.p * g.p, st>>>(geo, R, g.n_nodes, h.acoef, uin,
+                                                                          h.pre);
+    EO_CUDA_TRY(cudaGetLastError());
+    if ((rc = h.trace_end(TR_PRE, st))) return rc;
+    s.src[0] = uin + g.n_nodes; s.src_rs[0] = 2 * g.n_nodes;
+    s.src[1] = h.pre;           s.src_rs[1] = g.n_int;
+  } else {
+    if ((rc = h.trace_begin(st))) return rc;
+    k_pre_sw<<<dim3(nleaf, R), 128, sizeof(double) * 2 * g.p * g.p, st>>>(geo, R, g.n_nodes, uin, h.pre);
+    EO_CUDA_TRY(cudaGetLastError());
+    if ((rc = h.trace_end(TR_PRE, st))) return rc;
+    s.src[0] = uin + 2 * g.n_nodes; s.src_rs[0] = 3 * g.n_nodes;
+    s.src[1] = h.pre;               s.src_rs[1] = 2 * g.n_int;
+    s.src[2] = h.pre + g.n_int;     s.src_rs[2] = 2 * g.n_int;
+  }
+  // up: leaves
+  cd* hcur = h.hA;
+  cd* hnext = h.hB;
+  if ((rc = h.trace_begin(st))) return rc;
+  if ((rc = dispatch<UpLeaf>(pick_nc(h.shared, R, ni, nb), s, h, nleaf, hcur, st))) return rc;
+  if ((rc = h.trace_end(TR_UP_LEAF, st))) return rc;
+  // up: merges
+  for (int l = 1; l <= L; ++l) {
+    MergeArgs m = merge_args(h, l);
+    if ((rc = h.trace_begin(st))) return rc;
+    if ((rc = dispatch<UpMerge>(pick_nc(h.shared, R, m.n3, m.zu_rows), s, m, hcur, hnext, st))) return rc;
+    if ((rc = h.trace_end(TR_UP_MERGE, st))) return rc;
+    std::swap(hcur, hnext);
+  }
+  // root
+  if (h.kind == EO_SW_WALLS) {
+    const Level& rl = h.plan.lv[L];
+    RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.Binv, h.bcoef, h.nu, uin, 3};
+    if ((rc = h.trace_begin(st))) return rc;
+    if ((rc = dispatch<RootSW>(pick_nc(0, R, rl.nbd, rl.nbd), s, ra, hcur, h.E, st))) return rc;
+    if ((rc = h.trace_end(TR_ROOT, st))) return rc;
+  }
+  // down: merges
+  for (int l = L; l >= 1; --l) {
+    MergeArgs m = merge_args(h, l);
+    if ((rc = h.trace_begin(st))) return rc;
+    if ((rc = dispatch<DownMerge>(pick_nc(h.shared, R, m.nbd, m.n3), s, m, h.E, st))) return rc;
+    if ((rc = h.trace_end(TR_DOWN_MERGE, st))) return rc;
+  }
+  // down: leaves with the pole sum
+  const int nc = pick_nc(h.shared, R, ni + nb, ni);
+  const int ncg = (nleaf * R + nc - 1) / nc;
+  int nchunk = std::max(1, std::min(np, (608 + ncg - 1) / ncg));
+  nchunk = std::min(nchunk, h.nchunk);
+  const int ppc = (np + nchunk - 1) / nchunk;
+  nchunk = (np + ppc - 1) / ppc;
+  if ((rc = h.trace_begin(st))) return rc;
+  if ((rc = dispatch<DownLeaf>(nc, s, h, nleaf, nchunk, ppc, h.E, h.part, st))) return rc;
+  if ((rc = h.trace_end(TR_DOWN_LEAF, st))) return rc;
+  if ((rc = h.trace_begin(st))) return rc;
+  k_edge_acc<<<(unsigned)std::max<long long>(1, std::min<long long>(4096, (R * g.n_edge + 255) / 256)), 256, 0, st>>>(
+      s, h.E, h.eacc);
+  EO_CUDA_TRY(cudaGetLastError());
+  if ((rc = h.trace_end(TR_EDGE, st))) return rc;
+  if ((rc = h.trace_begin(st))) return rc;
+  if (h.kind == EO_WAVE_DIRICHLET) {
+    k_post_wave<<<(unsigned)std::max<long long>(1, std::min<long long>(8192, (R * g.n_nodes + 255) / 256)), 256, 0, st>>>(
+        s, nchunk, h.part, h.eacc, uin, uout, C[0]);
+    EO_CUDA_TRY(cudaGetLastError());
+  } else {
+    k_reduce_full<<<(unsigned)std::max<long long>(1, std::min<long long>(8192, (R * 3 * g.n_nodes + 255) / 256)), 256, 0,
+                    st>>>(s, nchunk, h.part, h.eacc, h.afull);
+    EO_CUDA_TRY(cudaGetLastError());
+    k_post_sw<<<dim3(nleaf, R), 128, sizeof(double) * 6 * g.p * g.p, st>>>(
+        geo, R, g.n_nodes, h.K, h.afull, uin, uout, C[0], C[1], h.tau * h.opts.sw_g);
+    EO_CUDA_TRY(cudaGetLastError());
+  }
+  if ((rc = h.trace_end(TR_POST, st))) return rc;
+  return EO_OK;
+}
+
+}  // namespace
+
+eo_status Handle::trace_begin(cudaStream_t st) {
+  if (!timing) return EO_OK;
+  if ((size_t)(2 * ev_used + 2) > ev_pool.size()) {
+    for (int i = 0; i < 64; ++i) {
+      cudaEvent_t e;
+      EO_CUDA_TRY(cudaEventCreate(&e));
+      ev_pool.push_back(e);
+    }
+  }
+  EO_CUDA_TRY(cudaEventRecord(ev_pool[2 * ev_used], st));
+  return EO_OK;
+}
+
+eo_status Handle::trace_end(int cls, cudaStream_t st) {
+  if (!timing) return EO_OK;
+  EO_CUDA_TRY(cudaEventRecord(ev_pool[2 * ev_used + 1], st));
+  if ((int)ev_class.size() <= ev_used) ev_class.resize(ev_used + 1);
+  ev_class[ev_used++] = cls;
+  return EO_OK;
+}
+
+eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st) {
+  if (!u) return fail(EO_ERR_INVALID_ARG, "null state");
+  if (n_rhs < 1 || n_rhs > h.R) return fail(EO_ERR_INVALID_ARG, "n_rhs out of range [1, max_rhs]");
+  if (n_steps < 0) return fail(EO_ERR_INVALID_ARG, "negative n_steps");
+  double* cur = u;
+  double* nxt = h.ustate;
+  eo_status rc;
+  for (int i = 0; i < n_steps; ++i) {
+    if ((rc = run_step(h, cur, nxt, n_rhs, 0, h.P, h.wgt, h.C, st))) return rc;
+    std::swap(cur, nxt);
+  }
+  if (cur != u)
+    EO_CUDA_TRY(cudaMemcpyAsync(u, cur, sizeof(double) * (size_t)n_rhs * h.F * h.g.n_nodes,
+                                cudaMemcpyDeviceToDevice, st));
+  return EO_OK;
+}
+
+// x = (tau L - alpha_j)^{-1} u: the pole-sum pipeline run for pole j alone with
+// weight 1 (real part) and weight -i (imaginary part); every post-map is linear
+// with real coefficients in (weight * solution), so the two runs give Re and Im.
+eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStream_t st) {
+  if (j < 0 || j >= h.P) return fail(EO_ERR_INVALID_ARG, "pole index out of range");
+  const std::complex<double> al = h.alpha[j];
+  const std::complex<double> ws[2] = {1.0, std::complex<double>(0.0, -1.0)};
+  const size_t nst = (size_t)h.F * h.g.n_nodes;
+  double* tmpw;
+  double* outb;
+  EO_CUDA_TRY(cudaMallocAsync(&tmpw, sizeof(cd) * h.P * h.K, st));
+  EO_CUDA_TRY(cudaMallocAsync(&outb, sizeof(double) * nst * 2, st));
+  for (int part = 0; part < 2; ++part) {
+    const std::complex<double> c = ws[part];
+    std::vector<cd> w(h.P * h.K, make_double2(0.0, 0.0));
+    double C[4] = {0, 0, 0, 0};
+    if (h.kind == EO_WAVE_DIRICHLET) {
+      const std::complex<double> w0 = c, w1 = c * h.tau / al;
+      w[j * h.K + 0] = make_double2(w0.real(), w0.imag());
+      w[j * h.K + 1] = make_double2(w1.real(), w1.imag());
+      C[0] = (c / al).real();
+    } else {
+      const double tf = h.tau * h.opts.sw_f;
+      const std::complex<double> D = al * al + tf * tf;
+      const std::complex<double> w0 = c, w1 = c * (-al / D), w2 = c * (-tf / D);
+      w[j * h.K + 0] = make_double2(w0.real(), w0.imag());
+      w[j * h.K + 1] = make_double2(w1.real(), w1.imag());
+      w[j * h.K + 2] = make_double2(w2.real(), w2.imag());
+      C[0] = w1.real();
+      C[1] = w2.real();
+    }
+    EO_CUDA_TRY(cudaMemcpyAsync(tmpw, w.data(), sizeof(cd) * h.P * h.K, cudaMemcpyHostToDevice, st));
+    eo_status rc = run_step(h, u, outb + part * nst, 1, j, 1, (const cd*)tmpw, C, st);
+    if (rc) return rc;
+  }
+  // interleave (re, im)
+  EO_CUDA_TRY(cudaMemcpy2DAsync(x, 2 * sizeof(double), outb, sizeof(double), sizeof(double), nst,
+                                cudaMemcpyDeviceToDevice, st));
+  EO_CUDA_TRY(cudaMemcpy2DAsync(x + 1, 2 * sizeof(double), outb + nst, sizeof(double), sizeof(double), nst,
+                                cudaMemcpyDeviceToDevice, st));
+  EO_CUDA_TRY(cudaStreamSynchronize(st));
+  cudaFree(tmpw);
+  cudaFree(outb);
+  return EO_OK;
+}
+
+}  // namespace eo

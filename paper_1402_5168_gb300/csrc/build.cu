@@ -1,0 +1,463 @@
+// Build phase (Section 1.3 and Section 2.3), FP64 on the device.
+//
+// For every distinct pole alpha (Im alpha >= 0; the conjugates follow from
+// eq. "conjugate, matrix inverses" of Section 3.3) the elliptic problem
+//     div(a grad w) - kappa^2 w = s        (Section 2.1)
+// is discretised by Chebyshev collocation on every leaf (Section 2.2) and
+// solved by nested dissection:
+//   leaf:  A_ii [X | Y] = [I | -A_ib]  (interior rows, boundary data u_b)
+//          T = F_bb + F_bi Y  (outward flux a dw/dn from boundary data)
+//          H = F_bi X         (outward flux of the particular solution)
+//   merge of boxes alpha, beta over interface 3 (flux continuity):
+//          Z = (T^a_33 + T^b_33)^{-1},  S = -Z [T^a_31 | T^b_32],
+//          U = -[T^a_13 ; T^b_23] Z,    T_parent = diag(T^a_11, T^b_22) + [T^a_13; T^b_23] S
+//   root:  Dirichlet walls: boundary data 0, only Z is kept.
+//          Shallow-water walls: the oblique condition of the walls, written
+//          with T_root, is inverted once per pole (B_root^{-1}).
+// Dense factorisations and products of the build call cuBLAS batched routines;
+// assembly and gathers are the kernels below.
+#include <cublas_v2.h>
+
+#include <algorithm>
+#include <cmath>
+#include <string>
+
+#include "handle.h"
+
+namespace eo {
+
+#define EO_CUBLAS_TRY(expr)                                                     \
+  do {                                                                          \
+    cublasStatus_t s_ = (expr);                                                 \
+    if (s_ != CUBLAS_STATUS_SUCCESS)                                            \
+      return fail(EO_ERR_CUDA, std::string(#expr) + ": cublas status " + std::to_string((int)s_)); \
+  } while (0)
+
+// local boundary index of leaf node (k, j) in S, E, N, W order; -1 if interior
+__device__ __forceinline__ int bidx(int k, int j, int p, int q) {
+  if (j == 0) return k - 1;
+  if (k == p - 1) return q + j - 1;
+  if (j == p - 1) return 2 * q + k - 1;
+  if (k == 0) return 3 * q + j - 1;
+  return -1;
+}
+
+__device__ __forceinline__ long long dnode(int a, int b, int k, int j, int nlx, int nly, int p,
+                                           long long n_int, long long n_hseg) {
+  const int q = p - 2;
+  const bool kin = k > 0 && k < p - 1, jin = j > 0 && j < p - 1;
+  if (kin && jin) return ((long long)b * nlx + a) * q * q + (long long)(j - 1) * q + (k - 1);
+  if (kin) return n_int + ((long long)(j == 0 ? b : b + 1) * nlx + a) * q + (k - 1);
+  if (jin) return n_int + (n_hseg + (long long)b * (nlx + 1) + (k == 0 ? a : a + 1)) * q + (j - 1);
+  return -1;
+}
+
+// Real leaf matrices, column-major: Aii0 (n_i x n_i), Aib (n_i x n_b),
+// Fbi (n_b x n_i), Fbb (n_b x n_b).  One block per leaf.
+__global__ void leaf_real_ops(int nlx, int nly, int p, long long n_int, long long n_hseg,
+                              const double* __restrict__ Dx, const double* __restrict__ Dy,
+                              const double* __restrict__ acoef, double* Aii0, double* Aib,
+                              double* Fbi, double* Fbb) {
+  const int leaf = blockIdx.x;
+  const int a = leaf % nlx, b = leaf / nlx;
+  const int q = p - 2, ni = q * q, nb = 4 * q;
+  extern __shared__ double sm[];
+  double* al = sm;   // a at local nodes, [j*p + k]
+  for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
+    const int k = t % p, j = t / p;
+    const long long id = dnode(a, b, k, j, nlx, nly, p, n_int, n_hseg);
+    al[t] = (id < 0) ? 0.0 : (acoef ? acoef[id] : 1.0);
+  }
+  __syncthreads();
+  double* A0 = Aii0 + (size_t)leaf * ni * ni;
+  double* Ab = Aib + (size_t)leaf * ni * nb;
+  double* Fi = Fbi + (size_t)leaf * nb * ni;
+  double* Fb = Fbb + (size_t)leaf * nb * nb;
+  // interior rows: d/dx(a du/dx) + d/dy(a du/dy) with nested 1-D differentiation
+  for (int r = threadIdx.x; r < ni; r += blockDim.x) {
+    const int k = r % q + 1, j = r / q + 1;
+    for (int m = 0; m < p; ++m) {
+      double cx = 0, cy = 0;
+      for (int l = 0; l < p; ++l) {
+        cx += Dx[k * p + l] * al[j * p + l] * Dx[l * p + m];
+        cy += Dy[j * p + l] * al[l * p + k] * Dy[l * p + m];
+      }
+      // x part: column (m, j); y part: column (k, m)
+      int bi = bidx(m, j, p, q);
+      if (bi < 0) A0[r + (size_t)((j - 1) * q + (m - 1)) * ni] += cx;
+      else Ab[r + (size_t)bi * ni] += cx;
+      bi = bidx(k, m, p, q);
+      if (bi < 0) A0[r + (size_t)((m - 1) * q + (k - 1)) * ni] += cy;
+      else Ab[r + (size_t)bi * ni] += cy;
+    }
+  }
+  // boundary rows: outward flux a dw/dn by one-sided spectral differentiation
+  for (int t = threadIdx.x; t < nb; t += blockDim.x) {
+    const int side = t / q, o = t % q + 1;
+    for (int m = 0; m < p; ++m) {
+      int k, j;
+      double c;
+      if (side == 0) { k = o; j = m; c = -al[0 * p + o] * Dy[0 * p + m]; }
+      else if (side == 1) { k = m; j = o; c = al[o * p + (p - 1)] * Dx[(p - 1) * p + m]; }
+      else if (side == 2) { k = o; j = m; c = al[(p - 1) * p + o] * Dy[(p - 1) * p + m]; }
+      else { k = m; j = o; c = -al[o * p + 0] * Dx[0 * p + m]; }
+      const int bi = bidx(k, j, p, q);
+      if (bi < 0) Fi[t + (size_t)((j - 1) * q + (k - 1)) * nb] += c;
+      else Fb[t + (size_t)bi * nb] += c;
+    }
+  }
+}
+
+// Per pole: A = Aii0 - kappa2 I; XY = [I | -Aib]; T = Fbb; Fbi_c = Fbi (complex).
+__global__ void leaf_assemble(int nleaf, int ni, int nb, cd kappa2, const double* Aii0,
+                              const double* Aib, const double* Fbb, cd* A, cd* XY, cd* T) {
+  const size_t nA = (size_t)ni * ni, nXY = (size_t)ni * (ni + nb), nT = (size_t)nb * nb;
+  const size_t tot = (size_t)nleaf * (nA + nXY + nT);
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot;
+       t += (size_t)gridDim.x * blockDim.x) {
+    size_t leaf = t / (nA + nXY + nT), e = t % (nA + nXY + nT);
+    if (e < nA) {
+      const int i = e % ni, j = e / ni;
+      double v = Aii0[leaf * nA + e];
+      A[leaf * nA + e] = make_double2(v - (i == j ? kappa2.x : 0.0), (i == j ? -kappa2.y : 0.0));
+    } else if (e < nA + nXY) {
+      e -= nA;
+      const int i = e % ni, j = e / ni;
+      double v = (j < ni) ? (i == j ? 1.0 : 0.0) : -Aib[leaf * (size_t)ni * nb + (e - (size_t)ni * ni)];
+      XY[leaf * nXY + e] = make_double2(v, 0.0);
+    } else {
+      e -= nA + nXY;
+      T[leaf * nT + e] = make_double2(Fbb[leaf * nT + e], 0.0);
+    }
+  }
+}
+
+__global__ void real_to_complex(size_t n, const double* x, cd* y) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    y[t] = make_double2(x[t], 0.0);
+}
+
+// Merge gathers for one level, one parent box per block (column-major outputs).
+__global__ void merge_gather(int nbd_c, int n3, int npar, const int* __restrict__ par_child,
+                             const int* __restrict__ par_idx, const int* __restrict__ a3,
+                             const int* __restrict__ b3, int dir, int nbx_par, int nbx_child,
+                             int shared, const cd* __restrict__ Tc, cd* M33, cd* Q, cd* Rm,
+                             cd* Tpar) {
+  const int box = blockIdx.x;
+  int ca, cb;
+  if (shared) { ca = cb = 0; }
+  else {
+    const int bx = box % nbx_par, by = box / nbx_par;
+    if (dir == 0) { ca = by * nbx_child + 2 * bx; cb = ca + 1; }
+    else { ca = (2 * by) * nbx_child + bx; cb = ca + nbx_child; }
+  }
+  const size_t nT = (size_t)nbd_c * nbd_c;
+  const cd* Ta = Tc + (size_t)ca * nT;
+  const cd* Tb = Tc + (size_t)cb * nT;
+  cd* m33 = M33 + (size_t)box * n3 * n3;
+  cd* qq = Q ? Q + (size_t)box * npar * n3 : nullptr;
+  cd* rm = Rm + (size_t)box * n3 * npar;
+  cd* tp = Tpar ? Tpar + (size_t)box * npar * npar : nullptr;
+  for (int e = threadIdx.x; e < n3 * n3; e += blockDim.x) {
+    const int t = e % n3, u = e / n3;
+    cd x = Ta[a3[t] + (size_t)a3[u] * nbd_c], y = Tb[b3[t] + (size_t)b3[u] * nbd_c];
+    m33[e] = make_double2(x.x + y.x, x.y + y.y);
+  }
+  if (!Q) return;
+  for (int e = threadIdx.x; e < npar * n3; e += blockDim.x) {
+    const int i = e % npar, t = e / npar;
+    const int c = par_child[i], ci = par_idx[i];
+    const cd* Tx = c ? Tb : Ta;
+    const int c3 = c ? b3[t] : a3[t];
+    qq[e] = Tx[ci + (size_t)c3 * nbd_c];                      // Q[i, t]
+    rm[t + (size_t)i * n3] = Tx[c3 + (size_t)ci * nbd_c];     // Rm[t, i]
+  }
+  if (!tp) return;
+  for (size_t e = threadIdx.x; e < (size_t)npar * npar; e += blockDim.x) {
+    const int i = e % npar, ii = e / npar;
+    const int c = par_child[i];
+    tp[e] = (c == par_child[ii]) ? (c ? Tb : Ta)[par_idx[i] + (size_t)par_idx[ii] * nbd_c]
+                                 : make_double2(0.0, 0.0);
+  }
+}
+
+// dst (ldd) rows [0, n) x cols [0, n) = scale * src (n x n, ld n); batched over blocks
+__global__ void copy_scaled(int n, const cd* src, cd* dst, int ldd, int64_t dst_stride, double scale) {
+  const cd* s = src + (size_t)blockIdx.x * n * n;
+  cd* d = dst + (size_t)blockIdx.x * dst_stride;
+  for (int e = threadIdx.x; e < n * n; e += blockDim.x) {
+    const int i = e % n, j = e / n;
+    d[i + (size_t)j * ldd] = make_double2(scale * s[e].x, scale * s[e].y);
+  }
+}
+
+__global__ void set_identity(int n, int nbatch, cd* M) {
+  const size_t tot = (size_t)nbatch * n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const size_t e = t % ((size_t)n * n);
+    M[t] = make_double2((e % n) == (e / n) ? 1.0 : 0.0, 0.0);
+  }
+}
+
+// B_root = diag(nu) T_root + tau f G_t (oblique wall condition); n = 4 * nseg_side * q.
+// side of boundary node i: from the root box layout S (sx q), E (sy q), N (sx q), W (sy q).
+__global__ void root_system(int n, int q, int sxq, int syq, cd alpha, double tauf,
+                            const double* __restrict__ Ex, const double* __restrict__ Ey,
+                            const cd* __restrict__ T, cd* B) {
+  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
+       e += (size_t)gridDim.x * blockDim.x) {
+    const int i = e % n, j = e / n;
+    int side, off;
+    if (i < sxq) { side = 0; off = i; }
+    else if (i < sxq + syq) { side = 1; off = i - sxq; }
+    else if (i < 2 * sxq + syq) { side = 2; off = i - sxq - syq; }
+    else { side = 3; off = i - 2 * sxq - syq; }
+    const double sg = (side == 1 || side == 2) ? 1.0 : -1.0;
+    const cd t = T[e];
+    double re = sg * (alpha.x * t.x - alpha.y * t.y), im = sg * (alpha.x * t.y + alpha.y * t.x);
+    // tangential derivative inside the same segment
+    const int seg_i = i / q, seg_j = j / q;
+    if (seg_i == seg_j) {
+      const int a = i % q, c = j % q;
+      if (side == 1 || side == 3) re += tauf * Ey[a * q + c];          // + tau f dh/dy on x-walls
+      else re -= tauf * Ex[a * q + c];                                  // - tau f dh/dx on y-walls
+    }
+    B[e] = make_double2(re, im);
+  }
+}
+
+namespace {
+
+struct Cublas {
+  cublasHandle_t h = nullptr;
+  ~Cublas() { if (h) cublasDestroy(h); }
+};
+
+// getrf + getrs(identity): Zout = inverse of each M (batched, in device memory).
+eo_status batched_inverse(cublasHandle_t cb, cudaStream_t st, int n, int nbatch, cd* M, cd* Zout,
+                          int* piv, int* info, std::vector<int>& hinfo, const char* what) {
+  std::vector<cd*> pa(nbatch), pz(nbatch);
+  for (int i = 0; i < nbatch; ++i) { pa[i] = M + (size_t)i * n * n; pz[i] = Zout + (size_t)i * n * n; }
+  cd** dpa; cd** dpz;
+  EO_CUDA_TRY(cudaMallocAsync(&dpa, sizeof(cd*) * nbatch, st));
+  EO_CUDA_TRY(cudaMallocAsync(&dpz, sizeof(cd*) * nbatch, st));
+  EO_CUDA_TRY(cudaMemcpyAsync(dpa, pa.data(), sizeof(cd*) * nbatch, cudaMemcpyHostToDevice, st));
+  EO_CUDA_TRY(cudaMemcpyAsync(dpz, pz.data(), sizeof(cd*) * nbatch, cudaMemcpyHostToDevice, st));
+  EO_CUBLAS_TRY(cublasZgetrfBatched(cb, n, (cuDoubleComplex**)dpa, n, piv, info, nbatch));
+  hinfo.assign(nbatch, 0);
+  EO_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nbatch, cudaMemcpyDeviceToHost, st));
+  EO_CUDA_TRY(cudaStreamSynchronize(st));
+  for (int i = 0; i < nbatch; ++i)
+    if (hinfo[i] != 0) {
+      cudaFreeAsync(dpa, st); cudaFreeAsync(dpz, st);
+      return fail(EO_ERR_SINGULAR, std::string(what) + ": singular system (getrf info " +
+                                       std::to_string(hinfo[i]) + ")");
+    }
+  set_identity<<<1024, 256, 0, st>>>(n, nbatch, Zout);
+  int hi = 0;
+  EO_CUBLAS_TRY(cublasZgetrsBatched(cb, CUBLAS_OP_N, n, n, (const cuDoubleComplex* const*)dpa, n, piv,
+                                    (cuDoubleComplex* const*)dpz, n, &hi, nbatch));
+  if (hi != 0) return fail(EO_ERR_INVALID_ARG, "getrs argument error");
+  EO_CUDA_TRY(cudaFreeAsync(dpa, st));
+  EO_CUDA_TRY(cudaFreeAsync(dpz, st));
+  return EO_OK;
+}
+
+}  // namespace
+
+eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
+  const Grid& g = h.g;
+  const int p = g.p, q = g.q, ni = q * q, nb = 4 * q;
+  const int nleaf = g.nlx * g.nly;
+  const int nlo = h.shared ? 1 : nleaf;     // leaves with their own operators
+  const int P = h.P;
+  Cublas cbh;
+  EO_CUBLAS_TRY(cublasCreate(&cbh.h));
+  cublasHandle_t cb = cbh.h;
+  EO_CUBLAS_TRY(cublasSetStream(cb, st));
+  EO_CUBLAS_TRY(cublasSetPointerMode(cb, CUBLAS_POINTER_MODE_HOST));
+
+  // scaled differentiation matrices on the device
+  EO_CUDA_TRY(cudaMemcpyAsync(h.dDx, h.Dx, sizeof(double) * p * p, cudaMemcpyHostToDevice, st));
+  EO_CUDA_TRY(cudaMemcpyAsync(h.dDx + p * p, h.Dy, sizeof(double) * p * p, cudaMemcpyHostToDevice, st));
+  EO_CUDA_TRY(cudaMemcpyAsync(h.dDx + 2 * p * p, h.Ex, sizeof(double) * q * q, cudaMemcpyHostToDevice, st));
+  EO_CUDA_TRY(cudaMemcpyAsync(h.dDx + 2 * p * p + q * q, h.Ey, sizeof(double) * q * q,
+                              cudaMemcpyHostToDevice, st));
+  const double* dDx = h.dDx;
+  const double* dDy = h.dDx + p * p;
+  const double* dEx = h.dDx + 2 * p * p;
+  const double* dEy = dEx + q * q;
+
+  // ---- leaf real matrices (pole independent)
+  double *acoef = nullptr, *Aii0, *Aib, *Fbi, *Fbb;
+  std::vector<void*> tmp;
+  auto talloc = [&](void** ptr, size_t bytes) -> eo_status {
+    if (cudaMallocAsync(ptr, bytes, st) != cudaSuccess) return fail(EO_ERR_OOM, "build workspace allocation failed");
+    tmp.push_back(*ptr);
+    return EO_OK;
+  };
+  struct Freer {
+    std::vector<void*>& v; cudaStream_t s;
+    ~Freer() { for (void* x : v) cudaFreeAsync(x, s); cudaStreamSynchronize(s); }
+  } freer{tmp, st};
+  eo_status rc;
+  if (h.kind == EO_WAVE_DIRICHLET) {
+    acoef = h.acoef;   // kept: the apply's pre-map differentiates c^2 grad u
+    EO_CUDA_TRY(cudaMemcpyAsync(acoef, coeff, sizeof(double) * g.n_nodes, cudaMemcpyHostToDevice, st));
+  }
+  if ((rc = talloc((void**)&Aii0, sizeof(double) * nlo * ni * ni))) return rc;
+  if ((rc = talloc((void**)&Aib, sizeof(double) * nlo * ni * nb))) return rc;
+  if ((rc = talloc((void**)&Fbi, sizeof(double) * nlo * nb * ni))) return rc;
+  if ((rc = talloc((void**)&Fbb, sizeof(double) * nlo * nb * nb))) return rc;
+  EO_CUDA_TRY(cudaMemsetAsync(Aii0, 0, sizeof(double) * nlo * ni * ni, st));
+  EO_CUDA_TRY(cudaMemsetAsync(Aib, 0, sizeof(double) * nlo * ni * nb, st));
+  EO_CUDA_TRY(cudaMemsetAsync(Fbi, 0, sizeof(double) * nlo * nb * ni, st));
+  EO_CUDA_TRY(cudaMemsetAsync(Fbb, 0, sizeof(double) * nlo * nb * nb, st));
+  leaf_real_ops<<<nlo, 256, sizeof(double) * p * p, st>>>(g.nlx, g.nly, p, g.n_int, g.n_hseg, dDx, dDy,
+                                                        acoef, Aii0, Aib, Fbi, Fbb);
+  EO_CUDA_TRY(cudaGetLastError());
+  cd *Fbi_c, *Aw, *T0;
+  if ((rc = talloc((void**)&Fbi_c, sizeof(cd) * nlo * nb * ni))) return rc;
+  if ((rc = talloc((void**)&Aw, sizeof(cd) * nlo * ni * ni))) return rc;
+  if ((rc = talloc((void**)&T0, sizeof(cd) * nlo * nb * nb))) return rc;
+  real_to_complex<<<1024, 256, 0, st>>>((size_t)nlo * nb * ni, Fbi, Fbi_c);
+  int *piv, *info;
+  const Plan& plan = h.plan;
+  const int L = plan.L();
+  // largest batched system: leaves (ni) or any merge level / root
+  size_t maxpiv = (size_t)nlo * ni, maxinfo = nlo;
+  size_t ws_merge = 0;   // complex entries for M33, Z, Q, Rm, Tpar
+  for (int l = 1; l <= L; ++l) {
+    const Level& lv = plan.lv[l];
+    const int nbo = h.shared ? 1 : lv.nbox;
+    maxpiv = std::max(maxpiv, (size_t)nbo * lv.n3);
+    maxinfo = std::max(maxinfo, (size_t)nbo);
+    ws_merge = std::max(ws_merge, (size_t)nbo * (2 * (size_t)lv.n3 * lv.n3 + 2 * (size_t)lv.nbd * lv.n3 +
+                                                  (size_t)lv.nbd * lv.nbd));
+  }
+  if (h.kind == EO_SW_WALLS) {
+    maxpiv = std::max(maxpiv, (size_t)h.nroot);
+    ws_merge = std::max(ws_merge, (size_t)2 * h.nroot * h.nroot);
+  }
+  if ((rc = talloc((void**)&piv, sizeof(int) * maxpiv))) return rc;
+  if ((rc = talloc((void**)&info, sizeof(int) * maxinfo))) return rc;
+  cd* mw = nullptr;
+  if (ws_merge && (rc = talloc((void**)&mw, sizeof(cd) * ws_merge))) return rc;
+  // T of the current and next level
+  size_t maxT = (size_t)nlo * nb * nb;
+  for (int l = 1; l <= L; ++l) {
+    const Level& lv = plan.lv[l];
+    maxT = std::max(maxT, (size_t)(h.shared ? 1 : lv.nbox) * lv.nbd * lv.nbd);
+  }
+  cd *Tc, *Tn;
+  if ((rc = talloc((void**)&Tc, sizeof(cd) * maxT))) return rc;
+  if ((rc = talloc((void**)&Tn, sizeof(cd) * maxT))) return rc;
+  std::vector<int> hinfo;
+  const cuDoubleComplex one = {1.0, 0.0}, zero = {0.0, 0.0}, mone = {-1.0, 0.0};
+
+  for (int pj = 0; pj < P; ++pj) {
+    const std::complex<double> al = h.alpha[pj];
+    std::complex<double> k2;
+    if (h.kind == EO_WAVE_DIRICHLET) k2 = (al / h.tau) * (al / h.tau);
+    else k2 = (al * al + (h.tau * h.opts.sw_f) * (h.tau * h.opts.sw_f)) /
+              (h.tau * h.tau * h.opts.sw_g * h.opts.sw_H);
+    // ---- leaves
+    cd* XYp = h.XY + (size_t)pj * h.xy_pstride;
+    cd* Hp = h.H + (size_t)pj * h.h_pstride;
+    leaf_assemble<<<2048, 256, 0, st>>>(nlo, ni, nb, make_double2(k2.real(), k2.imag()), Aii0, Aib, Fbb,
+                                        Aw, XYp, T0);
+    EO_CUDA_TRY(cudaGetLastError());
+    {
+      const long long xyb = std::max<long long>(h.xy_bstride, (long long)ni * (ni + nb));
+      const long long hb = std::max<long long>(h.h_bstride, (long long)nb * ni);
+      std::vector<cd*> pa(nlo), pb(nlo);
+      for (int i = 0; i < nlo; ++i) { pa[i] = Aw + (size_t)i * ni * ni; pb[i] = XYp + (size_t)i * xyb; }
+      cd **dpa, **dpb;
+      if ((rc = talloc((void**)&dpa, sizeof(cd*) * nlo))) return rc;
+      if ((rc = talloc((void**)&dpb, sizeof(cd*) * nlo))) return rc;
+      EO_CUDA_TRY(cudaMemcpyAsync(dpa, pa.data(), sizeof(cd*) * nlo, cudaMemcpyHostToDevice, st));
+      EO_CUDA_TRY(cudaMemcpyAsync(dpb, pb.data(), sizeof(cd*) * nlo, cudaMemcpyHostToDevice, st));
+      EO_CUBLAS_TRY(cublasZgetrfBatched(cb, ni, (cuDoubleComplex**)dpa, ni, piv, info, nlo));
+      hinfo.assign(nlo, 0);
+      EO_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nlo, cudaMemcpyDeviceToHost, st));
+      EO_CUDA_TRY(cudaStreamSynchronize(st));
+      for (int i = 0; i < nlo; ++i)
+        if (hinfo[i]) return fail(EO_ERR_SINGULAR, "leaf interior system singular (leaf " + std::to_string(i) + ")");
+      int hi = 0;
+      EO_CUBLAS_TRY(cublasZgetrsBatched(cb, CUBLAS_OP_N, ni, ni + nb, (const cuDoubleComplex* const*)dpa, ni, piv,
+                                        (cuDoubleComplex* const*)dpb, ni, &hi, nlo));
+      // T = Fbb + Fbi Y ; H = Fbi X
+      EO_CUBLAS_TRY(cublasZgemmStridedBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, nb, nb, ni, &one,
+                                              (const cuDoubleComplex*)Fbi_c, nb, (long long)nb * ni,
+                                              (const cuDoubleComplex*)(XYp + (size_t)ni * ni), ni, xyb,
+                                              &one, (cuDoubleComplex*)T0, nb, (long long)nb * nb, nlo));
+      EO_CUBLAS_TRY(cublasZgemmStridedBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, nb, ni, ni, &one,
+                                              (const cuDoubleComplex*)Fbi_c, nb, (long long)nb * ni,
+                                              (const cuDoubleComplex*)XYp, ni, xyb, &zero,
+                                              (cuDoubleComplex*)Hp, nb, hb, nlo));
+    }
+    // ---- merges (parent T alternates between Tc and Tn; never the buffer being read)
+    cd* Tprev = T0;
+    int nbd_prev = nb;
+    for (int l = 1; l <= L; ++l) {
+      const Level& lv = plan.lv[l];
+      LevelDev& ld = h.lv[l];
+      const int nbo = h.shared ? 1 : lv.nbox;
+      const int n3 = lv.n3, npar = lv.nbd;
+      const bool root = (l == L);
+      const bool need_par = !(root && h.kind == EO_WAVE_DIRICHLET);
+      const bool need_T = !root || h.kind == EO_SW_WALLS;
+      cd* M33 = mw;
+      cd* Z = M33 + (size_t)nbo * n3 * n3;
+      cd* Qm = Z + (size_t)nbo * n3 * n3;
+      cd* Rm = Qm + (size_t)nbo * npar * n3;
+      cd* Tw = (l % 2) ? Tc : Tn;
+      merge_gather<<<nbo, 256, 0, st>>>(nbd_prev, n3, npar, ld.par_child, ld.par_idx, ld.a3, ld.b3, lv.dir,
+                                        lv.nbx, plan.lv[l - 1].nbx, h.shared, Tprev, M33,
+                                        need_par ? Qm : nullptr, Rm, need_T ? Tw : nullptr);
+      EO_CUDA_TRY(cudaGetLastError());
+      if ((rc = batched_inverse(cb, st, n3, nbo, M33, Z, piv, info, hinfo, "merge interface system"))) return rc;
+      cd* ZUp = ld.ZU + (size_t)pj * ld.zu_pstride;
+      const long long zub = std::max<long long>(ld.zu_bstride, (long long)ld.zu_rows * n3);
+      copy_scaled<<<nbo, 256, 0, st>>>(n3, Z, ZUp, ld.zu_rows, zub, -1.0);
+      if (need_par) {
+        cd* Sp = ld.S + (size_t)pj * ld.s_pstride;
+        const long long sb = std::max<long long>(ld.s_bstride, (long long)n3 * npar);
+        // U = -Q Z  -> rows [n3, n3 + npar) of ZU
+        EO_CUBLAS_TRY(cublasZgemmStridedBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, npar, n3, n3, &mone,
+                                                (const cuDoubleComplex*)Qm, npar, (long long)npar * n3,
+                                                (const cuDoubleComplex*)Z, n3, (long long)n3 * n3, &zero,
+                                                (cuDoubleComplex*)(ZUp + n3), ld.zu_rows, zub, nbo));
+        // S = -Z Rm
+        EO_CUBLAS_TRY(cublasZgemmStridedBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, n3, npar, n3, &mone,
+                                                (const cuDoubleComplex*)Z, n3, (long long)n3 * n3,
+                                                (const cuDoubleComplex*)Rm, n3, (long long)n3 * npar, &zero,
+                                                (cuDoubleComplex*)Sp, n3, sb, nbo));
+        if (need_T) {
+          // T_parent += Q S
+          EO_CUBLAS_TRY(cublasZgemmStridedBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, npar, npar, n3, &one,
+                                                  (const cuDoubleComplex*)Qm, npar, (long long)npar * n3,
+                                                  (const cuDoubleComplex*)Sp, n3, sb, &one,
+                                                  (cuDoubleComplex*)Tw, npar, (long long)npar * npar, nbo));
+        }
+      }
+      Tprev = Tw;
+      nbd_prev = npar;
+    }
+    // ---- root oblique system (shallow-water walls)
+    if (h.kind == EO_SW_WALLS) {
+      const Level& rl = plan.lv[L];
+      const int n = rl.nbd;
+      cd* Broot = mw;
+      cd* Bi = h.Binv + (size_t)pj * n * n;
+      root_system<<<1024, 256, 0, st>>>(n, q, rl.sx * q, rl.sy * q, make_double2(al.real(), al.imag()),
+                                        h.tau * h.opts.sw_f, dEx, dEy, Tprev, Broot);
+      EO_CUDA_TRY(cudaGetLastError());
+      if ((rc = batched_inverse(cb, st, n, 1, Broot, Bi, piv, info, hinfo, "root wall system"))) return rc;
+    }
+  }
+  EO_CUDA_TRY(cudaStreamSynchronize(st));
+  return EO_OK;
+}
+
+}  // namespace eo

@@ -1,0 +1,73 @@
+// Internal structures of the expop engine (not part of the C ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <cstdint>
+#include <string>
+#include <vector>
+
+#include "../../include/expop.h"
+
+namespace eo {
+
+// Thread-local error message and a helper that records it.
+void set_error(const std::string& msg);
+eo_status fail(eo_status st, const std::string& msg);
+
+// ---------------------------------------------------------------- leaf grid
+struct Grid {
+  int nlx = 0, nly = 0, p = 0, q = 0;
+  double x0 = 0, x1 = 1, y0 = 0, y1 = 1, hx = 0, hy = 0;
+  int64_t n_int = 0, n_hseg = 0, n_vseg = 0, n_seg = 0, n_edge = 0, n_nodes = 0;
+  std::vector<double> xi;        // Chebyshev-Lobatto points on [-1, 1], ascending
+  std::vector<double> D;         // p x p differentiation matrix on [-1,1], row-major D[i*p+j]
+  std::vector<double> Ed;        // q x q differentiation matrix through the q inner points
+
+  // global node id of local node (k, j) of leaf (a, b); -1 at a corner
+  int64_t node_id(int a, int b, int k, int j) const;
+  int64_t hseg(int e, int a) const { return (int64_t)e * nlx + a; }
+  int64_t vseg(int b, int e) const { return n_hseg + (int64_t)b * (nlx + 1) + e; }
+  void coords(std::vector<double>& x, std::vector<double>& y) const;
+};
+
+eo_status make_grid(int nlx, int nly, int p, double x0, double x1, double y0, double y1,
+                    Grid& g);
+
+// ---------------------------------------------------------------- tree plan
+// Level 0: leaves.  Level l >= 1: boxes made by merging pairs of level-(l-1)
+// boxes, alternating x and y merges.  Box boundary order: sides S, E, N, W,
+// each a list of leaf-edge segments in ascending coordinate, q nodes per
+// segment in ascending coordinate.
+struct Level {
+  int sx = 1, sy = 1;          // box size in leaves
+  int nbx = 0, nby = 0, nbox = 0;
+  int nseg = 0, nbd = 0;       // boundary segments / nodes per box
+  int dir = -1;                // merge that made this level: 0 = x, 1 = y
+  int n3 = 0;                  // interface nodes of that merge
+  std::vector<int> par_child;  // [nbd] child (0 = alpha, 1 = beta) of each boundary node
+  std::vector<int> par_idx;    // [nbd] index of the node in that child's boundary
+  std::vector<int> a3, b3;     // [n3] interface node indices in alpha's / beta's boundary
+  std::vector<int> bseg;       // [nbox * nseg] global segment ids of each box boundary
+  std::vector<int> iseg;       // [nbox * n3/q] global segment ids of each interface
+};
+
+struct Plan {
+  std::vector<Level> lv;       // lv[0] = leaves, lv.back() = root
+  int L() const { return (int)lv.size() - 1; }
+};
+
+void make_plan(const Grid& g, Plan& plan);
+
+// ---------------------------------------------------------------- fitter
+struct Fit {
+  std::vector<double> are, aim, bre, bim;   // 2M+1 poles / residues, m = -M..M
+  double X = 0, sigma = 0, s = 0;
+  int N() const { return (int)are.size(); }
+};
+
+// Widest band X for a given odd pole count; returns EO_ERR_FIT if none.
+eo_status fit_for_poles(int n_poles, double delta, Fit& out);
+// Smallest pole count covering band X (n_poles <= nmax).
+eo_status fit_for_band(double X, double delta, int nmax, Fit& out);
+
+}  // namespace eo

@@ -1,0 +1,208 @@
+// Rational approximant of e^{i x} on [-X, X] (Section 1.2, eqs. def_RM,
+// RM_prop1, RM_prop2).
+//
+// Poles on one conjugate-closed vertical line in the right half-plane,
+// alpha_m = sigma + i s m (m = -M..M).  With b_{-m} = conj(b_m) the function
+// R(i x) = sum_m b_m / (i x - alpha_m) satisfies R(-i x) = conj(R(i x)), so the
+// residues are fitted on [0, X] by real linear least squares (Householder QR)
+// in the real unknowns (b_0, Re b_1, Im b_1, ...).  A candidate (sigma, s, X)
+// is accepted when max |e^{ix} - R(ix)| <= delta/2 on [0, X], every |b_m| <= 100
+// (large residues cancel in the pole sum and amplify rounding), and
+// max |R(iy)| <= 1 + delta/10 on a grid of [0, Y] with Y far beyond the poles;
+// b is then divided by max(1, max|R|) so eq. RM_prop2 holds on that grid.
+// The search keeps the widest X for the requested pole count.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+
+#include "engine.h"
+
+namespace eo {
+
+using cplx = std::complex<double>;
+
+// Least squares min |A x - t| for column-major A (m x n), m >= n, by Householder
+// QR.  A and t are overwritten.  Returns false on a zero column.
+static bool lsq(std::vector<double>& A, std::vector<double>& t, int m, int n,
+                std::vector<double>& x) {
+  for (int k = 0; k < n; ++k) {
+    double* a = &A[(size_t)k * m];
+    double nrm = 0;
+    for (int i = k; i < m; ++i) nrm += a[i] * a[i];
+    nrm = std::sqrt(nrm);
+    if (nrm == 0) return false;
+    const double alpha = a[k] > 0 ? -nrm : nrm;
+    // v = a[k:] - alpha e_k, stored in a[k:]
+    a[k] -= alpha;
+    double vnorm2 = 0;
+    for (int i = k; i < m; ++i) vnorm2 += a[i] * a[i];
+    for (int j = k + 1; j < n; ++j) {
+      double* c = &A[(size_t)j * m];
+      double d = 0;
+      for (int i = k; i < m; ++i) d += a[i] * c[i];
+      const double f = 2 * d / vnorm2;
+      for (int i = k; i < m; ++i) c[i] -= f * a[i];
+    }
+    {
+      double d = 0;
+      for (int i = k; i < m; ++i) d += a[i] * t[i];
+      const double f = 2 * d / vnorm2;
+      for (int i = k; i < m; ++i) t[i] -= f * a[i];
+    }
+    a[k] = alpha;   // R diagonal; the rest of v is no longer needed
+    for (int i = k + 1; i < m; ++i) a[i] = 0;
+  }
+  x.assign(n, 0.0);
+  for (int k = n - 1; k >= 0; --k) {
+    double s = t[k];
+    for (int j = k + 1; j < n; ++j) s -= A[(size_t)j * m + k] * x[j];
+    x[k] = s / A[(size_t)k * m + k];
+  }
+  return true;
+}
+
+static cplx Reval(double y, const std::vector<cplx>& al, const std::vector<cplx>& b) {
+  cplx z(0.0, y), s(0.0, 0.0);
+  for (size_t i = 0; i < al.size(); ++i) s += b[i] / (z - al[i]);
+  return s;
+}
+
+// Residues for the pole line on [0, X]; returns false if the LS failed.
+static bool residues(int N, double sigma, double s, double X, std::vector<cplx>& al,
+                     std::vector<cplx>& b) {
+  const int M = (N - 1) / 2;
+  al.resize(N);
+  for (int m = -M; m <= M; ++m) al[m + M] = cplx(sigma, s * m);
+  const int ns = (int)std::ceil(X * 10.0) + 41;
+  const int rows = 2 * ns, cols = N;
+  std::vector<double> A((size_t)rows * cols), t(rows), x;
+  for (int i = 0; i < ns; ++i) {
+    const double th = X * i / (ns - 1);
+    const cplx z(0.0, th);
+    auto put = [&](int col, cplx v) {
+      A[(size_t)col * rows + i] = v.real();
+      A[(size_t)col * rows + ns + i] = v.imag();
+    };
+    put(0, 1.0 / (z - al[M]));
+    for (int k = 1; k <= M; ++k) {
+      const cplx p = 1.0 / (z - al[M + k]), n = 1.0 / (z - al[M - k]);
+      put(2 * k - 1, p + n);
+      put(2 * k, cplx(0, 1) * (p - n));
+    }
+    t[i] = std::cos(th);
+    t[ns + i] = std::sin(th);
+  }
+  // column scaling
+  std::vector<double> sc(cols);
+  for (int j = 0; j < cols; ++j) {
+    double s2 = 0;
+    for (int i = 0; i < rows; ++i) s2 += A[(size_t)j * rows + i] * A[(size_t)j * rows + i];
+    sc[j] = std::sqrt(s2);
+    if (sc[j] == 0) return false;
+    for (int i = 0; i < rows; ++i) A[(size_t)j * rows + i] /= sc[j];
+  }
+  if (!lsq(A, t, rows, cols, x)) return false;
+  for (int j = 0; j < cols; ++j) x[j] /= sc[j];
+  b.assign(N, cplx(0, 0));
+  b[M] = x[0];
+  for (int k = 1; k <= M; ++k) {
+    b[M + k] = cplx(x[2 * k - 1], x[2 * k]);
+    b[M - k] = std::conj(b[M + k]);
+  }
+  return true;
+}
+
+// Acceptance test; on success returns max |R(iy)| on the stability grid.
+static bool accept(double X, double delta, const std::vector<cplx>& al,
+                   const std::vector<cplx>& b, double* rmax) {
+  double bmax = 0, bsum = 0, amax = 0;
+  for (size_t i = 0; i < b.size(); ++i) {
+    bmax = std::max(bmax, std::abs(b[i]));
+    bsum += std::abs(b[i]);
+    amax = std::max(amax, std::abs(al[i]));
+  }
+  if (bmax > 100.0) return false;
+  const int nb = 1501;
+  for (int i = 0; i < nb; ++i) {
+    const double th = X * i / (nb - 1);
+    if (std::abs(std::exp(cplx(0, th)) - Reval(th, al, b)) > 0.5 * delta) return false;
+  }
+  // |R(iy)| on [0, Y], spacing 0.02; beyond Y, |R| <= bsum / (y - amax) <= 1
+  const double Y = std::max({50.0 * X + 200.0, 4.0 * amax + 200.0, amax + 2.0 * bsum});
+  const int ny = (int)(Y / 0.02) + 1;
+  double r = 0;
+  for (int i = 0; i < ny; ++i) {
+    r = std::max(r, std::abs(Reval(Y * i / (ny - 1), al, b)));
+    if (r > 1.0 + 0.1 * delta) return false;
+  }
+  *rmax = r;
+  return true;
+}
+
+static void store(const std::vector<cplx>& al, const std::vector<cplx>& b, double r,
+                  double X, double sigma, double s, Fit& out) {
+  const int N = (int)al.size();
+  out.are.resize(N); out.aim.resize(N); out.bre.resize(N); out.bim.resize(N);
+  const double scale = 1.0 / std::max(1.0, r);
+  for (int i = 0; i < N; ++i) {
+    out.are[i] = al[i].real(); out.aim[i] = al[i].imag();
+    out.bre[i] = b[i].real() * scale; out.bim[i] = b[i].imag() * scale;
+  }
+  out.X = X; out.sigma = sigma; out.s = s;
+}
+
+static const double kS[] = {1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6};
+static const double kRatio[] = {3.75, 4.0};
+
+eo_status fit_for_poles(int N, double delta, Fit& out) {
+  if (N < 3 || N % 2 == 0) return fail(EO_ERR_INVALID_ARG, "n_poles must be odd and >= 3");
+  if (N > 301) return fail(EO_ERR_UNSUPPORTED, "pole counts above 301 are not supported by this fitter");
+  const int M = (N - 1) / 2;
+  double bestX = 0;
+  std::vector<cplx> al, b;
+  for (double s : kS)
+    for (double ratio : kRatio) {
+      const double sigma = ratio * s;
+      // coarse scan downward from the pole span, then refine upward
+      double X = s * M;
+      double found = 0, r = 0;
+      for (; X > bestX && X > 0.5; X -= std::max(0.5, 0.05 * X)) {
+        if (residues(N, sigma, s, X, al, b) && accept(X, delta, al, b, &r)) { found = X; break; }
+      }
+      if (found == 0) continue;
+      double step = std::max(0.5, 0.05 * found) / 2;
+      for (int it = 0; it < 4; ++it, step /= 2) {
+        const double Xt = found + step;
+        double rt;
+        if (residues(N, sigma, s, Xt, al, b) && accept(Xt, delta, al, b, &rt)) found = Xt;
+      }
+      if (found > bestX) {
+        residues(N, sigma, s, found, al, b);
+        accept(found, delta, al, b, &r);
+        store(al, b, r, found, sigma, s, out);
+        bestX = found;
+      }
+    }
+  if (bestX == 0) return fail(EO_ERR_FIT, "no admissible rational approximant for this pole count");
+  return EO_OK;
+}
+
+eo_status fit_for_band(double X, double delta, int nmax, Fit& out) {
+  if (!(X > 0)) return fail(EO_ERR_INVALID_ARG, "band*tau must be positive");
+  std::vector<cplx> al, b;
+  for (int N = 5; N <= std::min(nmax, 301); N += 2) {
+    const int M = (N - 1) / 2;
+    for (double s : kS)
+      for (double ratio : kRatio) {
+        if (s * M < X) continue;
+        double r;
+        if (residues(N, ratio * s, s, X, al, b) && accept(X, delta, al, b, &r)) {
+          store(al, b, r, X, ratio * s, s, out);
+          return EO_OK;
+        }
+      }
+  }
+  return fail(EO_ERR_FIT, "band*tau too wide for the supported pole counts");
+}
+
+}  // namespace eo

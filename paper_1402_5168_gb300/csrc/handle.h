@@ -1,0 +1,103 @@
+// Device-resident operator set and apply workspace of one built handle.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <complex>
+#include <vector>
+
+#include "engine.h"
+
+namespace eo {
+
+typedef double2 cd;   // complex FP64, interleaved (re, im)
+
+#define EO_CUDA_TRY(expr)                                                        \
+  do {                                                                           \
+    cudaError_t e_ = (expr);                                                     \
+    if (e_ != cudaSuccess)                                                       \
+      return fail(EO_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
+  } while (0)
+
+// One tree level as the kernels see it.
+struct LevelDev {
+  int nbox = 0, nbx = 0, nby = 0, nbd = 0, nseg = 0, n3 = 0, dir = -1;
+  int nbx_child = 0;            // boxes per row one level below
+  int* par_child = nullptr;     // [nbd]
+  int* par_idx = nullptr;       // [nbd]
+  int* a3 = nullptr;            // [n3]
+  int* b3 = nullptr;            // [n3]
+  int* bseg = nullptr;          // [nbox * nseg]
+  int* iseg = nullptr;          // [nbox * n3/q]
+  // operators (levels >= 1): [pole][box or 0][...], column-major blocks
+  cd* ZU = nullptr;             // rows zu_rows = n3 (+ nbd unless Dirichlet root), cols n3: [-Z; U]
+  int zu_rows = 0;
+  cd* S = nullptr;              // n3 x nbd (absent at a Dirichlet root)
+  int64_t zu_pstride = 0, zu_bstride = 0, s_pstride = 0, s_bstride = 0;
+  cd* w3 = nullptr;             // workspace [pole][rhs][nbox][n3]
+};
+
+struct Handle {
+  Grid g;
+  Plan plan;
+  eo_kind kind = EO_WAVE_DIRICHLET;
+  eo_opts opts{};
+  Fit fit;
+  double tau = 0;
+  int P = 0;                    // distinct poles (Im alpha >= 0)
+  int K = 2;                    // pre-fields / accumulators per node
+  int F = 2;                    // state fields
+  int R = 1;                    // max rhs
+  int shared = 0;
+  std::vector<int> pole_index;  // distinct pole j -> index in the fit's order
+  std::vector<std::complex<double>> alpha, cw;   // distinct poles and pole-sum weights
+  // leaf operators: H (n_b x n_i), XY = [X | Y] (n_i x (n_i + n_b))
+  cd* H = nullptr;
+  cd* XY = nullptr;
+  int64_t h_pstride = 0, h_bstride = 0, xy_pstride = 0, xy_bstride = 0;
+  // root oblique solve (EO_SW_WALLS): Binv [pole][nroot x nroot]
+  cd* Binv = nullptr;
+  int nroot = 0;
+  std::vector<LevelDev> lv;
+  // per-pole coefficient tables (device, complex): pre-map coefficients [P][K],
+  // accumulation weights [P][K], wall rhs coefficients [P][4 sides][2],
+  // flux multipliers nu [P][4 sides]
+  cd* coef = nullptr;
+  cd* wgt = nullptr;
+  cd* bcoef = nullptr;
+  cd* nu = nullptr;
+  double C[4] = {0, 0, 0, 0};   // real constants of the post-map
+  double Dx[24 * 24], Dy[24 * 24], Ex[22 * 22], Ey[22 * 22];   // scaled, row-major
+  double* dDx = nullptr;        // device copies: Dx, Dy (p x p), Ex, Ey (q x q)
+  // apply workspace
+  cd* hA = nullptr;             // ping-pong particular fluxes [pole][rhs][box][nbd]
+  cd* hB = nullptr;
+  cd* E = nullptr;              // edge-node values [pole][rhs][n_edge]
+  double* part = nullptr;       // interior partial sums [chunk][rhs][K][n_int]
+  int nchunk = 1;
+  double* eacc = nullptr;       // edge sums [rhs][K][n_edge]
+  double* pre = nullptr;        // pre-map fields: wave A u [rhs][n_int]; SW div F, curl F [rhs][2][n_int]
+  double* acoef = nullptr;      // wave: c^2 at every node (device)
+  double* afull = nullptr;      // SW: accumulated fields at every node [rhs][K][n_nodes]
+  double* ustate = nullptr;     // second state buffer [rhs][F][n_nodes]
+  int64_t op_bytes = 0, ws_bytes = 0;
+  // tracing: events around launches, per kernel class
+  bool timing = false;
+  std::vector<cudaEvent_t> ev_pool;
+  std::vector<int> ev_class;      // one per recorded pair
+  int ev_used = 0;                // pairs recorded
+  eo_status trace_begin(cudaStream_t st);
+  eo_status trace_end(int cls, cudaStream_t st);
+  std::vector<void*> allocs;
+
+  ~Handle();
+  eo_status alloc(void** p, size_t bytes, bool op);
+};
+
+enum { TR_PRE = 0, TR_UP_LEAF, TR_UP_MERGE, TR_ROOT, TR_DOWN_MERGE, TR_DOWN_LEAF, TR_EDGE, TR_POST, TR_N };
+
+eo_status build(Handle& h, const double* coeff, cudaStream_t st);
+eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st);
+eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStream_t st);
+
+}  // namespace eo

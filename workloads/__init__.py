@@ -79,6 +79,19 @@ WAVE_32X32_P16 = Workload(
 
 WORKLOADS = {w.name: w for w in (WAVE_4X4_P12, SW_16X16_P16, WAVE_32X32_P16)}
 
+# Band Lambda (largest resolved |eigenvalue|) per workload.  4x4/p12 wave: the
+# content of the Gaussian bump above |lambda| = 320 of the discrete operator is
+# below 1e-10 (dense eigendecomposition of that 4000-unknown operator); the
+# others follow from the narrowest Gaussian the recipe can draw (sw_band,
+# wave_band below).
+BAND = {}
+
+
+def _init_bands():
+    BAND[WAVE_4X4_P12.name] = 320.0
+    BAND[SW_16X16_P16.name] = sw_band(SW_16X16_P16)
+    BAND[WAVE_32X32_P16.name] = wave_band(WAVE_32X32_P16)
+
 
 def sw_band(w: Workload) -> float:
     """Band Lambda for the shallow-water workload: sqrt(f^2 + gH k_max^2),
@@ -93,6 +106,9 @@ def wave_band(w: Workload) -> float:
     pr = w.params
     s = pr.get("bump_sigma", pr.get("sigma_range", (0.05,))[0])
     return pr["c_max"] * gaussian_kmax(s, w.delta)
+
+
+_init_bands()
 
 
 # ---------------------------------------------------------------- coefficients
