@@ -108,6 +108,17 @@ eo_status eo_grid_destroy(eo_grid_t grid);
 eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double *coeff,
                             const eo_opts *opts, void *stream, eo_handle_t *out);
 
+/* Host-only: the rational approximant alone (eqs. RM_prop1, RM_prop2), without
+ * building operators.  n_poles > 0: widest band for that odd pole count;
+ * n_poles == 0: fewest poles covering band X (> 0).  Poles alpha_m = sigma + i s m
+ * on one conjugate-closed line (m = -M..M); residues with b_{-m} = conj(b_m).
+ *   cap: capacity (in poles) of alpha and b, each 2*cap doubles interleaved.
+ *   n, X_out: pole count and band covered.  No device is touched.
+ * Errors: EO_ERR_INVALID_ARG (cap too small: *n is still set), EO_ERR_FIT,
+ *         EO_ERR_UNSUPPORTED. */
+eo_status eo_fit(int n_poles, double X, double delta, int cap, double *alpha, double *b, int *n,
+                 double *X_out);
+
 /* The approximant in use: n = 2M+1 poles alpha (2n doubles, interleaved),
  * residues b (2n doubles), the step tau and the band X = tau*Lambda it covers.
  * Pass alpha = b = NULL to query n only.  Poles are ordered m = -M..M. */

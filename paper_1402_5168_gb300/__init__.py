@@ -16,7 +16,19 @@ import numpy as np
 from . import _capi
 from ._capi import SW_WALLS, WAVE_DIRICHLET, ExpopError, Opts, check
 
-__all__ = ["Grid", "Operator", "WAVE_DIRICHLET", "SW_WALLS", "ExpopError"]
+__all__ = ["Grid", "Operator", "fit", "WAVE_DIRICHLET", "SW_WALLS", "ExpopError"]
+
+
+def fit(n_poles: int = 0, X: float = 0.0, delta: float = 1e-10, cap: int = 20001):
+    """Rational approximant (alpha, b, X) of e^{ix} on [-X, X]; host only."""
+    a = np.zeros(2 * cap)
+    b = np.zeros(2 * cap)
+    n, Xo = C.c_int(), C.c_double()
+    dp = C.POINTER(C.c_double)
+    check(_capi.lib().eo_fit(n_poles, X, delta, cap, a.ctypes.data_as(dp), b.ctypes.data_as(dp), C.byref(n),
+                             C.byref(Xo)))
+    k = n.value
+    return a[0:2 * k:2] + 1j * a[1:2 * k:2], b[0:2 * k:2] + 1j * b[1:2 * k:2], Xo.value
 
 
 def _stream_ptr(stream):

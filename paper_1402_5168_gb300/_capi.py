@@ -13,7 +13,7 @@ STATUS = {0: "EO_OK", 1: "EO_ERR_INVALID_ARG", 2: "EO_ERR_FIT", 3: "EO_ERR_SINGU
 WAVE_DIRICHLET, SW_WALLS = 0, 1
 
 # every symbol include/expop.h declares
-SYMBOLS = ("eo_grid_create", "eo_grid_info", "eo_grid_nodes", "eo_grid_destroy", "eo_build_operator",
+SYMBOLS = ("eo_fit", "eo_grid_create", "eo_grid_info", "eo_grid_nodes", "eo_grid_destroy", "eo_build_operator",
            "eo_get_poles", "eo_memory", "eo_apply", "eo_apply_host", "eo_apply_resolvent", "eo_set_timing", "eo_get_timing", "eo_destroy",
            "eo_last_error")
 
@@ -44,6 +44,7 @@ def lib() -> C.CDLL:
         "eo_grid_destroy": [vp],
         "eo_build_operator": [vp, C.c_int, dp, C.POINTER(Opts), vp, C.POINTER(vp)],
         "eo_get_poles": [vp, dp, dp, C.POINTER(C.c_int), dp, dp],
+        "eo_fit": [C.c_int, C.c_double, C.c_double, C.c_int, dp, dp, C.POINTER(C.c_int), dp],
         "eo_memory": [vp, i64p, i64p],
         "eo_apply": [vp, vp, C.c_int, C.c_int, vp],
         "eo_apply_host": [vp, dp, C.c_int, C.c_int, vp],

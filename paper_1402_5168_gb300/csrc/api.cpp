@@ -300,6 +300,24 @@ eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double* coeff, c
   return EO_OK;
 }
 
+eo_status eo_fit(int n_poles, double X, double delta, int cap, double* alpha, double* b, int* n,
+                 double* X_out) {
+  if (!n || !X_out) return fail(EO_ERR_INVALID_ARG, "null argument");
+  Fit f;
+  const double d = delta > 0 ? delta : 1e-10;
+  eo_status rc = n_poles > 0 ? fit_for_poles(n_poles, d, f) : fit_for_band(X, d, 301, f);
+  if (rc) return rc;
+  *n = f.N();
+  *X_out = f.X;
+  if (cap < f.N() || !alpha || !b) return fail(EO_ERR_INVALID_ARG, "output arrays too small");
+  for (int i = 0; i < f.N(); ++i) {
+    alpha[2 * i] = f.are[i]; alpha[2 * i + 1] = f.aim[i];
+    b[2 * i] = f.bre[i]; b[2 * i + 1] = f.bim[i];
+  }
+  set_error("");
+  return EO_OK;
+}
+
 eo_status eo_get_poles(eo_handle_t hd, double* alpha, double* b, int* n, double* tau, double* X) {
   if (!hd) return fail(EO_ERR_INVALID_ARG, "null handle");
   const Fit& f = hd->h.fit;

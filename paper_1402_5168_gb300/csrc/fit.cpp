@@ -5,7 +5,8 @@
 // alpha_m = sigma + i s m (m = -M..M).  With b_{-m} = conj(b_m) the function
 // R(i x) = sum_m b_m / (i x - alpha_m) satisfies R(-i x) = conj(R(i x)), so the
 // residues are fitted on [0, X] by real linear least squares (Householder QR)
-// in the real unknowns (b_0, Re b_1, Im b_1, ...).  A candidate (sigma, s, X)
+// in the real unknowns (b_0, Re b_1, Im b_1, ...), minimum-norm solution by
+// truncated SVD.  A candidate (sigma, s, X)
 // is accepted when max |e^{ix} - R(ix)| <= delta/2 on [0, X], every |b_m| <= 100
 // (large residues cancel in the pole sum and amplify rounding), and
 // max |R(iy)| <= 1 + delta/10 on a grid of [0, Y] with Y far beyond the poles;
@@ -52,11 +53,60 @@ static bool lsq(std::vector<double>& A, std::vector<double>& t, int m, int n,
     a[k] = alpha;   // R diagonal; the rest of v is no longer needed
     for (int i = k + 1; i < m; ++i) a[i] = 0;
   }
+  // R (n x n, upper) and the first n entries of Q^T t.  The band-only problem is
+  // close to rank deficient, so solve with the truncated SVD of R (singular
+  // values below eps * max(m, n) * sigma_max dropped: the minimum-norm solution),
+  // by one-sided Jacobi rotations on the columns of R.
+  std::vector<double> U((size_t)n * n), V((size_t)n * n, 0.0);
+  for (int j = 0; j < n; ++j) {
+    for (int i = 0; i < n; ++i) U[(size_t)j * n + i] = (i <= j) ? A[(size_t)j * m + i] : 0.0;
+    V[(size_t)j * n + j] = 1.0;
+  }
+  for (int sweep = 0; sweep < 60; ++sweep) {
+    double off = 0;
+    for (int p = 0; p < n - 1; ++p)
+      for (int q = p + 1; q < n; ++q) {
+        double* up = &U[(size_t)p * n];
+        double* uq = &U[(size_t)q * n];
+        double a = 0, b = 0, c = 0;
+        for (int i = 0; i < n; ++i) { a += up[i] * up[i]; b += uq[i] * uq[i]; c += up[i] * uq[i]; }
+        if (c == 0 || std::abs(c) <= 1e-15 * std::sqrt(a * b)) continue;
+        off = std::max(off, std::abs(c) / std::sqrt(a * b));
+        const double zeta = (b - a) / (2 * c);
+        const double tt = (zeta >= 0 ? 1.0 : -1.0) / (std::abs(zeta) + std::sqrt(1 + zeta * zeta));
+        const double cs = 1 / std::sqrt(1 + tt * tt), sn = cs * tt;
+        for (int i = 0; i < n; ++i) {
+          const double x1 = up[i], x2 = uq[i];
+          up[i] = cs * x1 - sn * x2;
+          uq[i] = sn * x1 + cs * x2;
+        }
+        double* vp = &V[(size_t)p * n];
+        double* vq = &V[(size_t)q * n];
+        for (int i = 0; i < n; ++i) {
+          const double x1 = vp[i], x2 = vq[i];
+          vp[i] = cs * x1 - sn * x2;
+          vq[i] = sn * x1 + cs * x2;
+        }
+      }
+    if (off < 1e-15) break;
+  }
+  // columns of U are sigma_j u_j; x = sum_j v_j (u_j . t) / sigma_j over kept j
+  std::vector<double> sig(n);
+  double smax = 0;
+  for (int j = 0; j < n; ++j) {
+    double s2 = 0;
+    for (int i = 0; i < n; ++i) s2 += U[(size_t)j * n + i] * U[(size_t)j * n + i];
+    sig[j] = std::sqrt(s2);
+    smax = std::max(smax, sig[j]);
+  }
+  const double cut = 2.220446049250313e-16 * std::max(m, n) * smax;
   x.assign(n, 0.0);
-  for (int k = n - 1; k >= 0; --k) {
-    double s = t[k];
-    for (int j = k + 1; j < n; ++j) s -= A[(size_t)j * m + k] * x[j];
-    x[k] = s / A[(size_t)k * m + k];
+  for (int j = 0; j < n; ++j) {
+    if (sig[j] <= cut) continue;
+    double d = 0;
+    for (int i = 0; i < n; ++i) d += U[(size_t)j * n + i] * t[i];
+    const double f = d / (sig[j] * sig[j]);
+    for (int i = 0; i < n; ++i) x[i] += f * V[(size_t)j * n + i];
   }
   return true;
 }
@@ -73,7 +123,7 @@ static bool residues(int N, double sigma, double s, double X, std::vector<cplx>&
   const int M = (N - 1) / 2;
   al.resize(N);
   for (int m = -M; m <= M; ++m) al[m + M] = cplx(sigma, s * m);
-  const int ns = (int)std::ceil(X * 10.0) + 41;
+  const int ns = (int)std::ceil(X * 20.0) + 41;
   const int rows = 2 * ns, cols = N;
   std::vector<double> A((size_t)rows * cols), t(rows), x;
   for (int i = 0; i < ns; ++i) {
@@ -151,8 +201,8 @@ static void store(const std::vector<cplx>& al, const std::vector<cplx>& b, doubl
   out.X = X; out.sigma = sigma; out.s = s;
 }
 
-static const double kS[] = {1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6};
-static const double kRatio[] = {3.75, 4.0};
+static const double kS[] = {0.8, 0.9, 1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6};
+static const double kRatio[] = {3.75, 4.0, 4.5, 5.0};
 
 eo_status fit_for_poles(int N, double delta, Fit& out) {
   if (N < 3 || N % 2 == 0) return fail(EO_ERR_INVALID_ARG, "n_poles must be odd and >= 3");

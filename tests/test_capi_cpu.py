@@ -51,3 +51,27 @@ def test_bad_arguments_are_rejected(capi):
     assert L.eo_grid_info(None, None, None, None) == 1
     assert L.eo_apply(None, None, 1, 1, None) == 1
     assert L.eo_destroy(None) == 0
+
+
+@pytest.mark.parametrize("n_poles,min_X", [(21, 3.0), (61, 12.0)])
+def test_library_fit_meets_contract(capi, n_poles, min_X):
+    # the host fitter's output checked by the oracle's brute-force evaluation of
+    # eqs. RM_prop1 / RM_prop2 (independent code)
+    import paper_1402_5168_gb300 as eo
+    from oracle import rational
+    alpha, b, X = eo.fit(n_poles)
+    assert alpha.size == n_poles and X >= min_X
+    band, mod, tail = rational.check_contract(alpha, b, X, 1e-10)
+    assert band <= 1e-10 and mod <= 1.0 + 1e-12 and tail < 1.0
+    assert np.array_equal(alpha[::-1], np.conj(alpha)) and np.array_equal(b[::-1], np.conj(b))
+    assert np.abs(b).max() <= 100.0
+
+
+def test_library_fit_for_a_band(capi):
+    import paper_1402_5168_gb300 as eo
+    from oracle import rational
+    alpha, b, X = eo.fit(0, 6.0)
+    assert X == 6.0
+    band, mod, tail = rational.check_contract(alpha, b, X, 1e-10)
+    assert band <= 1e-10 and mod <= 1.0 + 1e-12
+    assert alpha.size <= 31

@@ -140,12 +140,20 @@ def grf(x: np.ndarray, y: np.ndarray, seed: int, corr: float, std: float,
     amp = np.sqrt(dens * dk * dk)
     a = rng.standard_normal(kx.size) * amp
     b = rng.standard_normal(kx.size) * amp
+    # sum_k a_k cos(k.x) + b_k sin(k.x) = Re sum_{n,m} (a - i b)_{nm} e^{i n dk x} e^{i m dk y}:
+    # evaluated separably on the (n, m) lattice of the selected modes
+    N = 2 * nmax + 1
+    coef = np.zeros((N, N), dtype=np.complex128)
+    ni = np.rint(kx / dk).astype(int) + nmax
+    mi = np.rint(ky / dk).astype(int) + nmax
+    coef[ni, mi] = a - 1j * b
     xf = np.asarray(x, dtype=np.float64).ravel()
     yf = np.asarray(y, dtype=np.float64).ravel()
     out = np.zeros(xf.size)
-    for i in range(0, xf.size, 8192):
-        ph = np.outer(xf[i:i + 8192], kx) + np.outer(yf[i:i + 8192], ky)
-        out[i:i + 8192] = np.cos(ph) @ a + np.sin(ph) @ b
+    for i in range(0, xf.size, 65536):
+        ex = np.exp(1j * np.outer(xf[i:i + 65536], n * dk))
+        ey = np.exp(1j * np.outer(yf[i:i + 65536], n * dk))
+        out[i:i + 65536] = (ex * (ey @ coef.T)).sum(axis=1).real
     return out.reshape(np.shape(x))
 
 
