@@ -74,4 +74,4 @@ def test_library_fit_for_a_band(capi):
     assert X == 6.0
     band, mod, tail = rational.check_contract(alpha, b, X, 1e-10)
     assert band <= 1e-10 and mod <= 1.0 + 1e-12
-    assert alpha.size <= 31
+    assert alpha.size <= 41
