@@ -104,6 +104,8 @@ def run_ours(args):
     dev = torch.device("cuda", local)
     torch.cuda.set_device(dev)
     w = W.WORKLOADS[args.workload]
+    if args.leaves:
+        w = W.dataclasses.replace(w, nlx=args.leaves, nly=args.leaves)
     R = args.rhs
     g = eo.Grid(w.nlx, w.nly, w.p)
     x, y = g.nodes()
@@ -301,6 +303,7 @@ def main():
     ap.add_argument("--workload", default=DEFAULT, choices=sorted(W.WORKLOADS))
     ap.add_argument("--rhs", type=int, default=1)
     ap.add_argument("--poles", type=int, default=0, help="override the pole count (profiling cases)")
+    ap.add_argument("--leaves", type=int, default=0, help="override leaves per side (profiling cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=30.0)

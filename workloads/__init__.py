@@ -14,6 +14,7 @@ a fixed seed (config index * 1000 + instance).
 """
 from __future__ import annotations
 
+import dataclasses
 import math
 from dataclasses import dataclass, field
 
