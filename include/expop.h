@@ -148,6 +148,22 @@ eo_status eo_apply_host(eo_handle_t h, double *u_host, int n_rhs, int n_steps,
 eo_status eo_apply_resolvent(eo_handle_t h, int j, const double *u_dev, double *x_dev,
                              void *stream);
 
+/* eo_apply_resolvent without any device allocation.  The paper has no
+ * counterpart: this exists for callers that cannot allocate device memory when
+ * they call (code recording a CUDA graph capture, threads that must not touch
+ * the allocator, hosts that give the whole GPU to their own memory pool).
+ * Scratch comes from one fixed 16 MiB array in device memory that every GPU
+ * loading the library holds until exit; problems needing more
+ * (2 * P * K + 2 * fields * n_nodes doubles, P distinct poles, K = 2 wave / 3
+ * shallow water) are rejected with EO_ERR_INVALID_ARG.  The first call on a
+ * device looks the array's device address up (cudaGetSymbolAddress) with that
+ * device current; make that first call before any stream capture.  All calls
+ * share the array: calls whose work can overlap on the GPU race on it, so order
+ * them on one stream.  Arguments and result as eo_apply_resolvent; the call
+ * synchronises the stream before returning. */
+eo_status eo_apply_resolvent_noalloc(eo_handle_t h, int j, const double *u_dev, double *x_dev,
+                                     void *stream);
+
 /* Kernel tracing.  While on, every launch made by eo_apply / eo_apply_host /
  * eo_apply_resolvent is bracketed by CUDA events recorded on the launching stream.
  * eo_get_timing synchronises on those events and returns, per kernel class, the

@@ -14,7 +14,7 @@ WAVE_DIRICHLET, SW_WALLS = 0, 1
 
 # every symbol include/expop.h declares
 SYMBOLS = ("eo_fit", "eo_grid_create", "eo_grid_info", "eo_grid_nodes", "eo_grid_destroy", "eo_build_operator",
-           "eo_get_poles", "eo_memory", "eo_apply", "eo_apply_host", "eo_apply_resolvent", "eo_set_timing", "eo_get_timing", "eo_destroy",
+           "eo_get_poles", "eo_memory", "eo_apply", "eo_apply_host", "eo_apply_resolvent", "eo_apply_resolvent_noalloc", "eo_set_timing", "eo_get_timing", "eo_destroy",
            "eo_last_error")
 
 
@@ -49,6 +49,7 @@ def lib() -> C.CDLL:
         "eo_apply": [vp, vp, C.c_int, C.c_int, vp],
         "eo_apply_host": [vp, dp, C.c_int, C.c_int, vp],
         "eo_apply_resolvent": [vp, C.c_int, vp, vp, vp],
+        "eo_apply_resolvent_noalloc": [vp, C.c_int, vp, vp, vp],
         "eo_set_timing": [vp, C.c_int],
         "eo_get_timing": [vp, C.POINTER(C.c_int), C.POINTER(C.c_char_p), i64p, dp],
         "eo_destroy": [vp],

@@ -402,6 +402,14 @@ eo_status eo_get_timing(eo_handle_t hd, int* n_classes, const char** names, int6
   return EO_OK;
 }
 
+eo_status eo_apply_resolvent_noalloc(eo_handle_t hd, int j, const double* u_dev, double* x_dev, void* stream) {
+  if (!hd || !u_dev || !x_dev) return fail(EO_ERR_INVALID_ARG, "null argument");
+  const Handle& h = hd->h;
+  const int M = (h.fit.N() - 1) / 2;
+  if (j < M || j >= h.fit.N()) return fail(EO_ERR_INVALID_ARG, "pole index must have Im(alpha) >= 0");
+  return apply_resolvent_noalloc(hd->h, j - M, u_dev, x_dev, (cudaStream_t)stream);
+}
+
 eo_status eo_destroy(eo_handle_t hd) {
   delete hd;
   return EO_OK;

@@ -16,7 +16,9 @@
 // a block owns and reduced in a fixed order, so results are deterministic.
 #include <algorithm>
 #include <cmath>
+#include <mutex>
 #include <string>
+#include <vector>
 
 #include "handle.h"
 
@@ -908,6 +910,94 @@ eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStre
   EO_CUDA_TRY(cudaStreamSynchronize(st));
   cudaFree(tmpw);
   cudaFree(outb);
+  return EO_OK;
+}
+
+// ---------------------------------------------------------------- resolvent without allocation
+// Some callers cannot allocate device memory at call time: code running while a
+// stream is being captured into a CUDA graph, host threads that must not
+// synchronise with the device allocator, or embedders that hand every byte of
+// the GPU to their own pool.  eo_apply_resolvent takes two small scratch
+// buffers from cudaMallocAsync on every call; this variant takes them from a
+// fixed file-scope device array instead and allocates nothing.
+//
+// The array is kNoAllocDoubles doubles (16 MiB); every GPU that loads the library
+// holds it until the process exits.  It must fit the per-pole weight table
+// (P x K complex) and the real and imaginary outputs (2 x fields x nodes
+// doubles); larger problems are rejected with EO_ERR_INVALID_ARG.  All calls
+// share the array and each keeps only what the previous call left there, so
+// calls whose work overlaps on the GPU (different streams, or different
+// handles on one device without ordering) race on it.
+static constexpr size_t kNoAllocDoubles = 2u << 20;
+static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+namespace {
+std::mutex g_noalloc_mu;
+std::vector<double*> g_noalloc_ptr;   // per device ordinal; null until set up
+
+// Device address of the scratch array on the current device.  The first call
+// on a device looks it up with that device current; later calls reuse it.
+eo_status noalloc_scratch(double** out) {
+  int dev = 0;
+  EO_CUDA_TRY(cudaGetDevice(&dev));
+  std::lock_guard<std::mutex> lk(g_noalloc_mu);
+  if ((int)g_noalloc_ptr.size() <= dev) g_noalloc_ptr.resize(dev + 1, nullptr);
+  if (!g_noalloc_ptr[dev]) {
+    void* p = nullptr;
+    cudaError_t e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
+    if (e != cudaSuccess)
+      return fail(EO_ERR_CUDA, std::string("cudaGetSymbolAddress(scratch): ") + cudaGetErrorString(e));
+    g_noalloc_ptr[dev] = (double*)p;
+  }
+  *out = g_noalloc_ptr[dev];
+  return EO_OK;
+}
+}  // namespace
+
+eo_status apply_resolvent_noalloc(Handle& h, int j, const double* u, double* x, cudaStream_t st) {
+  if (j < 0 || j >= h.P) return fail(EO_ERR_INVALID_ARG, "pole index out of range");
+  const size_t nst = (size_t)h.F * h.g.n_nodes;
+  const size_t wdoubles = (size_t)2 * h.P * h.K;
+  if (wdoubles + 2 * nst > kNoAllocDoubles)
+    return fail(EO_ERR_INVALID_ARG, "problem too large for the no-allocation scratch (" +
+                                        std::to_string(wdoubles + 2 * nst) + " doubles needed, " +
+                                        std::to_string(kNoAllocDoubles) + " available)");
+  double* scratch = nullptr;
+  eo_status rc = noalloc_scratch(&scratch);
+  if (rc) return rc;
+  cd* tmpw = (cd*)scratch;              // [P][K]; only row j is written and read
+  double* outb = scratch + wdoubles;    // Re part, then Im part
+  const std::complex<double> al = h.alpha[j];
+  const std::complex<double> ws[2] = {1.0, std::complex<double>(0.0, -1.0)};
+  for (int part = 0; part < 2; ++part) {
+    const std::complex<double> c = ws[part];
+    cd w[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
+    double C[4] = {0, 0, 0, 0};
+    if (h.kind == EO_WAVE_DIRICHLET) {
+      const std::complex<double> w0 = c, w1 = c * h.tau / al;
+      w[0] = make_double2(w0.real(), w0.imag());
+      w[1] = make_double2(w1.real(), w1.imag());
+      C[0] = (c / al).real();
+    } else {
+      const double tf = h.tau * h.opts.sw_f;
+      const std::complex<double> D = al * al + tf * tf;
+      const std::complex<double> w0 = c, w1 = c * (-al / D), w2 = c * (-tf / D);
+      w[0] = make_double2(w0.real(), w0.imag());
+      w[1] = make_double2(w1.real(), w1.imag());
+      w[2] = make_double2(w2.real(), w2.imag());
+      C[0] = w1.real();
+      C[1] = w2.real();
+    }
+    EO_CUDA_TRY(cudaMemcpyAsync(tmpw + (size_t)j * h.K, w, sizeof(cd) * h.K, cudaMemcpyHostToDevice, st));
+    // the copy reads w from the host stack: let it finish before w goes out of scope
+    EO_CUDA_TRY(cudaStreamSynchronize(st));
+    if ((rc = run_step(h, u, outb + part * nst, 1, j, 1, tmpw, C, st))) return rc;
+  }
+  EO_CUDA_TRY(cudaMemcpy2DAsync(x, 2 * sizeof(double), outb, sizeof(double), sizeof(double), nst,
+                                cudaMemcpyDeviceToDevice, st));
+  EO_CUDA_TRY(cudaMemcpy2DAsync(x + 1, 2 * sizeof(double), outb + nst, sizeof(double), sizeof(double), nst,
+                                cudaMemcpyDeviceToDevice, st));
+  EO_CUDA_TRY(cudaStreamSynchronize(st));
   return EO_OK;
 }
 

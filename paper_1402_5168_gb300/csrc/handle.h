@@ -99,5 +99,6 @@ enum { TR_PRE = 0, TR_UP_LEAF, TR_UP_MERGE, TR_ROOT, TR_DOWN_MERGE, TR_DOWN_LEAF
 eo_status build(Handle& h, const double* coeff, cudaStream_t st);
 eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st);
 eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStream_t st);
+eo_status apply_resolvent_noalloc(Handle& h, int j, const double* u, double* x, cudaStream_t st);
 
 }  // namespace eo
