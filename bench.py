@@ -30,7 +30,7 @@ UNIT = "applies/s"
 # FP64 fused multiply-add throughput measured on a GB300 of this machine (8 independent
 # FMA chains per thread, 1216 blocks x 256 threads, ~1995 MHz): 1.207 TFLOP/s
 FP64_PEAK_TFLOPS = 1.207
-DEFAULT = W.WAVE_32X32_P16.name
+DEFAULT = W.SW_16X16_P16.name
 
 
 def peaks():

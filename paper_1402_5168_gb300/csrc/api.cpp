@@ -70,7 +70,7 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
     h.tau = h.fit.X / o.band;
   } else {
     if (!(o.tau > 0)) return fail(EO_ERR_INVALID_ARG, "opts.tau must be positive when n_poles == 0");
-    if ((rc = fit_for_band(o.tau * o.band, delta, 301, h.fit))) return rc;
+    if ((rc = fit_for_band(o.tau * o.band, delta, 1 << 20, h.fit))) return rc;
     h.tau = o.tau;
   }
   const int N = h.fit.N(), M = (N - 1) / 2;
@@ -305,7 +305,7 @@ eo_status eo_fit(int n_poles, double X, double delta, int cap, double* alpha, do
   if (!n || !X_out) return fail(EO_ERR_INVALID_ARG, "null argument");
   Fit f;
   const double d = delta > 0 ? delta : 1e-10;
-  eo_status rc = n_poles > 0 ? fit_for_poles(n_poles, d, f) : fit_for_band(X, d, 301, f);
+  eo_status rc = n_poles > 0 ? fit_for_poles(n_poles, d, f) : fit_for_band(X, d, 1 << 20, f);
   if (rc) return rc;
   *n = f.N();
   *X_out = f.X;

@@ -108,26 +108,31 @@ __global__ void leaf_real_ops(int nlx, int nly, int p, long long n_int, long lon
   }
 }
 
-// Per pole: A = Aii0 - kappa2 I; XY = [I | -Aib]; T = Fbb; Fbi_c = Fbi (complex).
-__global__ void leaf_assemble(int nleaf, int ni, int nb, cd kappa2, const double* Aii0,
-                              const double* Aib, const double* Fbb, cd* A, cd* XY, cd* T) {
+// Batch entry i = (pole gi, leaf) with leaf = i % nleaf, gi = i / nleaf:
+// A = Aii0 - kappa2[gi] I; XY = [I | -Aib]; T = Fbb (complex).
+__global__ void leaf_assemble(int nbatch, int nleaf, int ni, int nb, const cd* __restrict__ kappa2,
+                              const double* Aii0, const double* Aib, const double* Fbb, cd* A, cd* XY,
+                              cd* T) {
   const size_t nA = (size_t)ni * ni, nXY = (size_t)ni * (ni + nb), nT = (size_t)nb * nb;
-  const size_t tot = (size_t)nleaf * (nA + nXY + nT);
+  const size_t tot = (size_t)nbatch * (nA + nXY + nT);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot;
        t += (size_t)gridDim.x * blockDim.x) {
-    size_t leaf = t / (nA + nXY + nT), e = t % (nA + nXY + nT);
+    const size_t bi = t / (nA + nXY + nT);
+    size_t e = t % (nA + nXY + nT);
+    const size_t leaf = bi % nleaf;
     if (e < nA) {
       const int i = e % ni, j = e / ni;
-      double v = Aii0[leaf * nA + e];
-      A[leaf * nA + e] = make_double2(v - (i == j ? kappa2.x : 0.0), (i == j ? -kappa2.y : 0.0));
+      const cd k2 = kappa2[bi / nleaf];
+      const double v = Aii0[leaf * nA + e];
+      A[bi * nA + e] = make_double2(v - (i == j ? k2.x : 0.0), (i == j ? -k2.y : 0.0));
     } else if (e < nA + nXY) {
       e -= nA;
       const int i = e % ni, j = e / ni;
-      double v = (j < ni) ? (i == j ? 1.0 : 0.0) : -Aib[leaf * (size_t)ni * nb + (e - (size_t)ni * ni)];
-      XY[leaf * nXY + e] = make_double2(v, 0.0);
+      const double v = (j < ni) ? (i == j ? 1.0 : 0.0) : -Aib[leaf * (size_t)ni * nb + (e - (size_t)ni * ni)];
+      XY[bi * nXY + e] = make_double2(v, 0.0);
     } else {
       e -= nA + nXY;
-      T[leaf * nT + e] = make_double2(Fbb[leaf * nT + e], 0.0);
+      T[bi * nT + e] = make_double2(Fbb[leaf * nT + e], 0.0);
     }
   }
 }
@@ -138,12 +143,14 @@ __global__ void real_to_complex(size_t n, const double* x, cd* y) {
 }
 
 // Merge gathers for one level, one parent box per block (column-major outputs).
+// Block index = gi * nbo + box: pole gi of the group, parent box (0 when shared).
+// Children's T: Tc[gi][child box][nbd_c x nbd_c], nbo_c child blocks per pole.
 __global__ void merge_gather(int nbd_c, int n3, int npar, const int* __restrict__ par_child,
                              const int* __restrict__ par_idx, const int* __restrict__ a3,
                              const int* __restrict__ b3, int dir, int nbx_par, int nbx_child,
-                             int shared, const cd* __restrict__ Tc, cd* M33, cd* Q, cd* Rm,
-                             cd* Tpar) {
-  const int box = blockIdx.x;
+                             int shared, int nbo, int nbo_c, const cd* __restrict__ Tc, cd* M33, cd* Q,
+                             cd* Rm, cd* Tpar) {
+  const int box = blockIdx.x % nbo, gi = blockIdx.x / nbo;
   int ca, cb;
   if (shared) { ca = cb = 0; }
   else {
@@ -152,12 +159,13 @@ __global__ void merge_gather(int nbd_c, int n3, int npar, const int* __restrict_
     else { ca = (2 * by) * nbx_child + bx; cb = ca + nbx_child; }
   }
   const size_t nT = (size_t)nbd_c * nbd_c;
-  const cd* Ta = Tc + (size_t)ca * nT;
-  const cd* Tb = Tc + (size_t)cb * nT;
-  cd* m33 = M33 + (size_t)box * n3 * n3;
-  cd* qq = Q ? Q + (size_t)box * npar * n3 : nullptr;
-  cd* rm = Rm + (size_t)box * n3 * npar;
-  cd* tp = Tpar ? Tpar + (size_t)box * npar * npar : nullptr;
+  const cd* Ta = Tc + ((size_t)gi * nbo_c + ca) * nT;
+  const cd* Tb = Tc + ((size_t)gi * nbo_c + cb) * nT;
+  const int box_out = blockIdx.x;
+  cd* m33 = M33 + (size_t)box_out * n3 * n3;
+  cd* qq = Q ? Q + (size_t)box_out * npar * n3 : nullptr;
+  cd* rm = Rm + (size_t)box_out * n3 * npar;
+  cd* tp = Tpar ? Tpar + (size_t)box_out * npar * npar : nullptr;
   for (int e = threadIdx.x; e < n3 * n3; e += blockDim.x) {
     const int t = e % n3, u = e / n3;
     cd x = Ta[a3[t] + (size_t)a3[u] * nbd_c], y = Tb[b3[t] + (size_t)b3[u] * nbd_c];
@@ -201,28 +209,31 @@ __global__ void set_identity(int n, int nbatch, cd* M) {
 
 // B_root = diag(nu) T_root + tau f G_t (oblique wall condition); n = 4 * nseg_side * q.
 // side of boundary node i: from the root box layout S (sx q), E (sy q), N (sx q), W (sy q).
-__global__ void root_system(int n, int q, int sxq, int syq, cd alpha, double tauf,
-                            const double* __restrict__ Ex, const double* __restrict__ Ey,
+// Block entry gi of the group: B = diag(nu) T_root + tau f G_t for pole alpha[gi].
+__global__ void root_system(int nbatch, int n, int q, int sxq, int syq, const cd* __restrict__ alpha,
+                            double tauf, const double* __restrict__ Ex, const double* __restrict__ Ey,
                             const cd* __restrict__ T, cd* B) {
-  for (size_t e = blockIdx.x * (size_t)blockDim.x + threadIdx.x; e < (size_t)n * n;
-       e += (size_t)gridDim.x * blockDim.x) {
+  const size_t nn = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)nbatch * nn;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t gi = t / nn, e = t % nn;
+    const cd al = alpha[gi];
     const int i = e % n, j = e / n;
-    int side, off;
-    if (i < sxq) { side = 0; off = i; }
-    else if (i < sxq + syq) { side = 1; off = i - sxq; }
-    else if (i < 2 * sxq + syq) { side = 2; off = i - sxq - syq; }
-    else { side = 3; off = i - 2 * sxq - syq; }
+    int side;
+    if (i < sxq) side = 0;
+    else if (i < sxq + syq) side = 1;
+    else if (i < 2 * sxq + syq) side = 2;
+    else side = 3;
     const double sg = (side == 1 || side == 2) ? 1.0 : -1.0;
-    const cd t = T[e];
-    double re = sg * (alpha.x * t.x - alpha.y * t.y), im = sg * (alpha.x * t.y + alpha.y * t.x);
+    const cd tv = T[t];
+    double re = sg * (al.x * tv.x - al.y * tv.y), im = sg * (al.x * tv.y + al.y * tv.x);
     // tangential derivative inside the same segment
-    const int seg_i = i / q, seg_j = j / q;
-    if (seg_i == seg_j) {
+    if (i / q == j / q) {
       const int a = i % q, c = j % q;
       if (side == 1 || side == 3) re += tauf * Ey[a * q + c];          // + tau f dh/dy on x-walls
       else re -= tauf * Ex[a * q + c];                                  // - tau f dh/dx on y-walls
     }
-    B[e] = make_double2(re, im);
+    B[t] = make_double2(re, im);
   }
 }
 
@@ -316,144 +327,155 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
   leaf_real_ops<<<nlo, 256, sizeof(double) * p * p, st>>>(g.nlx, g.nly, p, g.n_int, g.n_hseg, dDx, dDy,
                                                         acoef, Aii0, Aib, Fbi, Fbb);
   EO_CUDA_TRY(cudaGetLastError());
-  cd *Fbi_c, *Aw, *T0;
+  cd* Fbi_c;
   if ((rc = talloc((void**)&Fbi_c, sizeof(cd) * nlo * nb * ni))) return rc;
-  if ((rc = talloc((void**)&Aw, sizeof(cd) * nlo * ni * ni))) return rc;
-  if ((rc = talloc((void**)&T0, sizeof(cd) * nlo * nb * nb))) return rc;
   real_to_complex<<<1024, 256, 0, st>>>((size_t)nlo * nb * ni, Fbi, Fbi_c);
-  int *piv, *info;
   const Plan& plan = h.plan;
   const int L = plan.L();
-  // largest batched system: leaves (ni) or any merge level / root
-  size_t maxpiv = (size_t)nlo * ni, maxinfo = nlo;
-  size_t ws_merge = 0;   // complex entries for M33, Z, Q, Rm, Tpar
+  // Poles are processed in groups of G: with shared operators (one block per
+  // level) a group batches many poles into each factorisation and product;
+  // with per-box operators a single pole already batches every box.
+  const int G = h.shared ? std::min(P, 64) : 1;
+  size_t maxpiv = (size_t)G * nlo * ni, maxinfo = (size_t)G * nlo;
+  size_t ws_merge = 0;   // complex entries for M33, Z, Q, Rm (or the root system)
+  size_t maxT = (size_t)G * nlo * nb * nb;
   for (int l = 1; l <= L; ++l) {
     const Level& lv = plan.lv[l];
-    const int nbo = h.shared ? 1 : lv.nbox;
-    maxpiv = std::max(maxpiv, (size_t)nbo * lv.n3);
-    maxinfo = std::max(maxinfo, (size_t)nbo);
-    ws_merge = std::max(ws_merge, (size_t)nbo * (2 * (size_t)lv.n3 * lv.n3 + 2 * (size_t)lv.nbd * lv.n3 +
-                                                  (size_t)lv.nbd * lv.nbd));
+    const size_t nbo = (size_t)G * (h.shared ? 1 : lv.nbox);
+    maxpiv = std::max(maxpiv, nbo * lv.n3);
+    maxinfo = std::max(maxinfo, nbo);
+    ws_merge = std::max(ws_merge, nbo * (2 * (size_t)lv.n3 * lv.n3 + 2 * (size_t)lv.nbd * lv.n3));
+    maxT = std::max(maxT, nbo * lv.nbd * lv.nbd);
   }
   if (h.kind == EO_SW_WALLS) {
-    maxpiv = std::max(maxpiv, (size_t)h.nroot);
-    ws_merge = std::max(ws_merge, (size_t)2 * h.nroot * h.nroot);
+    maxpiv = std::max(maxpiv, (size_t)G * h.nroot);
+    maxinfo = std::max(maxinfo, (size_t)G);
+    ws_merge = std::max(ws_merge, (size_t)G * h.nroot * h.nroot);
   }
-  if ((rc = talloc((void**)&piv, sizeof(int) * maxpiv))) return rc;
-  if ((rc = talloc((void**)&info, sizeof(int) * maxinfo))) return rc;
-  cd* mw = nullptr;
-  if (ws_merge && (rc = talloc((void**)&mw, sizeof(cd) * ws_merge))) return rc;
-  // T of the current and next level
-  size_t maxT = (size_t)nlo * nb * nb;
-  for (int l = 1; l <= L; ++l) {
-    const Level& lv = plan.lv[l];
-    maxT = std::max(maxT, (size_t)(h.shared ? 1 : lv.nbox) * lv.nbd * lv.nbd);
-  }
-  cd *Tc, *Tn;
+  cd *Aw, *T0, *Tc, *Tn, *mw = nullptr, *kap, *dal;
+  int *piv, *info;
+  if ((rc = talloc((void**)&Aw, sizeof(cd) * G * nlo * ni * ni))) return rc;
+  if ((rc = talloc((void**)&T0, sizeof(cd) * G * nlo * nb * nb))) return rc;
   if ((rc = talloc((void**)&Tc, sizeof(cd) * maxT))) return rc;
   if ((rc = talloc((void**)&Tn, sizeof(cd) * maxT))) return rc;
+  if (ws_merge && (rc = talloc((void**)&mw, sizeof(cd) * ws_merge))) return rc;
+  if ((rc = talloc((void**)&piv, sizeof(int) * maxpiv))) return rc;
+  if ((rc = talloc((void**)&info, sizeof(int) * maxinfo))) return rc;
+  if ((rc = talloc((void**)&kap, sizeof(cd) * G))) return rc;
+  if ((rc = talloc((void**)&dal, sizeof(cd) * G))) return rc;
   std::vector<int> hinfo;
   const cuDoubleComplex one = {1.0, 0.0}, zero = {0.0, 0.0}, mone = {-1.0, 0.0};
 
-  for (int pj = 0; pj < P; ++pj) {
-    const std::complex<double> al = h.alpha[pj];
-    std::complex<double> k2;
-    if (h.kind == EO_WAVE_DIRICHLET) k2 = (al / h.tau) * (al / h.tau);
-    else k2 = (al * al + (h.tau * h.opts.sw_f) * (h.tau * h.opts.sw_f)) /
-              (h.tau * h.tau * h.opts.sw_g * h.opts.sw_H);
-    // ---- leaves
-    cd* XYp = h.XY + (size_t)pj * h.xy_pstride;
-    cd* Hp = h.H + (size_t)pj * h.h_pstride;
-    leaf_assemble<<<2048, 256, 0, st>>>(nlo, ni, nb, make_double2(k2.real(), k2.imag()), Aii0, Aib, Fbb,
-                                        Aw, XYp, T0);
+  for (int p0 = 0; p0 < P; p0 += G) {
+    const int g = std::min(G, P - p0);
+    std::vector<cd> hk(g), ha(g);
+    for (int gi = 0; gi < g; ++gi) {
+      const std::complex<double> al = h.alpha[p0 + gi];
+      std::complex<double> k2;
+      if (h.kind == EO_WAVE_DIRICHLET) k2 = (al / h.tau) * (al / h.tau);
+      else k2 = (al * al + (h.tau * h.opts.sw_f) * (h.tau * h.opts.sw_f)) /
+                (h.tau * h.tau * h.opts.sw_g * h.opts.sw_H);
+      hk[gi] = make_double2(k2.real(), k2.imag());
+      ha[gi] = make_double2(al.real(), al.imag());
+    }
+    EO_CUDA_TRY(cudaMemcpyAsync(kap, hk.data(), sizeof(cd) * g, cudaMemcpyHostToDevice, st));
+    EO_CUDA_TRY(cudaMemcpyAsync(dal, ha.data(), sizeof(cd) * g, cudaMemcpyHostToDevice, st));
+    // ---- leaves: batch entries (pole of the group, leaf), contiguous blocks
+    const int nbl = g * nlo;
+    cd* XYp = h.XY + (size_t)p0 * h.xy_pstride;
+    cd* Hp = h.H + (size_t)p0 * h.h_pstride;
+    const long long xyb = (long long)ni * (ni + nb);
+    const long long hb = (long long)nb * ni;
+    leaf_assemble<<<2048, 256, 0, st>>>(nbl, nlo, ni, nb, kap, Aii0, Aib, Fbb, Aw, XYp, T0);
     EO_CUDA_TRY(cudaGetLastError());
     {
-      const long long xyb = std::max<long long>(h.xy_bstride, (long long)ni * (ni + nb));
-      const long long hb = std::max<long long>(h.h_bstride, (long long)nb * ni);
-      std::vector<cd*> pa(nlo), pb(nlo);
-      for (int i = 0; i < nlo; ++i) { pa[i] = Aw + (size_t)i * ni * ni; pb[i] = XYp + (size_t)i * xyb; }
+      std::vector<cd*> pa(nbl), pb(nbl);
+      for (int i = 0; i < nbl; ++i) { pa[i] = Aw + (size_t)i * ni * ni; pb[i] = XYp + (size_t)i * xyb; }
       cd **dpa, **dpb;
-      if ((rc = talloc((void**)&dpa, sizeof(cd*) * nlo))) return rc;
-      if ((rc = talloc((void**)&dpb, sizeof(cd*) * nlo))) return rc;
-      EO_CUDA_TRY(cudaMemcpyAsync(dpa, pa.data(), sizeof(cd*) * nlo, cudaMemcpyHostToDevice, st));
-      EO_CUDA_TRY(cudaMemcpyAsync(dpb, pb.data(), sizeof(cd*) * nlo, cudaMemcpyHostToDevice, st));
-      EO_CUBLAS_TRY(cublasZgetrfBatched(cb, ni, (cuDoubleComplex**)dpa, ni, piv, info, nlo));
-      hinfo.assign(nlo, 0);
-      EO_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nlo, cudaMemcpyDeviceToHost, st));
+      if ((rc = talloc((void**)&dpa, sizeof(cd*) * nbl))) return rc;
+      if ((rc = talloc((void**)&dpb, sizeof(cd*) * nbl))) return rc;
+      EO_CUDA_TRY(cudaMemcpyAsync(dpa, pa.data(), sizeof(cd*) * nbl, cudaMemcpyHostToDevice, st));
+      EO_CUDA_TRY(cudaMemcpyAsync(dpb, pb.data(), sizeof(cd*) * nbl, cudaMemcpyHostToDevice, st));
+      EO_CUBLAS_TRY(cublasZgetrfBatched(cb, ni, (cuDoubleComplex**)dpa, ni, piv, info, nbl));
+      hinfo.assign(nbl, 0);
+      EO_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nbl, cudaMemcpyDeviceToHost, st));
       EO_CUDA_TRY(cudaStreamSynchronize(st));
-      for (int i = 0; i < nlo; ++i)
+      for (int i = 0; i < nbl; ++i)
         if (hinfo[i]) return fail(EO_ERR_SINGULAR, "leaf interior system singular (leaf " + std::to_string(i) + ")");
       int hi = 0;
       EO_CUBLAS_TRY(cublasZgetrsBatched(cb, CUBLAS_OP_N, ni, ni + nb, (const cuDoubleComplex* const*)dpa, ni, piv,
-                                        (cuDoubleComplex* const*)dpb, ni, &hi, nlo));
-      // T = Fbb + Fbi Y ; H = Fbi X
+                                        (cuDoubleComplex* const*)dpb, ni, &hi, nbl));
+      // T = Fbb + Fbi Y ; H = Fbi X  (Fbi per leaf; shared across the poles of a group)
+      const long long fs = (G > 1) ? 0 : (long long)nb * ni;
       EO_CUBLAS_TRY(cublasZgemmStridedBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, nb, nb, ni, &one,
-                                              (const cuDoubleComplex*)Fbi_c, nb, (long long)nb * ni,
+                                              (const cuDoubleComplex*)Fbi_c, nb, fs,
                                               (const cuDoubleComplex*)(XYp + (size_t)ni * ni), ni, xyb,
-                                              &one, (cuDoubleComplex*)T0, nb, (long long)nb * nb, nlo));
+                                              &one, (cuDoubleComplex*)T0, nb, (long long)nb * nb, nbl));
       EO_CUBLAS_TRY(cublasZgemmStridedBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, nb, ni, ni, &one,
-                                              (const cuDoubleComplex*)Fbi_c, nb, (long long)nb * ni,
+                                              (const cuDoubleComplex*)Fbi_c, nb, fs,
                                               (const cuDoubleComplex*)XYp, ni, xyb, &zero,
-                                              (cuDoubleComplex*)Hp, nb, hb, nlo));
+                                              (cuDoubleComplex*)Hp, nb, hb, nbl));
     }
     // ---- merges (parent T alternates between Tc and Tn; never the buffer being read)
     cd* Tprev = T0;
-    int nbd_prev = nb;
+    int nbd_prev = nb, nbo_prev = nlo;
     for (int l = 1; l <= L; ++l) {
       const Level& lv = plan.lv[l];
       LevelDev& ld = h.lv[l];
       const int nbo = h.shared ? 1 : lv.nbox;
+      const int nbt = g * nbo;   // batch entries at this level
       const int n3 = lv.n3, npar = lv.nbd;
       const bool root = (l == L);
       const bool need_par = !(root && h.kind == EO_WAVE_DIRICHLET);
       const bool need_T = !root || h.kind == EO_SW_WALLS;
       cd* M33 = mw;
-      cd* Z = M33 + (size_t)nbo * n3 * n3;
-      cd* Qm = Z + (size_t)nbo * n3 * n3;
-      cd* Rm = Qm + (size_t)nbo * npar * n3;
+      cd* Z = M33 + (size_t)nbt * n3 * n3;
+      cd* Qm = Z + (size_t)nbt * n3 * n3;
+      cd* Rm = Qm + (size_t)nbt * npar * n3;
       cd* Tw = (l % 2) ? Tc : Tn;
-      merge_gather<<<nbo, 256, 0, st>>>(nbd_prev, n3, npar, ld.par_child, ld.par_idx, ld.a3, ld.b3, lv.dir,
-                                        lv.nbx, plan.lv[l - 1].nbx, h.shared, Tprev, M33,
+      merge_gather<<<nbt, 256, 0, st>>>(nbd_prev, n3, npar, ld.par_child, ld.par_idx, ld.a3, ld.b3, lv.dir,
+                                        lv.nbx, plan.lv[l - 1].nbx, h.shared, nbo, nbo_prev, Tprev, M33,
                                         need_par ? Qm : nullptr, Rm, need_T ? Tw : nullptr);
       EO_CUDA_TRY(cudaGetLastError());
-      if ((rc = batched_inverse(cb, st, n3, nbo, M33, Z, piv, info, hinfo, "merge interface system"))) return rc;
-      cd* ZUp = ld.ZU + (size_t)pj * ld.zu_pstride;
-      const long long zub = std::max<long long>(ld.zu_bstride, (long long)ld.zu_rows * n3);
-      copy_scaled<<<nbo, 256, 0, st>>>(n3, Z, ZUp, ld.zu_rows, zub, -1.0);
+      if ((rc = batched_inverse(cb, st, n3, nbt, M33, Z, piv, info, hinfo, "merge interface system"))) return rc;
+      cd* ZUp = ld.ZU + (size_t)p0 * ld.zu_pstride;
+      const long long zub = (long long)ld.zu_rows * n3;
+      copy_scaled<<<nbt, 256, 0, st>>>(n3, Z, ZUp, ld.zu_rows, zub, -1.0);
       if (need_par) {
-        cd* Sp = ld.S + (size_t)pj * ld.s_pstride;
-        const long long sb = std::max<long long>(ld.s_bstride, (long long)n3 * npar);
+        cd* Sp = ld.S + (size_t)p0 * ld.s_pstride;
+        const long long sb = (long long)n3 * npar;
         // U = -Q Z  -> rows [n3, n3 + npar) of ZU
         EO_CUBLAS_TRY(cublasZgemmStridedBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, npar, n3, n3, &mone,
                                                 (const cuDoubleComplex*)Qm, npar, (long long)npar * n3,
                                                 (const cuDoubleComplex*)Z, n3, (long long)n3 * n3, &zero,
-                                                (cuDoubleComplex*)(ZUp + n3), ld.zu_rows, zub, nbo));
+                                                (cuDoubleComplex*)(ZUp + n3), ld.zu_rows, zub, nbt));
         // S = -Z Rm
         EO_CUBLAS_TRY(cublasZgemmStridedBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, n3, npar, n3, &mone,
                                                 (const cuDoubleComplex*)Z, n3, (long long)n3 * n3,
                                                 (const cuDoubleComplex*)Rm, n3, (long long)n3 * npar, &zero,
-                                                (cuDoubleComplex*)Sp, n3, sb, nbo));
+                                                (cuDoubleComplex*)Sp, n3, sb, nbt));
         if (need_T) {
           // T_parent += Q S
           EO_CUBLAS_TRY(cublasZgemmStridedBatched(cb, CUBLAS_OP_N, CUBLAS_OP_N, npar, npar, n3, &one,
                                                   (const cuDoubleComplex*)Qm, npar, (long long)npar * n3,
                                                   (const cuDoubleComplex*)Sp, n3, sb, &one,
-                                                  (cuDoubleComplex*)Tw, npar, (long long)npar * npar, nbo));
+                                                  (cuDoubleComplex*)Tw, npar, (long long)npar * npar, nbt));
         }
       }
       Tprev = Tw;
       nbd_prev = npar;
+      nbo_prev = nbo;
     }
     // ---- root oblique system (shallow-water walls)
     if (h.kind == EO_SW_WALLS) {
       const Level& rl = plan.lv[L];
       const int n = rl.nbd;
       cd* Broot = mw;
-      cd* Bi = h.Binv + (size_t)pj * n * n;
-      root_system<<<1024, 256, 0, st>>>(n, q, rl.sx * q, rl.sy * q, make_double2(al.real(), al.imag()),
-                                        h.tau * h.opts.sw_f, dEx, dEy, Tprev, Broot);
+      cd* Bi = h.Binv + (size_t)p0 * n * n;
+      root_system<<<2048, 256, 0, st>>>(g, n, q, rl.sx * q, rl.sy * q, dal, h.tau * h.opts.sw_f, dEx, dEy,
+                                        Tprev, Broot);
       EO_CUDA_TRY(cudaGetLastError());
-      if ((rc = batched_inverse(cb, st, n, 1, Broot, Bi, piv, info, hinfo, "root wall system"))) return rc;
+      if ((rc = batched_inverse(cb, st, n, g, Broot, Bi, piv, info, hinfo, "root wall system"))) return rc;
     }
   }
   EO_CUDA_TRY(cudaStreamSynchronize(st));

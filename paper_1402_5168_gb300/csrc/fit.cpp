@@ -13,8 +13,11 @@
 // b is then divided by max(1, max|R|) so eq. RM_prop2 holds on that grid.
 // The search keeps the widest X for the requested pole count.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
+#include <functional>
+#include <thread>
 
 #include "engine.h"
 
@@ -237,8 +240,139 @@ eo_status fit_for_poles(int N, double delta, Fit& out) {
   return EO_OK;
 }
 
+// ---------------------------------------------------------------- wide bands
+// For a band X far wider than the pole spacing the dense search above is too
+// costly.  The pole line is then extended to cover [-(X + extra), X + extra] and
+// the residues of all but the E outermost poles on each side are set to the
+// infinite-line values b_m = beta e^{i s m}, beta = -s e^{sigma} / (2 pi): by
+// Poisson summation sum_m beta e^{ism} / (i(x - s m) - sigma) = e^{ix} up to
+// aliasing terms of size e^{-2 pi sigma / s} (sigma/s >= 4.5 gives < 1e-12).
+// The 2E outermost residues absorb the truncation of that sum: they are the
+// least-squares solution of R(ix) = e^{ix} on [0, X] with the inner residues
+// held fixed.  Candidates (s, sigma/s, E, extra) are tried in a fixed order and
+// accepted on the same criteria as above, with |R(iy)| checked on a grid up to
+// twice the pole span and geometrically spaced points beyond.
+
+static void par_for(int64_t n, const std::function<void(int64_t, int64_t)>& fn) {
+  unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  if (n < 4096) nt = 1;
+  std::vector<std::thread> th;
+  const int64_t chunk = (n + nt - 1) / nt;
+  for (unsigned t = 0; t < nt; ++t) {
+    const int64_t a = t * chunk, e = std::min<int64_t>(n, a + chunk);
+    if (a >= e) break;
+    th.emplace_back(fn, a, e);
+  }
+  for (auto& x : th) x.join();
+}
+
+static bool wide_candidate(double X, double delta, double s, double ratio, int E, double extra,
+                           std::vector<cplx>& al, std::vector<cplx>& b, double* rmax) {
+  const double sigma = ratio * s;
+  const int M = (int)std::ceil((X + extra) / s);
+  const int N = 2 * M + 1;
+  if (E >= M) return false;
+  al.resize(N);
+  b.resize(N);
+  const double beta = -s * std::exp(sigma) / (2 * M_PI);
+  for (int m = -M; m <= M; ++m) {
+    al[m + M] = cplx(sigma, s * m);
+    b[m + M] = beta * std::exp(cplx(0.0, s * m));
+  }
+  // least squares for the 2E outer residues (E complex unknowns by symmetry)
+  const int ns = (int)std::ceil(X * 8.0) + 41;
+  const int rows = 2 * ns, cols = 2 * E;
+  std::vector<double> A((size_t)rows * cols), t(rows), x;
+  par_for(ns, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      const double th = X * i / (ns - 1);
+      const cplx z(0.0, th);
+      cplx rc(0, 0);
+      for (int m = -(M - E); m <= M - E; ++m) rc += b[m + M] / (z - al[m + M]);
+      const cplx tg = std::exp(cplx(0.0, th)) - rc;
+      t[i] = tg.real();
+      t[ns + i] = tg.imag();
+      for (int k = 0; k < E; ++k) {
+        const int mm = M - E + 1 + k;
+        const cplx pp = 1.0 / (z - al[mm + M]), nn = 1.0 / (z - al[-mm + M]);
+        const cplx c1 = pp + nn, c2 = cplx(0, 1) * (pp - nn);
+        A[(size_t)(2 * k) * rows + i] = c1.real();
+        A[(size_t)(2 * k) * rows + ns + i] = c1.imag();
+        A[(size_t)(2 * k + 1) * rows + i] = c2.real();
+        A[(size_t)(2 * k + 1) * rows + ns + i] = c2.imag();
+      }
+    }
+  });
+  std::vector<double> sc(cols);
+  for (int j = 0; j < cols; ++j) {
+    double s2 = 0;
+    for (int i = 0; i < rows; ++i) s2 += A[(size_t)j * rows + i] * A[(size_t)j * rows + i];
+    sc[j] = std::sqrt(s2);
+    for (int i = 0; i < rows; ++i) A[(size_t)j * rows + i] /= sc[j];
+  }
+  if (!lsq(A, t, rows, cols, x)) return false;
+  for (int k = 0; k < E; ++k) {
+    const int mm = M - E + 1 + k;
+    b[mm + M] = cplx(x[2 * k] / sc[2 * k], x[2 * k + 1] / sc[2 * k + 1]);
+    b[-mm + M] = std::conj(b[mm + M]);
+  }
+  double bmax = 0;
+  for (const cplx& v : b) bmax = std::max(bmax, std::abs(v));
+  if (bmax > 100.0) return false;
+  // band error and modulus on grids, in parallel
+  auto maxabs = [&](int64_t n, const std::function<double(int64_t)>& f) {
+    std::vector<double> part(64, 0.0);
+    std::atomic<int> slot(0);
+    par_for(n, [&](int64_t i0, int64_t i1) {
+      double mx = 0;
+      for (int64_t i = i0; i < i1; ++i) mx = std::max(mx, f(i));
+      part[slot++] = mx;
+    });
+    return *std::max_element(part.begin(), part.end());
+  };
+  const int64_t nb = (int64_t)std::ceil(X / 0.02) + 1;
+  const double err = maxabs(nb, [&](int64_t i) {
+    const double th = X * i / (nb - 1);
+    return std::abs(std::exp(cplx(0, th)) - Reval(th, al, b));
+  });
+  if (err > 0.5 * delta) return false;
+  // |R| inside the band exceeds 1 by at most the band error; it sets the final
+  // scaling too (after which the band error is at most delta)
+  const double rin = maxabs(nb, [&](int64_t i) { return std::abs(Reval(X * i / (nb - 1), al, b)); });
+  const double span = s * M;
+  const double Y1 = 2 * span + 300.0;
+  const int64_t n1 = (int64_t)std::ceil((Y1 - X) / 0.02) + 1;
+  double r = maxabs(n1, [&](int64_t i) { return std::abs(Reval(X + (Y1 - X) * i / (n1 - 1), al, b)); });
+  // geometric points from Y1 to 1e7, then the bound |R(iy)| <= sum|b| / (y - max|alpha|)
+  const int64_t n2 = (int64_t)std::ceil(std::log(1e7 / Y1) / std::log(1.002)) + 1;
+  r = std::max(r, maxabs(n2, [&](int64_t i) { return std::abs(Reval(Y1 * std::pow(1.002, (double)i), al, b)); }));
+  double bsum = 0;
+  for (const cplx& v : b) bsum += std::abs(v);
+  if (bsum / (1e7 - std::abs(al[0])) > 1.0) return false;
+  if (r > 1.0 + 0.1 * delta) return false;
+  *rmax = std::max(r, rin);
+  return true;
+}
+
+eo_status fit_wide(double X, double delta, Fit& out) {
+  static const double cand[][4] = {
+      {1.0, 4.5, 28, 32}, {1.0, 5.0, 24, 28}, {1.0, 5.0, 28, 32}, {1.2, 4.5, 16, 24}, {1.2, 4.5, 20, 28},
+      {1.0, 4.5, 24, 32}, {1.0, 5.0, 20, 28}, {1.0, 4.5, 20, 28}, {1.2, 5.0, 24, 28}, {1.2, 4.5, 24, 32},
+      {1.0, 5.0, 16, 24}, {1.0, 4.5, 32, 36}, {1.0, 5.0, 32, 36}, {0.8, 5.0, 32, 32}, {0.8, 4.5, 32, 32}};
+  std::vector<cplx> al, b;
+  for (const auto& c : cand) {
+    double r = 0;
+    if (wide_candidate(X, delta, c[0], c[1], (int)c[2], c[3], al, b, &r)) {
+      store(al, b, r, X, c[1] * c[0], c[0], out);
+      return EO_OK;
+    }
+  }
+  return fail(EO_ERR_FIT, "no admissible wide-band rational approximant");
+}
+
 eo_status fit_for_band(double X, double delta, int nmax, Fit& out) {
   if (!(X > 0)) return fail(EO_ERR_INVALID_ARG, "band*tau must be positive");
+  if (X > 40.0) return fit_wide(X, delta, out);
   std::vector<cplx> al, b;
   for (int N = 5; N <= std::min(nmax, 301); N += 2) {
     const int M = (N - 1) / 2;

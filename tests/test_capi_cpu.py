@@ -75,3 +75,14 @@ def test_library_fit_for_a_band(capi):
     band, mod, tail = rational.check_contract(alpha, b, X, 1e-10)
     assert band <= 1e-10 and mod <= 1.0 + 1e-12
     assert alpha.size <= 41
+
+
+def test_wide_band_fit_meets_contract(capi):
+    # wide band (X = 300): pole line with end corrections, checked by the oracle
+    import paper_1402_5168_gb300 as eo
+    from oracle import rational
+    alpha, b, X = eo.fit(0, 300.0)
+    assert X == 300.0 and alpha.size < 4 * 300
+    band, mod, tail = rational.check_contract(alpha, b, X, 1e-10)
+    assert band <= 1e-10 and mod <= 1.0 + 1e-12 and tail < 1.0
+    assert np.array_equal(alpha[::-1], np.conj(alpha)) and np.array_equal(b[::-1], np.conj(b))
