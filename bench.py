@@ -30,6 +30,8 @@ UNIT = "applies/s"
 # FP64 fused multiply-add throughput measured on a GB300 of this machine (8 independent
 # FMA chains per thread, 1216 blocks x 256 threads, ~1995 MHz): 1.207 TFLOP/s
 FP64_PEAK_TFLOPS = 1.207
+# FP32 FMA throughput measured the same way: 75.4 TFLOP/s
+FP32_PEAK_TFLOPS = 75.4
 DEFAULT = W.SW_16X16_P16.name
 
 
@@ -89,6 +91,69 @@ class Clocks:
                 "samples": len(sm)}
 
 
+def build_operator(eo, w, g, x, y, R, precision, poles=0):
+    if w.kind == "wave":
+        c = W.wave_c(w, x, y)
+        return eo.Operator(g, eo.WAVE_DIRICHLET, band=W.BAND[w.name], n_poles=poles or w.n_poles, c2=c * c,
+                           max_rhs=R, precision=precision)
+    pr = w.params
+    return eo.Operator(g, eo.SW_WALLS, band=W.BAND[w.name], tau=w.tau, f=pr["f"], g=pr["g"], H=pr["H"],
+                       shared_ops=True, max_rhs=R, precision=precision)
+
+
+def timed_steps(torch, op, u, steps, stream, dist):
+    """K steps bracketed by barrier + synchronize, CUDA events on the launching stream."""
+    op.set_timing(True)
+    op.timing()
+    if dist:
+        dist.barrier()
+    torch.cuda.synchronize()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        op.apply(u, 1)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    if dist:
+        dist.barrier()
+    ms = e0.elapsed_time(e1)
+    tim = op.timing()
+    op.set_timing(False)
+    return ms, tim
+
+
+def roofline(op, w, R, tim, fp32, pk, pk_kind):
+    """k_down_leaf: [X|Y] blocks of every distinct pole read once, applied to R
+    columns per leaf (8 flops per complex multiply-add)."""
+    dl_n, dl_ms = tim["down_leaf"]
+    avg = dl_ms / max(dl_n, 1) / 1e3
+    q = w.p - 2
+    ni, nb = q * q, 4 * q
+    P = (op.alpha.size + 1) // 2
+    nleaf = w.nlx * w.nly
+    shared = w.kind == "sw"
+    nlo = 1 if shared else nleaf
+    esz = 8 if fp32 else 16
+    alg_bytes = P * nlo * ni * (ni + nb) * esz + P * nleaf * R * (2 * ni * 8 + nb * 16)
+    alg_flops = 8.0 * P * nleaf * R * ni * (ni + nb)
+    tf = alg_flops / avg / 1e12
+    gbs = alg_bytes / avg / 1e9
+    alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    # shared operators (one block per level, reused by every leaf) make the
+    # product compute-bound; per-box FP32 blocks are read once (HBM-bound);
+    # per-box FP64 blocks are limited by the FP64 pipe
+    if shared or not fp32:
+        rf = {"bound": "alu", "achieved": tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": tf / alu_peak,
+              "peak_source": ("FP32" if fp32 else "FP64") + " FMA microbenchmark on this pool's GB300 (DESIGN.md)"}
+    else:
+        rf = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+              "peak_source": pk_kind}
+    rf.update({"kernel": "k_down_leaf<%s>" % ("float2" if fp32 else "double2"), "traffic": None,
+               "algorithmic_flops": alg_flops, "algorithmic_bytes": alg_bytes, "hbm_achieved_gbs": gbs,
+               "hbm_frac": gbs / pk["hbm_gbs"], "avg_launch_ms": avg * 1e3, "launches": dl_n})
+    return rf
+
+
 def run_ours(args):
     import torch
     import paper_1402_5168_gb300 as eo
@@ -107,17 +172,11 @@ def run_ours(args):
     if args.leaves:
         w = W.dataclasses.replace(w, nlx=args.leaves, nly=args.leaves)
     R = args.rhs
+    fp32 = args.precision == "fp32"
     g = eo.Grid(w.nlx, w.nly, w.p)
     x, y = g.nodes()
     t0 = time.time()
-    if w.kind == "wave":
-        c = W.wave_c(w, x, y)
-        op = eo.Operator(g, eo.WAVE_DIRICHLET, band=W.BAND[w.name], n_poles=args.poles or w.n_poles, c2=c * c,
-                         max_rhs=R)
-    else:
-        pr = w.params
-        op = eo.Operator(g, eo.SW_WALLS, band=W.BAND[w.name], tau=w.tau, f=pr["f"], g=pr["g"], H=pr["H"],
-                         shared_ops=True, max_rhs=R)
+    op = build_operator(eo, w, g, x, y, R, args.precision, args.poles)
     torch.cuda.synchronize()
     build_s = time.time() - t0
     U0 = np.stack([np.stack(W.initial_fields(w, x, y, r)) for r in range(R)])
@@ -127,33 +186,16 @@ def run_ours(args):
     for _ in range(args.warmup):
         op.apply(u, 1)
     torch.cuda.synchronize()
-    op.set_timing(True)
-    op.timing()
-    if dist:
-        dist.barrier()
-    torch.cuda.synchronize()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    e0.record(stream)
-    for _ in range(args.steps):
-        op.apply(u, 1)
-    e1.record(stream)
-    torch.cuda.synchronize()
-    if dist:
-        dist.barrier()
-    ms = e0.elapsed_time(e1)
+    ms, tim = timed_steps(torch, op, u, args.steps, stream, dist)
     clocks = clk.stop() if clk else None
-    tim = op.timing()
-    op.set_timing(False)
     if dist:
         t = torch.tensor([ms], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         ms = float(t.item())
-    ms_step = ms / args.steps
     value = world * R * args.steps / (ms / 1e3)
     launches = sum(v[0] for v in tim.values())
     # end to end through the host entry point: H2D copy, apply, D2H copy each step
-    uh = torch.tensor(U0).pin_memory()
-    uh_np = uh.numpy()
+    uh_np = torch.tensor(U0).pin_memory().numpy()
     op.apply_host(uh_np, 1)
     torch.cuda.synchronize()
     t0 = time.perf_counter()
@@ -164,48 +206,49 @@ def run_ours(args):
         t = torch.tensor([e2e_s], device=dev)
         dist.all_reduce(t, op=dist.ReduceOp.MAX)
         e2e_s = float(t.item())
+    # the FP64 apply of the same workload beside the mixed one: throughput and
+    # the mixed path's error after the same number of steps from the same input
+    fp64 = None
+    if fp32 and args.compare_fp64:
+        op64 = build_operator(eo, w, g, x, y, R, "fp64", args.poles)
+        u64 = torch.tensor(U0, device=dev)
+        for _ in range(args.warmup):
+            op64.apply(u64, 1)
+        ms64, _ = timed_steps(torch, op64, u64, args.steps, stream, dist)
+        a = torch.tensor(U0, device=dev)
+        b = torch.tensor(U0, device=dev)
+        op.apply(a, args.steps)
+        op64.apply(b, args.steps)
+        err = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+        fp64 = {"value": world * R * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
+                "mixed_vs_fp64_rel_l2": err, "after_steps": args.steps}
+        del op64
     if rank != 0:
         dist.destroy_process_group()
         return
     pk, pk_kind = peaks()
-    dl_n, dl_ms = tim["down_leaf"]
-    avg = dl_ms / max(dl_n, 1) / 1e3
-    q = w.p - 2
-    ni, nb = q * q, 4 * q
-    P = (op.alpha.size + 1) // 2
-    nleaf = w.nlx * w.nly
-    nlo = 1 if w.kind == "sw" else nleaf
-    # algorithmic work of one k_down_leaf launch: every [X|Y] block of every
-    # distinct pole read once (16 B per complex entry) and applied to R columns
-    # (8 FP64 flops per complex multiply-add); vectors read / partials written once
-    entries = P * nlo * ni * (ni + nb)
-    alg_bytes = entries * 16 + P * nleaf * R * (2 * ni * 8 + nb * 16)
-    alg_flops = 8.0 * P * nleaf * R * ni * (ni + nb)
-    achieved_tf = alg_flops / avg / 1e12
-    achieved_gbs = alg_bytes / avg / 1e9
     ob, wb = op.memory()
-    shares = {k: round(v[1] / max(sum(t[1] for t in tim.values()), 1e-9), 4) for k, v in tim.items() if v[0]}
+    tot_ms = max(sum(t[1] for t in tim.values()), 1e-9)
+    shares = {k: round(v[1] / tot_ms, 4) for k, v in tim.items() if v[0]}
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms_step, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
         "config": {"workload": w.name, "kind": w.kind, "leaves": f"{w.nlx}x{w.nly}", "p": w.p,
-                   "n_poles": int(op.alpha.size), "distinct_poles": P, "tau": op.tau, "band_X": op.X,
-                   "rhs": R, "n_nodes": g.n_nodes, "operator_gb": ob / 1e9, "workspace_gb": wb / 1e9,
-                   "build_s": build_s, "parallelism": f"replicas x{world}",
+                   "precision": ("FP32 operator blocks and products, FP64 vectors, pole sum and maps" if fp32
+                                 else "FP64 throughout"),
+                   "n_poles": int(op.alpha.size), "distinct_poles": (op.alpha.size + 1) // 2, "tau": op.tau,
+                   "band_X": op.X, "rhs": R, "n_nodes": g.n_nodes, "operator_gb": ob / 1e9,
+                   "workspace_gb": wb / 1e9, "build_s": build_s, "parallelism": f"replicas x{world}",
                    "l2": f"operators ({ob / 1e9:.1f} GB) are re-read every step, larger than the 126 MB L2",
-                   "accuracy": "per-step relative L2 vs FP64 oracle: see tests/test_parity_gpu.py"},
+                   "fp64": fp64,
+                   "accuracy": "FP64 per-step relative L2 vs the FP64 oracle: tests/test_parity_gpu.py, "
+                               "tests/test_sw_config_gpu.py"},
         "e2e": {"value": world * R * args.steps / e2e_s, "unit": UNIT,
                 "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(U0.nbytes)},
         "gpu_launches": int(launches),
         "kernel_share": shares,
-        "roofline": {"bound": "alu", "kernel": "k_down_leaf", "achieved": achieved_tf, "peak": FP64_PEAK_TFLOPS,
-                     "unit": "TFLOP/s", "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
-                     "peak_source": "FP64 FMA microbenchmark on this pool's GB300 (DESIGN.md)",
-                     "algorithmic_flops": alg_flops, "algorithmic_bytes": alg_bytes,
-                     "hbm_achieved_gbs": achieved_gbs, "hbm_peak_gbs": pk["hbm_gbs"],
-                     "hbm_frac": achieved_gbs / pk["hbm_gbs"], "hbm_peak_source": pk_kind,
-                     "avg_launch_ms": avg * 1e3, "launches": dl_n},
+        "roofline": roofline(op, w, R, tim, fp32, pk, pk_kind),
         "clocks": clocks,
     }
     if args.cpu_baseline:
@@ -305,6 +348,8 @@ def main():
     ap.add_argument("--poles", type=int, default=0, help="override the pole count (profiling cases)")
     ap.add_argument("--leaves", type=int, default=0, help="override leaves per side (profiling cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     args = ap.parse_args()

@@ -59,7 +59,9 @@ typedef enum {
 } eo_kind;
 
 typedef enum {
-  EO_PREC_FP64 = 0 /* operators stored and applied in FP64 */
+  EO_PREC_FP64 = 0, /* operators stored and applied in FP64                         */
+  EO_PREC_FP32 = 1  /* operators built in FP64, stored in FP32; block products in FP32,
+                       vectors, pole sum and pre/post maps in FP64                   */
 } eo_precision;
 
 typedef struct eo_grid_s *eo_grid_t;

@@ -44,6 +44,16 @@ eo_status Handle::alloc(void** p, size_t bytes, bool op) {
   return EO_OK;
 }
 
+void Handle::release(void* p, size_t bytes, bool op) {
+  for (size_t i = 0; i < allocs.size(); ++i)
+    if (allocs[i] == p) {
+      cudaFree(p);
+      allocs.erase(allocs.begin() + i);
+      (op ? op_bytes : ws_bytes) -= (int64_t)bytes;
+      return;
+    }
+}
+
 }  // namespace eo
 
 namespace {
@@ -163,7 +173,7 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
     h.nroot = plan.lv[L].nbd;
     ops += P * (int64_t)h.nroot * h.nroot;
   }
-  const double op_gb = (double)ops * sizeof(cd) / 1e9;
+  const double op_gb = (double)ops * (o.precision == EO_PREC_FP32 ? sizeof(float2) : sizeof(cd)) / 1e9;
   if (o.mem_budget_gb > 0 && op_gb > o.mem_budget_gb)
     return fail(EO_ERR_BUDGET, "operators need " + std::to_string(op_gb) + " GB, over the budget");
   // ---- allocations: operators
@@ -275,7 +285,8 @@ eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double* coeff, c
   if (kind == EO_WAVE_DIRICHLET && !coeff) return fail(EO_ERR_INVALID_ARG, "wave kind needs c^2 at the nodes");
   if (kind == EO_WAVE_DIRICHLET && opts->shared_ops)
     return fail(EO_ERR_INVALID_ARG, "shared operators need constant coefficients (EO_SW_WALLS)");
-  if (opts->precision != EO_PREC_FP64) return fail(EO_ERR_UNSUPPORTED, "only FP64 operators are built");
+  if (opts->precision != EO_PREC_FP64 && opts->precision != EO_PREC_FP32)
+    return fail(EO_ERR_INVALID_ARG, "unknown precision");
   if (opts->max_rhs < 0) return fail(EO_ERR_INVALID_ARG, "max_rhs must be >= 1");
   if (kind == EO_WAVE_DIRICHLET)
     for (int64_t i = 0; i < grid->g.n_nodes; ++i)
@@ -291,6 +302,7 @@ eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double* coeff, c
   cudaStream_t st = (cudaStream_t)stream;
   eo_status rc = setup(h, *opts, st);
   if (!rc) rc = build(h, coeff, st);
+  if (!rc && opts->precision == EO_PREC_FP32) rc = to_fp32(h, st);
   if (rc) {
     delete hs;
     return rc;

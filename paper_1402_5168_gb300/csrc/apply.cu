@@ -33,12 +33,41 @@ __device__ __forceinline__ void cfma(cd& acc, cd a, cd b) {
   acc.y = fma(a.x, b.y, acc.y);
   acc.y = fma(a.y, b.x, acc.y);
 }
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// Operator storage type TA (double2: FP64; float2: FP32 operators, FP32
+// products and per-product sums).  Vectors enter the products in the same type;
+// results leave as FP64.
+template <typename TA> struct Cv;
+template <> struct Cv<double2> {
+  __device__ static double2 from(cd v) { return v; }
+  __device__ static cd to(double2 v) { return v; }
+  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
+};
+template <> struct Cv<float2> {
+  __device__ static float2 from(cd v) { return make_float2((float)v.x, (float)v.y); }
+  __device__ static cd to(float2 v) { return make_double2(v.x, v.y); }
+  __device__ static float2 zero() { return make_float2(0.f, 0.f); }
+};
+__device__ __forceinline__ float2 operator_ld(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 operator_ld(const double2* p) { return __ldg(p); }
+
+// 16-byte aligned pointer past n elements of T
+template <typename T>
+__device__ __forceinline__ cd* after(T* base, size_t n) {
+  return (cd*)(((uintptr_t)(base + n) + 15) & ~(uintptr_t)15);
+}
 
 // C[c][r] = sum_{j<k} A[r + j*lda] B[c][j]  for r < rows, c < NC.
 // Bs: shared [NC][kb]; Cs: shared [NC][rows]; red: shared [blockDim * NC].
-template <int NC>
-__device__ void cmv(const cd* __restrict__ A, int lda, int rows, int k, const cd* Bs, int kb,
-                    cd* Cs, cd* red) {
+template <int NC, typename TA>
+__device__ void cmv(const TA* __restrict__ A, int lda, int rows, int k, const TA* Bs, int kb,
+                    cd* Cs, TA* red) {
   const int nt = blockDim.x, t = threadIdx.x;
   int rp = (rows + 31) & ~31;
   if (rp > nt) rp = nt;
@@ -46,17 +75,17 @@ __device__ void cmv(const cd* __restrict__ A, int lda, int rows, int k, const cd
   const int ri = t % rp, kg = t / rp;
   for (int r0 = 0; r0 < rows; r0 += rp) {
     const int r = r0 + ri;
-    cd acc[NC];
+    TA acc[NC];
 #pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = make_double2(0.0, 0.0);
+    for (int c = 0; c < NC; ++c) acc[c] = Cv<TA>::zero();
     if (kg < ks && r < rows) {
-      const cd* Ar = A + r;
+      const TA* Ar = A + r;
       int j = kg;
       for (; j + 3 * ks < k; j += 4 * ks) {
-        const cd a0 = __ldg(Ar + (size_t)j * lda);
-        const cd a1 = __ldg(Ar + (size_t)(j + ks) * lda);
-        const cd a2 = __ldg(Ar + (size_t)(j + 2 * ks) * lda);
-        const cd a3 = __ldg(Ar + (size_t)(j + 3 * ks) * lda);
+        const TA a0 = operator_ld(Ar + (size_t)j * lda);
+        const TA a1 = operator_ld(Ar + (size_t)(j + ks) * lda);
+        const TA a2 = operator_ld(Ar + (size_t)(j + 2 * ks) * lda);
+        const TA a3 = operator_ld(Ar + (size_t)(j + 3 * ks) * lda);
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
           cfma(acc[c], a0, Bs[c * kb + j]);
@@ -66,7 +95,7 @@ __device__ void cmv(const cd* __restrict__ A, int lda, int rows, int k, const cd
         }
       }
       for (; j < k; j += ks) {
-        const cd a = __ldg(Ar + (size_t)j * lda);
+        const TA a = operator_ld(Ar + (size_t)j * lda);
 #pragma unroll
         for (int c = 0; c < NC; ++c) cfma(acc[c], a, Bs[c * kb + j]);
       }
@@ -74,7 +103,7 @@ __device__ void cmv(const cd* __restrict__ A, int lda, int rows, int k, const cd
     if (ks == 1) {
       if (r < rows)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) Cs[c * rows + r] = acc[c];
+        for (int c = 0; c < NC; ++c) Cs[c * rows + r] = Cv<TA>::to(acc[c]);
     } else {
       if (kg < ks)
 #pragma unroll
@@ -83,13 +112,13 @@ __device__ void cmv(const cd* __restrict__ A, int lda, int rows, int k, const cd
       if (kg == 0 && r < rows) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          cd s = red[c * rp + ri];
+          TA s = red[c * rp + ri];
           for (int g = 1; g < ks; ++g) {
-            const cd v = red[(g * NC + c) * rp + ri];
+            const TA v = red[(g * NC + c) * rp + ri];
             s.x += v.x;
             s.y += v.y;
           }
-          Cs[c * rows + r] = s;
+          Cs[c * rows + r] = Cv<TA>::to(s);
         }
       }
     }
@@ -119,16 +148,17 @@ __device__ __forceinline__ void col_box(int c, int R, int& box, int& r) {
 }
 
 // ---------------------------------------------------------------- up: leaves
-template <int NC>
-__global__ void __launch_bounds__(256) k_up_leaf(Sweep s, const cd* __restrict__ H, long long hps,
+template <int NC, typename TA>
+__global__ void __launch_bounds__(256) k_up_leaf(Sweep s, const void* Hv, long long hps,
                                                  long long hbs, int nleaf, cd* __restrict__ h0) {
   extern __shared__ cd smem[];
+  const TA* H = (const TA*)Hv;
   const int pl = blockIdx.y, p = s.p0 + pl;
   const int ncols = nleaf * s.R;
   const int c0 = blockIdx.x * NC;
-  cd* Bs = smem;
-  cd* Cs = Bs + NC * s.ni;
-  cd* red = Cs + NC * s.nb;
+  TA* Bs = (TA*)smem;
+  cd* Cs = after(Bs, (size_t)NC * s.ni);
+  TA* red = (TA*)(Cs + NC * s.nb);
   int box0, r0;
   col_box(c0, s.R, box0, r0);
   cd cf[3];
@@ -145,11 +175,11 @@ __global__ void __launch_bounds__(256) k_up_leaf(Sweep s, const cd* __restrict__
         g.y += cf[kk].y * v;
       }
     }
-    Bs[e] = g;
+    Bs[e] = Cv<TA>::from(g);
   }
   __syncthreads();
-  const cd* A = H + (long long)p * hps + (s.shared ? 0 : (long long)box0 * hbs);
-  cmv<NC>(A, s.nb, s.nb, s.ni, Bs, s.ni, Cs, red);
+  const TA* A = H + (long long)p * hps + (s.shared ? 0 : (long long)box0 * hbs);
+  cmv<NC, TA>(A, s.nb, s.nb, s.ni, Bs, s.ni, Cs, red);
   for (int e = threadIdx.x; e < NC * s.nb; e += blockDim.x) {
     const int c = e / s.nb, row = e - c * s.nb;
     if (c0 + c >= ncols) continue;
@@ -166,9 +196,9 @@ struct MergeArgs {
   const int* par_idx;
   const int* a3;
   const int* b3;
-  const cd* ZU;
+  const void* ZU;
   long long zps, zbs;
-  const cd* S;
+  const void* S;
   long long sps, sbs;
   const int* bseg;
   const int* iseg;
@@ -182,16 +212,16 @@ __device__ __forceinline__ void children(const MergeArgs& m, int box, int& ca, i
   else { ca = (2 * by) * m.nbx_c + bx; cb = ca + m.nbx_c; }
 }
 
-template <int NC>
+template <int NC, typename TA>
 __global__ void __launch_bounds__(256) k_up_merge(Sweep s, MergeArgs m, const cd* __restrict__ hin,
                                                   cd* __restrict__ hout) {
   extern __shared__ cd smem[];
   const int pl = blockIdx.y, p = s.p0 + pl;
   const int ncols = m.nbox * s.R;
   const int c0 = blockIdx.x * NC;
-  cd* Bs = smem;
-  cd* Cs = Bs + NC * m.n3;
-  cd* red = Cs + NC * m.zu_rows;
+  TA* Bs = (TA*)smem;
+  cd* Cs = after(Bs, (size_t)NC * m.n3);
+  TA* red = (TA*)(Cs + NC * m.zu_rows);
   for (int e = threadIdx.x; e < NC * m.n3; e += blockDim.x) {
     const int c = e / m.n3, t = e - c * m.n3;
     cd v = make_double2(0.0, 0.0);
@@ -203,13 +233,13 @@ __global__ void __launch_bounds__(256) k_up_merge(Sweep s, MergeArgs m, const cd
       const cd x = hr[(long long)ca * m.nbd_c + m.a3[t]], y = hr[(long long)cb * m.nbd_c + m.b3[t]];
       v = make_double2(x.x + y.x, x.y + y.y);
     }
-    Bs[e] = v;
+    Bs[e] = Cv<TA>::from(v);
   }
   __syncthreads();
   int box0, r0;
   col_box(c0, s.R, box0, r0);
-  const cd* A = m.ZU + (long long)p * m.zps + (s.shared ? 0 : (long long)box0 * m.zbs);
-  cmv<NC>(A, m.zu_rows, m.zu_rows, m.n3, Bs, m.n3, Cs, red);
+  const TA* A = (const TA*)m.ZU + (long long)p * m.zps + (s.shared ? 0 : (long long)box0 * m.zbs);
+  cmv<NC, TA>(A, m.zu_rows, m.zu_rows, m.n3, Bs, m.n3, Cs, red);
   for (int e = threadIdx.x; e < NC * m.zu_rows; e += blockDim.x) {
     const int c = e / m.zu_rows, row = e - c * m.zu_rows;
     if (c0 + c >= ncols) continue;
@@ -233,23 +263,23 @@ __global__ void __launch_bounds__(256) k_up_merge(Sweep s, MergeArgs m, const cd
 struct RootArgs {
   int n, q, sxq, syq;
   const int* bseg;
-  const cd* Binv;
+  const void* Binv;
   const cd* bcoef;   // [P][4][2]
   const cd* nu;      // [P][4]
   const double* state;
   int F;
 };
 
-template <int NC>
+template <int NC, typename TA>
 __global__ void __launch_bounds__(256) k_root_sw(Sweep s, RootArgs ra, const cd* __restrict__ hroot,
                                                  cd* __restrict__ E) {
   extern __shared__ cd smem[];
   const int pl = blockIdx.y, p = s.p0 + pl;
   const int c0 = blockIdx.x * NC;
   const int n = ra.n;
-  cd* Bs = smem;
-  cd* Cs = Bs + NC * n;
-  cd* red = Cs + NC * n;
+  TA* Bs = (TA*)smem;
+  cd* Cs = after(Bs, (size_t)NC * n);
+  TA* red = (TA*)(Cs + NC * n);
   for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
     const int c = e / n, i = e - c * n;
     cd v = make_double2(0.0, 0.0);
@@ -269,10 +299,10 @@ __global__ void __launch_bounds__(256) k_root_sw(Sweep s, RootArgs ra, const cd*
       const cd nh = cmul(nu, hr);
       v = make_double2(b0.x * F1 + b1.x * F2 - nh.x, b0.y * F1 + b1.y * F2 - nh.y);
     }
-    Bs[e] = v;
+    Bs[e] = Cv<TA>::from(v);
   }
   __syncthreads();
-  cmv<NC>(ra.Binv + (long long)p * n * n, n, n, n, Bs, n, Cs, red);
+  cmv<NC, TA>((const TA*)ra.Binv + (long long)p * n * n, n, n, n, Bs, n, Cs, red);
   for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
     const int c = e / n, i = e - c * n;
     const int r = c0 + c;
@@ -282,15 +312,15 @@ __global__ void __launch_bounds__(256) k_root_sw(Sweep s, RootArgs ra, const cd*
 }
 
 // ---------------------------------------------------------------- down: merges
-template <int NC>
+template <int NC, typename TA>
 __global__ void __launch_bounds__(256) k_down_merge(Sweep s, MergeArgs m, cd* __restrict__ E) {
   extern __shared__ cd smem[];
   const int pl = blockIdx.y, p = s.p0 + pl;
   const int ncols = m.nbox * s.R;
   const int c0 = blockIdx.x * NC;
-  cd* Bs = smem;
-  cd* Cs = Bs + NC * m.nbd;
-  cd* red = Cs + NC * m.n3;
+  TA* Bs = (TA*)smem;
+  cd* Cs = after(Bs, (size_t)NC * m.nbd);
+  TA* red = (TA*)(Cs + NC * m.n3);
   const int q = s.q;
   if (m.S) {
     for (int e = threadIdx.x; e < NC * m.nbd; e += blockDim.x) {
@@ -301,13 +331,13 @@ __global__ void __launch_bounds__(256) k_down_merge(Sweep s, MergeArgs m, cd* __
         col_box(c0 + c, s.R, box, r);
         v = E[((long long)pl * s.R + r) * s.n_edge + (long long)m.bseg[box * m.nseg + i / q] * q + (i % q)];
       }
-      Bs[e] = v;
+      Bs[e] = Cv<TA>::from(v);
     }
     __syncthreads();
     int box0, r0;
     col_box(c0, s.R, box0, r0);
-    const cd* A = m.S + (long long)p * m.sps + (s.shared ? 0 : (long long)box0 * m.sbs);
-    cmv<NC>(A, m.n3, m.n3, m.nbd, Bs, m.nbd, Cs, red);
+    const TA* A = (const TA*)m.S + (long long)p * m.sps + (s.shared ? 0 : (long long)box0 * m.sbs);
+    cmv<NC, TA>(A, m.n3, m.n3, m.nbd, Bs, m.nbd, Cs, red);
   }
   const int n3s = m.n3 / q;
   for (int e = threadIdx.x; e < NC * m.n3; e += blockDim.x) {
@@ -325,8 +355,8 @@ __global__ void __launch_bounds__(256) k_down_merge(Sweep s, MergeArgs m, cd* __
 }
 
 // ---------------------------------------------------------------- down: leaves + pole sum
-template <int NC>
-__global__ void __launch_bounds__(256) k_down_leaf(Sweep s, const cd* __restrict__ XY, long long xps,
+template <int NC, typename TA>
+__global__ void __launch_bounds__(256) k_down_leaf(Sweep s, const void* XYv, long long xps,
                                                    long long xbs, const int* __restrict__ bseg, int nleaf,
                                                    int ppc, const cd* __restrict__ E,
                                                    double* __restrict__ part) {
@@ -335,10 +365,11 @@ __global__ void __launch_bounds__(256) k_down_leaf(Sweep s, const cd* __restrict
   const int ncols = nleaf * s.R;
   const int c0 = blockIdx.x * NC;
   const int chunk = blockIdx.y;
-  cd* Bs = smem;
-  cd* Cs = Bs + NC * k;
-  cd* red = Cs + NC * ni;
-  double* acc = (double*)(red + blockDim.x * NC);   // [NC][K][ni]
+  const TA* XY = (const TA*)XYv;
+  TA* Bs = (TA*)smem;
+  cd* Cs = after(Bs, (size_t)NC * k);
+  TA* red = (TA*)(Cs + NC * ni);
+  double* acc = (double*)after(red, (size_t)blockDim.x * NC);   // [NC][K][ni]
   for (int e = threadIdx.x; e < NC * s.K * ni; e += blockDim.x) acc[e] = 0.0;
   int box0, r0;
   col_box(c0, s.R, box0, r0);
@@ -365,11 +396,11 @@ __global__ void __launch_bounds__(256) k_down_leaf(Sweep s, const cd* __restrict
           v = E[((long long)pl * s.R + r) * s.n_edge + (long long)bseg[box * 4 + i / q] * q + (i % q)];
         }
       }
-      Bs[e] = v;
+      Bs[e] = Cv<TA>::from(v);
     }
     __syncthreads();
-    const cd* A = XY + (long long)p * xps + (s.shared ? 0 : (long long)box0 * xbs);
-    cmv<NC>(A, ni, ni, k, Bs, k, Cs, red);
+    const TA* A = XY + (long long)p * xps + (s.shared ? 0 : (long long)box0 * xbs);
+    cmv<NC, TA>(A, ni, ni, k, Bs, k, Cs, red);
     cd w[3];
     for (int kk = 0; kk < s.K; ++kk) w[kk] = s.wgt[p * s.K + kk];
     for (int e = threadIdx.x; e < NC * ni; e += blockDim.x) {
@@ -640,13 +671,21 @@ int pick_nc(int shared, int R, int k, int rows) {
   return nc;
 }
 
-template <template <int> class Launcher, typename... Args>
-eo_status dispatch(int nc, Args&&... args) {
+template <template <int, typename> class Launcher, typename... Args>
+eo_status dispatch(int fp32, int nc, Args&&... args) {
+  if (fp32) {
+    switch (nc) {
+      case 1: return Launcher<1, float2>::run(args...);
+      case 2: return Launcher<2, float2>::run(args...);
+      case 4: return Launcher<4, float2>::run(args...);
+      default: return Launcher<8, float2>::run(args...);
+    }
+  }
   switch (nc) {
-    case 1: return Launcher<1>::run(args...);
-    case 2: return Launcher<2>::run(args...);
-    case 4: return Launcher<4>::run(args...);
-    default: return Launcher<8>::run(args...);
+    case 1: return Launcher<1, double2>::run(args...);
+    case 2: return Launcher<2, double2>::run(args...);
+    case 4: return Launcher<4, double2>::run(args...);
+    default: return Launcher<8, double2>::run(args...);
   }
 }
 
@@ -656,64 +695,64 @@ eo_status dispatch(int nc, Args&&... args) {
       EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes))); \
   } while (0)
 
-template <int NC>
+template <int NC, typename TA>
 struct UpLeaf {
   static eo_status run(const Sweep& s, const Handle& h, int nleaf, cd* h0, cudaStream_t st) {
     const int ncols = nleaf * s.R;
     dim3 grid((ncols + NC - 1) / NC, s.P);
-    const size_t smem = sizeof(cd) * ((size_t)NC * (s.ni + s.nb) + 256 * NC);
-    EO_SET_SMEM(k_up_leaf<NC>, smem);
-    k_up_leaf<NC><<<grid, 256, smem, st>>>(s, h.H, h.h_pstride, h.h_bstride, nleaf, h0);
+    const size_t smem = sizeof(cd) * ((size_t)NC * (s.ni + s.nb) + 256 * NC) + 64;
+    EO_SET_SMEM((k_up_leaf<NC, TA>), smem);
+    k_up_leaf<NC, TA><<<grid, 256, smem, st>>>(s, h.aH, h.h_pstride, h.h_bstride, nleaf, h0);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
 };
 
-template <int NC>
+template <int NC, typename TA>
 struct UpMerge {
   static eo_status run(const Sweep& s, const MergeArgs& m, const cd* hin, cd* hout, cudaStream_t st) {
     dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
-    const size_t smem = sizeof(cd) * ((size_t)NC * (m.n3 + m.zu_rows) + 256 * NC);
-    EO_SET_SMEM(k_up_merge<NC>, smem);
-    k_up_merge<NC><<<grid, 256, smem, st>>>(s, m, hin, hout);
+    const size_t smem = sizeof(cd) * ((size_t)NC * (m.n3 + m.zu_rows) + 256 * NC) + 64;
+    EO_SET_SMEM((k_up_merge<NC, TA>), smem);
+    k_up_merge<NC, TA><<<grid, 256, smem, st>>>(s, m, hin, hout);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
 };
 
-template <int NC>
+template <int NC, typename TA>
 struct DownMerge {
   static eo_status run(const Sweep& s, const MergeArgs& m, cd* E, cudaStream_t st) {
     dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
-    const size_t smem = sizeof(cd) * ((size_t)NC * (m.nbd + m.n3) + 256 * NC);
-    EO_SET_SMEM(k_down_merge<NC>, smem);
-    k_down_merge<NC><<<grid, 256, smem, st>>>(s, m, E);
+    const size_t smem = sizeof(cd) * ((size_t)NC * (m.nbd + m.n3) + 256 * NC) + 64;
+    EO_SET_SMEM((k_down_merge<NC, TA>), smem);
+    k_down_merge<NC, TA><<<grid, 256, smem, st>>>(s, m, E);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
 };
 
-template <int NC>
+template <int NC, typename TA>
 struct RootSW {
   static eo_status run(const Sweep& s, const RootArgs& ra, const cd* hroot, cd* E, cudaStream_t st) {
     dim3 grid((s.R + NC - 1) / NC, s.P);
-    const size_t smem = sizeof(cd) * ((size_t)NC * 2 * ra.n + 256 * NC);
-    EO_SET_SMEM(k_root_sw<NC>, smem);
-    k_root_sw<NC><<<grid, 256, smem, st>>>(s, ra, hroot, E);
+    const size_t smem = sizeof(cd) * ((size_t)NC * 2 * ra.n + 256 * NC) + 64;
+    EO_SET_SMEM((k_root_sw<NC, TA>), smem);
+    k_root_sw<NC, TA><<<grid, 256, smem, st>>>(s, ra, hroot, E);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
 };
 
-template <int NC>
+template <int NC, typename TA>
 struct DownLeaf {
   static eo_status run(const Sweep& s, const Handle& h, int nleaf, int nchunk, int ppc, const cd* E,
                        double* part, cudaStream_t st) {
     dim3 grid((nleaf * s.R + NC - 1) / NC, nchunk);
     const size_t smem = sizeof(cd) * ((size_t)NC * (s.ni + s.nb + s.ni) + 256 * NC) +
-                        sizeof(double) * NC * s.K * s.ni;
-    EO_SET_SMEM(k_down_leaf<NC>, smem);
-    k_down_leaf<NC><<<grid, 256, smem, st>>>(s, h.XY, h.xy_pstride, h.xy_bstride, h.lv[0].bseg, nleaf, ppc,
+                        sizeof(double) * NC * s.K * s.ni + 64;
+    EO_SET_SMEM((k_down_leaf<NC, TA>), smem);
+    k_down_leaf<NC, TA><<<grid, 256, smem, st>>>(s, h.aXY, h.xy_pstride, h.xy_bstride, h.lv[0].bseg, nleaf, ppc,
                                             E, part);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
@@ -727,8 +766,8 @@ MergeArgs merge_args(const Handle& h, int l) {
   m.nbox = ld.nbox; m.nbx = ld.nbx; m.nbx_c = lc.nbx; m.nbox_c = lc.nbox; m.dir = ld.dir;
   m.nbd = ld.nbd; m.nbd_c = lc.nbd; m.n3 = ld.n3; m.zu_rows = ld.zu_rows;
   m.par_child = ld.par_child; m.par_idx = ld.par_idx; m.a3 = ld.a3; m.b3 = ld.b3;
-  m.ZU = ld.ZU; m.zps = ld.zu_pstride; m.zbs = ld.zu_bstride;
-  m.S = ld.S; m.sps = ld.s_pstride; m.sbs = ld.s_bstride;
+  m.ZU = ld.aZU; m.zps = ld.zu_pstride; m.zbs = ld.zu_bstride;
+  m.S = ld.aS; m.sps = ld.s_pstride; m.sbs = ld.s_bstride;
   m.bseg = ld.bseg; m.iseg = ld.iseg; m.nseg = ld.nseg; m.w3 = ld.w3;
   return m;
 }
@@ -770,29 +809,29 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   cd* hcur = h.hA;
   cd* hnext = h.hB;
   if ((rc = h.trace_begin(st))) return rc;
-  if ((rc = dispatch<UpLeaf>(pick_nc(h.shared, R, ni, nb), s, h, nleaf, hcur, st))) return rc;
+  if ((rc = dispatch<UpLeaf>(h.fp32, pick_nc(h.shared, R, ni, nb), s, h, nleaf, hcur, st))) return rc;
   if ((rc = h.trace_end(TR_UP_LEAF, st))) return rc;
   // up: merges
   for (int l = 1; l <= L; ++l) {
     MergeArgs m = merge_args(h, l);
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<UpMerge>(pick_nc(h.shared, R, m.n3, m.zu_rows), s, m, hcur, hnext, st))) return rc;
+    if ((rc = dispatch<UpMerge>(h.fp32, pick_nc(h.shared, R, m.n3, m.zu_rows), s, m, hcur, hnext, st))) return rc;
     if ((rc = h.trace_end(TR_UP_MERGE, st))) return rc;
     std::swap(hcur, hnext);
   }
   // root
   if (h.kind == EO_SW_WALLS) {
     const Level& rl = h.plan.lv[L];
-    RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.Binv, h.bcoef, h.nu, uin, 3};
+    RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, uin, 3};
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<RootSW>(pick_nc(0, R, rl.nbd, rl.nbd), s, ra, hcur, h.E, st))) return rc;
+    if ((rc = dispatch<RootSW>(h.fp32, pick_nc(0, R, rl.nbd, rl.nbd), s, ra, hcur, h.E, st))) return rc;
     if ((rc = h.trace_end(TR_ROOT, st))) return rc;
   }
   // down: merges
   for (int l = L; l >= 1; --l) {
     MergeArgs m = merge_args(h, l);
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<DownMerge>(pick_nc(h.shared, R, m.nbd, m.n3), s, m, h.E, st))) return rc;
+    if ((rc = dispatch<DownMerge>(h.fp32, pick_nc(h.shared, R, m.nbd, m.n3), s, m, h.E, st))) return rc;
     if ((rc = h.trace_end(TR_DOWN_MERGE, st))) return rc;
   }
   // down: leaves with the pole sum
@@ -803,7 +842,7 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   const int ppc = (np + nchunk - 1) / nchunk;
   nchunk = (np + ppc - 1) / ppc;
   if ((rc = h.trace_begin(st))) return rc;
-  if ((rc = dispatch<DownLeaf>(nc, s, h, nleaf, nchunk, ppc, h.E, h.part, st))) return rc;
+  if ((rc = dispatch<DownLeaf>(h.fp32, nc, s, h, nleaf, nchunk, ppc, h.E, h.part, st))) return rc;
   if ((rc = h.trace_end(TR_DOWN_LEAF, st))) return rc;
   if ((rc = h.trace_begin(st))) return rc;
   k_edge_acc<<<(unsigned)std::max<long long>(1, std::min<long long>(4096, (R * g.n_edge + 255) / 256)), 256, 0, st>>>(

@@ -479,6 +479,49 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
     }
   }
   EO_CUDA_TRY(cudaStreamSynchronize(st));
+  h.aH = h.H;
+  h.aXY = h.XY;
+  h.aBinv = h.Binv;
+  for (size_t l = 1; l < h.lv.size(); ++l) {
+    h.lv[l].aZU = h.lv[l].ZU;
+    h.lv[l].aS = h.lv[l].S;
+  }
+  return EO_OK;
+}
+
+// ---------------------------------------------------------------- FP32 operator copies
+__global__ void to_float2(size_t n, const cd* __restrict__ x, float2* __restrict__ y) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
+    y[t] = make_float2((float)x[t].x, (float)x[t].y);
+}
+
+// Replace every FP64 operator block by an FP32 copy (rounded to nearest); the
+// apply then multiplies in FP32 and keeps vectors, pole sums and maps in FP64.
+eo_status to_fp32(Handle& h, cudaStream_t st) {
+  auto conv = [&](cd*& src, size_t n, const void** view) -> eo_status {
+    if (!src) { *view = nullptr; return EO_OK; }
+    float2* dst;
+    eo_status rc = h.alloc((void**)&dst, sizeof(float2) * n, true);
+    if (rc) return rc;
+    to_float2<<<4096, 256, 0, st>>>(n, src, dst);
+    EO_CUDA_TRY(cudaGetLastError());
+    EO_CUDA_TRY(cudaStreamSynchronize(st));
+    h.release(src, sizeof(cd) * n, true);
+    src = nullptr;
+    *view = dst;
+    return EO_OK;
+  };
+  eo_status rc;
+  const size_t P = h.P;
+  if ((rc = conv(h.H, P * h.h_pstride, &h.aH))) return rc;
+  if ((rc = conv(h.XY, P * h.xy_pstride, &h.aXY))) return rc;
+  for (size_t l = 1; l < h.lv.size(); ++l) {
+    LevelDev& ld = h.lv[l];
+    if ((rc = conv(ld.ZU, P * ld.zu_pstride, &ld.aZU))) return rc;
+    if ((rc = conv(ld.S, P * ld.s_pstride, &ld.aS))) return rc;
+  }
+  if ((rc = conv(h.Binv, P * (size_t)h.nroot * h.nroot, &h.aBinv))) return rc;
+  h.fp32 = 1;
   return EO_OK;
 }
 

@@ -35,6 +35,8 @@ struct LevelDev {
   cd* S = nullptr;              // n3 x nbd (absent at a Dirichlet root)
   int64_t zu_pstride = 0, zu_bstride = 0, s_pstride = 0, s_bstride = 0;
   cd* w3 = nullptr;             // workspace [pole][rhs][nbox][n3]
+  const void* aZU = nullptr;    // operators the apply reads (FP64 above, or FP32 copies)
+  const void* aS = nullptr;
 };
 
 struct Handle {
@@ -58,6 +60,10 @@ struct Handle {
   // root oblique solve (EO_SW_WALLS): Binv [pole][nroot x nroot]
   cd* Binv = nullptr;
   int nroot = 0;
+  int fp32 = 0;                 // operators stored and multiplied in FP32
+  const void* aH = nullptr;     // operators the apply reads
+  const void* aXY = nullptr;
+  const void* aBinv = nullptr;
   std::vector<LevelDev> lv;
   // per-pole coefficient tables (device, complex): pre-map coefficients [P][K],
   // accumulation weights [P][K], wall rhs coefficients [P][4 sides][2],
@@ -92,11 +98,13 @@ struct Handle {
 
   ~Handle();
   eo_status alloc(void** p, size_t bytes, bool op);
+  void release(void* p, size_t bytes, bool op);
 };
 
 enum { TR_PRE = 0, TR_UP_LEAF, TR_UP_MERGE, TR_ROOT, TR_DOWN_MERGE, TR_DOWN_LEAF, TR_EDGE, TR_POST, TR_N };
 
 eo_status build(Handle& h, const double* coeff, cudaStream_t st);
+eo_status to_fp32(Handle& h, cudaStream_t st);
 eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st);
 eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStream_t st);
 eo_status apply_resolvent_noalloc(Handle& h, int j, const double* u, double* x, cudaStream_t st);
