@@ -122,7 +122,7 @@ def timed_steps(torch, op, u, steps, stream, dist):
     return ms, tim
 
 
-def roofline(op, w, R, tim, fp32, pk, pk_kind):
+def roofline(op, w, R, tim, prec, pk, pk_kind):
     """k_down_leaf: [X|Y] blocks of every distinct pole read once, applied to R
     columns per leaf (8 flops per complex multiply-add)."""
     dl_n, dl_ms = tim["down_leaf"]
@@ -133,22 +133,30 @@ def roofline(op, w, R, tim, fp32, pk, pk_kind):
     nleaf = w.nlx * w.nly
     shared = w.kind == "sw"
     nlo = 1 if shared else nleaf
-    esz = 8 if fp32 else 16
+    esz = 8 if prec == "fp32" else 16
     alg_bytes = P * nlo * ni * (ni + nb) * esz + P * nleaf * R * (2 * ni * 8 + nb * 16)
     alg_flops = 8.0 * P * nleaf * R * ni * (ni + nb)
     tf = alg_flops / avg / 1e12
     gbs = alg_bytes / avg / 1e9
-    alu_peak = FP32_PEAK_TFLOPS if fp32 else FP64_PEAK_TFLOPS
+    # FP32-pair products cost 48 FP32 instructions per complex multiply-add
+    # (4 split products of 12), so their pipe bound in FP64-equivalent flops
+    # (8 per complex multiply-add) is FP32_peak / 2 / 48 * 8
+    alu_peak = {"fp32": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS,
+                "df32": FP32_PEAK_TFLOPS / 2 / 48 * 8}[prec]
+    src = {"fp32": "FP32 FMA microbenchmark", "fp64": "FP64 FMA microbenchmark",
+           "df32": "FP32 FMA microbenchmark, 48 FP32 instructions per FP32-pair complex multiply-add"}[prec]
     # shared operators (one block per level, reused by every leaf) make the
     # product compute-bound; per-box FP32 blocks are read once (HBM-bound);
     # per-box FP64 blocks are limited by the FP64 pipe
-    if shared or not fp32:
-        rf = {"bound": "alu", "achieved": tf, "peak": alu_peak, "unit": "TFLOP/s", "frac": tf / alu_peak,
-              "peak_source": ("FP32" if fp32 else "FP64") + " FMA microbenchmark on this pool's GB300 (DESIGN.md)"}
+    if shared or prec != "fp32":
+        rf = {"bound": "alu", "achieved": tf, "peak": alu_peak,
+              "unit": "TFLOP/s" + (" (FP64-equivalent)" if prec == "df32" else ""), "frac": tf / alu_peak,
+              "peak_source": src + " on this pool's GB300 (DESIGN.md)"}
     else:
         rf = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
               "peak_source": pk_kind}
-    rf.update({"kernel": "k_down_leaf<%s>" % ("float2" if fp32 else "double2"), "traffic": None,
+    rf.update({"kernel": "k_down_leaf<%s>" % {"fp32": "float2", "fp64": "double2", "df32": "float4"}[prec],
+               "traffic": None,
                "algorithmic_flops": alg_flops, "algorithmic_bytes": alg_bytes, "hbm_achieved_gbs": gbs,
                "hbm_frac": gbs / pk["hbm_gbs"], "avg_launch_ms": avg * 1e3, "launches": dl_n})
     return rf
@@ -172,7 +180,7 @@ def run_ours(args):
     if args.leaves:
         w = W.dataclasses.replace(w, nlx=args.leaves, nly=args.leaves)
     R = args.rhs
-    fp32 = args.precision == "fp32"
+    reduced = args.precision != "fp64"
     g = eo.Grid(w.nlx, w.nly, w.p)
     x, y = g.nodes()
     t0 = time.time()
@@ -209,7 +217,7 @@ def run_ours(args):
     # the FP64 apply of the same workload beside the mixed one: throughput and
     # the mixed path's error after the same number of steps from the same input
     fp64 = None
-    if fp32 and args.compare_fp64:
+    if reduced and args.compare_fp64:
         op64 = build_operator(eo, w, g, x, y, R, "fp64", args.poles)
         u64 = torch.tensor(U0, device=dev)
         for _ in range(args.warmup):
@@ -233,10 +241,13 @@ def run_ours(args):
     out = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
-        "vs_baseline": None, "dtype": "f32" if fp32 else "f64", "data": "synthetic",
+        "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "df32": "f32x2"}[args.precision],
+        "data": "synthetic",
         "config": {"workload": w.name, "kind": w.kind, "leaves": f"{w.nlx}x{w.nly}", "p": w.p,
-                   "precision": ("FP32 operator blocks and products, FP64 vectors, pole sum and maps" if fp32
-                                 else "FP64 throughout"),
+                   "precision": {"fp32": "FP32 operator blocks and products; FP64 vectors, pole sum, maps",
+                                 "df32": "FP32-pair (hi, lo) operator blocks, exact split products and "
+                                         "compensated sums on the FP32 pipe; FP64 vectors, pole sum, maps",
+                                 "fp64": "FP64 throughout"}[args.precision],
                    "n_poles": int(op.alpha.size), "distinct_poles": (op.alpha.size + 1) // 2, "tau": op.tau,
                    "band_X": op.X, "rhs": R, "n_nodes": g.n_nodes, "operator_gb": ob / 1e9,
                    "workspace_gb": wb / 1e9, "build_s": build_s, "parallelism": f"replicas x{world}",
@@ -248,7 +259,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(U0.nbytes)},
         "gpu_launches": int(launches),
         "kernel_share": shares,
-        "roofline": roofline(op, w, R, tim, fp32, pk, pk_kind),
+        "roofline": roofline(op, w, R, tim, args.precision, pk, pk_kind),
         "clocks": clocks,
     }
     if args.cpu_baseline:
@@ -348,7 +359,7 @@ def main():
     ap.add_argument("--poles", type=int, default=0, help="override the pole count (profiling cases)")
     ap.add_argument("--leaves", type=int, default=0, help="override leaves per side (profiling cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--precision", default="fp32", choices=["fp32", "fp64"])
+    ap.add_argument("--precision", default="df32", choices=["df32", "fp32", "fp64"])
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=30.0)

@@ -60,8 +60,11 @@ typedef enum {
 
 typedef enum {
   EO_PREC_FP64 = 0, /* operators stored and applied in FP64                         */
-  EO_PREC_FP32 = 1  /* operators built in FP64, stored in FP32; block products in FP32,
+  EO_PREC_FP32 = 1, /* operators built in FP64, stored in FP32; block products in FP32,
                        vectors, pole sum and pre/post maps in FP64                   */
+  EO_PREC_DF32 = 2  /* operators built in FP64, stored as FP32 (hi, lo) pairs (same
+                       bytes as FP64, ~2^-48 relative); block products on the FP32
+                       pipe with exact product splitting and compensated sums     */
 } eo_precision;
 
 typedef struct eo_grid_s *eo_grid_t;
@@ -81,6 +84,8 @@ typedef struct {
                           constant coefficients; EO_SW_WALLS); 0: one per box     */
   int max_rhs;         /* largest n_rhs that eo_apply will be called with (>=1)   */
   double mem_budget_gb;/* cap on operator storage in GB (0: no cap)               */
+  int fp64_top_levels; /* EO_PREC_FP32/DF32: this many top merge levels, and then also the
+                          root wall solve, keep FP64 operators (0: all FP32)       */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.
@@ -137,6 +142,14 @@ eo_status eo_memory(eo_handle_t h, int64_t *operator_bytes, int64_t *workspace_b
  * Errors: EO_ERR_INVALID_ARG, EO_ERR_CUDA (launch errors only; asynchronous
  * faults surface at the caller's next synchronisation). */
 eo_status eo_apply(eo_handle_t h, double *u_dev, int n_rhs, int n_steps, void *stream);
+
+/* Adjoint of the step: y <- (G^T)^n_steps y, G the real linear map of one
+ * eo_apply step (transpose for the Euclidean inner product of the state vector):
+ * the forward sweeps run backwards with every stored block transposed
+ * (conjugate-pole form of Section 3.3 kept).  Layout, stream and errors as
+ * eo_apply.  EO_WAVE_DIRICHLET only (EO_ERR_UNSUPPORTED otherwise).  The first
+ * call allocates a seed buffer of P * max_rhs * n_interior complex values. */
+eo_status eo_apply_adjoint(eo_handle_t h, double *y_dev, int n_rhs, int n_steps, void *stream);
 
 /* Same as eo_apply for a state in HOST memory (pinned or pageable): copies in,
  * applies, copies back and synchronises the stream before returning. */

@@ -161,6 +161,54 @@ class Stepper:
         return out
 
 
+def step_matrix(stepper: Stepper) -> np.ndarray:
+    """Dense real matrix G of one step, column by column (G e_j): the plainest
+    definition of the step's transpose is G.T.  Small grids only."""
+    shape = (stepper.prob.n_fields, stepper.prob.grid.n_nodes)
+    n = shape[0] * shape[1]
+    G = np.zeros((n, n))
+    for j in range(n):
+        e = np.zeros(n)
+        e[j] = 1.0
+        G[:, j] = stepper.step(e.reshape(shape)).ravel()
+    return G
+
+
+def adjoint_step(stepper: Stepper, y: np.ndarray) -> np.ndarray:
+    """G^T y for the real step G of Stepper.step (wave kind), factor by factor.
+
+    With s_p = P_int (alpha_p f_v + tau A f_u) / tau^2, w_p = B_p^{-1} s_p,
+    v_out = Re sum_p c_p w_p and u_out = Re sum_p (c_p tau / alpha_p) w_p - C0 f_u
+    (C0 = Re sum_p c_p / alpha_p, c_p the conjugate-pair weights of Section 3.3),
+    the transpose for a real seed y = (y_u, y_v) is, with the bilinear pairing,
+      zeta_p = B_p^{-T} (c_p y_v + (c_p tau / alpha_p) y_u),
+      u_bar = Re sum_p A^T P_int zeta_p / tau - C0 y_u,
+      v_bar = Re sum_p alpha_p P_int zeta_p / tau^2.
+    """
+    prob = stepper.prob
+    if prob.kind != "wave":
+        raise NotImplementedError("adjoint_step: wave kind")
+    tau = prob.tau
+    yu, yv = y
+    ub = np.zeros(prob.grid.n_nodes)
+    vb = np.zeros(prob.grid.n_nodes)
+    C0 = 0.0
+    inter = (prob.cls == 0).astype(float)
+    for i in range(stepper.alpha.size):
+        a = stepper.alpha[i]
+        if a.imag < 0:
+            continue
+        c = (1.0 if a.imag == 0 else 2.0) * stepper.b[i]
+        z = c * yv + (c * tau / a) * yu
+        zeta = stepper._solver(i).solve(z.astype(np.complex128), trans="T")
+        pz = inter * zeta
+        ub += (prob.Lap.T @ pz).real / tau
+        vb += (a * pz).real / tau ** 2
+        C0 += (c / a).real
+    ub -= C0 * yu
+    return np.stack([ub, vb])
+
+
 def conjugate_closed(alpha, b, tol=0.0) -> bool:
     """True when the multiset {(alpha, b)} is closed under conjugation."""
     alpha = np.asarray(alpha)

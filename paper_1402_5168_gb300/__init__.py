@@ -70,11 +70,12 @@ class Operator:
 
     def __init__(self, grid: Grid, kind: int, band: float, n_poles: int = 0, tau: float = 0.0,
                  c2=None, f=0.0, g=1.0, H=1.0, delta=1e-10, shared_ops=False, max_rhs=1,
-                 mem_budget_gb=0.0, precision="fp64", stream=None):
+                 mem_budget_gb=0.0, precision="fp64", fp64_top_levels=0, stream=None):
         L = _capi.lib()
-        prec = {"fp64": 0, "fp32": 1}[precision]
+        prec = {"fp64": 0, "fp32": 1, "df32": 2}[precision]
         o = Opts(n_poles=n_poles, band=band, tau=tau, delta=delta, sw_f=f, sw_g=g, sw_H=H, precision=prec,
-                 shared_ops=int(shared_ops), max_rhs=max_rhs, mem_budget_gb=mem_budget_gb)
+                 shared_ops=int(shared_ops), max_rhs=max_rhs, mem_budget_gb=mem_budget_gb,
+                 fp64_top_levels=fp64_top_levels)
         coeff = None
         if c2 is not None:
             self._c2 = np.ascontiguousarray(c2, dtype=np.float64)
@@ -110,6 +111,14 @@ class Operator:
             raise ValueError(f"state shape must end with ({self.fields}, {self.grid.n_nodes})")
         check(_capi.lib().eo_apply(self._h, C.c_void_p(u.data_ptr()), n_rhs, n_steps, _stream_ptr(stream)))
         return u
+
+    def apply_adjoint(self, y, n_steps=1, stream=None):
+        """y <- (G^T)^n_steps y in place (G = one apply step); same layout as apply."""
+        if not (y.is_cuda and y.element_size() == 8 and y.is_contiguous()):
+            raise ValueError("y must be a contiguous CUDA float64 tensor")
+        n_rhs = 1 if y.dim() == 2 else y.shape[0]
+        check(_capi.lib().eo_apply_adjoint(self._h, C.c_void_p(y.data_ptr()), n_rhs, n_steps, _stream_ptr(stream)))
+        return y
 
     def apply_host(self, u: np.ndarray, n_steps=1, stream=None):
         """Same as apply for a host float64 array (copies in and out inside the call)."""

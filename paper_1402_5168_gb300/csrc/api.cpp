@@ -285,7 +285,7 @@ eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double* coeff, c
   if (kind == EO_WAVE_DIRICHLET && !coeff) return fail(EO_ERR_INVALID_ARG, "wave kind needs c^2 at the nodes");
   if (kind == EO_WAVE_DIRICHLET && opts->shared_ops)
     return fail(EO_ERR_INVALID_ARG, "shared operators need constant coefficients (EO_SW_WALLS)");
-  if (opts->precision != EO_PREC_FP64 && opts->precision != EO_PREC_FP32)
+  if (opts->precision != EO_PREC_FP64 && opts->precision != EO_PREC_FP32 && opts->precision != EO_PREC_DF32)
     return fail(EO_ERR_INVALID_ARG, "unknown precision");
   if (opts->max_rhs < 0) return fail(EO_ERR_INVALID_ARG, "max_rhs must be >= 1");
   if (kind == EO_WAVE_DIRICHLET)
@@ -302,7 +302,7 @@ eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double* coeff, c
   cudaStream_t st = (cudaStream_t)stream;
   eo_status rc = setup(h, *opts, st);
   if (!rc) rc = build(h, coeff, st);
-  if (!rc && opts->precision == EO_PREC_FP32) rc = to_fp32(h, st);
+  if (!rc && opts->precision != EO_PREC_FP64) rc = to_reduced(h, opts->precision, st);
   if (rc) {
     delete hs;
     return rc;
@@ -353,6 +353,11 @@ eo_status eo_memory(eo_handle_t hd, int64_t* operator_bytes, int64_t* workspace_
 eo_status eo_apply(eo_handle_t hd, double* u_dev, int n_rhs, int n_steps, void* stream) {
   if (!hd) return fail(EO_ERR_INVALID_ARG, "null handle");
   return apply(hd->h, u_dev, n_rhs, n_steps, (cudaStream_t)stream);
+}
+
+eo_status eo_apply_adjoint(eo_handle_t hd, double* y_dev, int n_rhs, int n_steps, void* stream) {
+  if (!hd) return fail(EO_ERR_INVALID_ARG, "null handle");
+  return apply_adjoint(hd->h, y_dev, n_rhs, n_steps, (cudaStream_t)stream);
 }
 
 eo_status eo_apply_host(eo_handle_t hd, double* u_host, int n_rhs, int n_steps, void* stream) {

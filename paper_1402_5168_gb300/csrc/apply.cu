@@ -20,132 +20,9 @@
 #include <string>
 #include <vector>
 
-#include "handle.h"
+#include "sweep.cuh"
 
 namespace eo {
-
-__device__ __forceinline__ cd cmul(cd a, cd b) {
-  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
-}
-__device__ __forceinline__ void cfma(cd& acc, cd a, cd b) {
-  acc.x = fma(a.x, b.x, acc.x);
-  acc.x = fma(-a.y, b.y, acc.x);
-  acc.y = fma(a.x, b.y, acc.y);
-  acc.y = fma(a.y, b.x, acc.y);
-}
-__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
-  acc.x = fmaf(a.x, b.x, acc.x);
-  acc.x = fmaf(-a.y, b.y, acc.x);
-  acc.y = fmaf(a.x, b.y, acc.y);
-  acc.y = fmaf(a.y, b.x, acc.y);
-}
-
-// Operator storage type TA (double2: FP64; float2: FP32 operators, FP32
-// products and per-product sums).  Vectors enter the products in the same type;
-// results leave as FP64.
-template <typename TA> struct Cv;
-template <> struct Cv<double2> {
-  __device__ static double2 from(cd v) { return v; }
-  __device__ static cd to(double2 v) { return v; }
-  __device__ static double2 zero() { return make_double2(0.0, 0.0); }
-};
-template <> struct Cv<float2> {
-  __device__ static float2 from(cd v) { return make_float2((float)v.x, (float)v.y); }
-  __device__ static cd to(float2 v) { return make_double2(v.x, v.y); }
-  __device__ static float2 zero() { return make_float2(0.f, 0.f); }
-};
-__device__ __forceinline__ float2 operator_ld(const float2* p) { return __ldg(p); }
-__device__ __forceinline__ double2 operator_ld(const double2* p) { return __ldg(p); }
-
-// 16-byte aligned pointer past n elements of T
-template <typename T>
-__device__ __forceinline__ cd* after(T* base, size_t n) {
-  return (cd*)(((uintptr_t)(base + n) + 15) & ~(uintptr_t)15);
-}
-
-// C[c][r] = sum_{j<k} A[r + j*lda] B[c][j]  for r < rows, c < NC.
-// Bs: shared [NC][kb]; Cs: shared [NC][rows]; red: shared [blockDim * NC].
-template <int NC, typename TA>
-__device__ void cmv(const TA* __restrict__ A, int lda, int rows, int k, const TA* Bs, int kb,
-                    cd* Cs, TA* red) {
-  const int nt = blockDim.x, t = threadIdx.x;
-  int rp = (rows + 31) & ~31;
-  if (rp > nt) rp = nt;
-  const int ks = nt / rp;
-  const int ri = t % rp, kg = t / rp;
-  for (int r0 = 0; r0 < rows; r0 += rp) {
-    const int r = r0 + ri;
-    TA acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = Cv<TA>::zero();
-    if (kg < ks && r < rows) {
-      const TA* Ar = A + r;
-      int j = kg;
-      for (; j + 3 * ks < k; j += 4 * ks) {
-        const TA a0 = operator_ld(Ar + (size_t)j * lda);
-        const TA a1 = operator_ld(Ar + (size_t)(j + ks) * lda);
-        const TA a2 = operator_ld(Ar + (size_t)(j + 2 * ks) * lda);
-        const TA a3 = operator_ld(Ar + (size_t)(j + 3 * ks) * lda);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          cfma(acc[c], a0, Bs[c * kb + j]);
-          cfma(acc[c], a1, Bs[c * kb + j + ks]);
-          cfma(acc[c], a2, Bs[c * kb + j + 2 * ks]);
-          cfma(acc[c], a3, Bs[c * kb + j + 3 * ks]);
-        }
-      }
-      for (; j < k; j += ks) {
-        const TA a = operator_ld(Ar + (size_t)j * lda);
-#pragma unroll
-        for (int c = 0; c < NC; ++c) cfma(acc[c], a, Bs[c * kb + j]);
-      }
-    }
-    if (ks == 1) {
-      if (r < rows)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) Cs[c * rows + r] = Cv<TA>::to(acc[c]);
-    } else {
-      if (kg < ks)
-#pragma unroll
-        for (int c = 0; c < NC; ++c) red[(kg * NC + c) * rp + ri] = acc[c];
-      __syncthreads();
-      if (kg == 0 && r < rows) {
-#pragma unroll
-        for (int c = 0; c < NC; ++c) {
-          TA s = red[c * rp + ri];
-          for (int g = 1; g < ks; ++g) {
-            const TA v = red[(g * NC + c) * rp + ri];
-            s.x += v.x;
-            s.y += v.y;
-          }
-          Cs[c * rows + r] = Cv<TA>::to(s);
-        }
-      }
-    }
-    __syncthreads();
-  }
-}
-
-// Kernel arguments shared by the sweep kernels.
-struct Sweep {
-  int R;                 // right-hand sides in this call
-  int P;                 // poles in this call (local index pl, operator index p0 + pl)
-  int p0;
-  int q, ni, nb;
-  long long n_int, n_edge, n_nodes;
-  int shared;
-  // pre-map sources (real, per rhs stride), K of them, and coefficients [P][K]
-  int K;
-  const double* src[3];
-  long long src_rs[3];
-  const cd* coef;
-  const cd* wgt;
-};
-
-__device__ __forceinline__ void col_box(int c, int R, int& box, int& r) {
-  box = c / R;
-  r = c - box * R;
-}
 
 // ---------------------------------------------------------------- up: leaves
 template <int NC, typename TA>
@@ -158,7 +35,7 @@ __global__ void __launch_bounds__(256) k_up_leaf(Sweep s, const void* Hv, long l
   const int c0 = blockIdx.x * NC;
   TA* Bs = (TA*)smem;
   cd* Cs = after(Bs, (size_t)NC * s.ni);
-  TA* red = (TA*)(Cs + NC * s.nb);
+  cd* red = Cs + NC * s.nb;
   int box0, r0;
   col_box(c0, s.R, box0, r0);
   cd cf[3];
@@ -190,28 +67,6 @@ __global__ void __launch_bounds__(256) k_up_leaf(Sweep s, const void* Hv, long l
 }
 
 // ---------------------------------------------------------------- up: merges
-struct MergeArgs {
-  int nbox, nbx, nbx_c, nbox_c, dir, nbd, nbd_c, n3, zu_rows;
-  const int* par_child;
-  const int* par_idx;
-  const int* a3;
-  const int* b3;
-  const void* ZU;
-  long long zps, zbs;
-  const void* S;
-  long long sps, sbs;
-  const int* bseg;
-  const int* iseg;
-  int nseg;
-  cd* w3;
-};
-
-__device__ __forceinline__ void children(const MergeArgs& m, int box, int& ca, int& cb) {
-  const int bx = box % m.nbx, by = box / m.nbx;
-  if (m.dir == 0) { ca = by * m.nbx_c + 2 * bx; cb = ca + 1; }
-  else { ca = (2 * by) * m.nbx_c + bx; cb = ca + m.nbx_c; }
-}
-
 template <int NC, typename TA>
 __global__ void __launch_bounds__(256) k_up_merge(Sweep s, MergeArgs m, const cd* __restrict__ hin,
                                                   cd* __restrict__ hout) {
@@ -221,7 +76,7 @@ __global__ void __launch_bounds__(256) k_up_merge(Sweep s, MergeArgs m, const cd
   const int c0 = blockIdx.x * NC;
   TA* Bs = (TA*)smem;
   cd* Cs = after(Bs, (size_t)NC * m.n3);
-  TA* red = (TA*)(Cs + NC * m.zu_rows);
+  cd* red = Cs + NC * m.zu_rows;
   for (int e = threadIdx.x; e < NC * m.n3; e += blockDim.x) {
     const int c = e / m.n3, t = e - c * m.n3;
     cd v = make_double2(0.0, 0.0);
@@ -260,16 +115,6 @@ __global__ void __launch_bounds__(256) k_up_merge(Sweep s, MergeArgs m, const cd
 }
 
 // ---------------------------------------------------------------- root (walls)
-struct RootArgs {
-  int n, q, sxq, syq;
-  const int* bseg;
-  const void* Binv;
-  const cd* bcoef;   // [P][4][2]
-  const cd* nu;      // [P][4]
-  const double* state;
-  int F;
-};
-
 template <int NC, typename TA>
 __global__ void __launch_bounds__(256) k_root_sw(Sweep s, RootArgs ra, const cd* __restrict__ hroot,
                                                  cd* __restrict__ E) {
@@ -279,7 +124,7 @@ __global__ void __launch_bounds__(256) k_root_sw(Sweep s, RootArgs ra, const cd*
   const int n = ra.n;
   TA* Bs = (TA*)smem;
   cd* Cs = after(Bs, (size_t)NC * n);
-  TA* red = (TA*)(Cs + NC * n);
+  cd* red = Cs + NC * n;
   for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
     const int c = e / n, i = e - c * n;
     cd v = make_double2(0.0, 0.0);
@@ -320,7 +165,7 @@ __global__ void __launch_bounds__(256) k_down_merge(Sweep s, MergeArgs m, cd* __
   const int c0 = blockIdx.x * NC;
   TA* Bs = (TA*)smem;
   cd* Cs = after(Bs, (size_t)NC * m.nbd);
-  TA* red = (TA*)(Cs + NC * m.n3);
+  cd* red = Cs + NC * m.n3;
   const int q = s.q;
   if (m.S) {
     for (int e = threadIdx.x; e < NC * m.nbd; e += blockDim.x) {
@@ -368,8 +213,8 @@ __global__ void __launch_bounds__(256) k_down_leaf(Sweep s, const void* XYv, lon
   const TA* XY = (const TA*)XYv;
   TA* Bs = (TA*)smem;
   cd* Cs = after(Bs, (size_t)NC * k);
-  TA* red = (TA*)(Cs + NC * ni);
-  double* acc = (double*)after(red, (size_t)blockDim.x * NC);   // [NC][K][ni]
+  cd* red = Cs + NC * ni;
+  double* acc = (double*)(red + (size_t)blockDim.x * NC);   // [NC][K][ni]
   for (int e = threadIdx.x; e < NC * s.K * ni; e += blockDim.x) acc[e] = 0.0;
   int box0, r0;
   col_box(c0, s.R, box0, r0);
@@ -477,36 +322,6 @@ __global__ void k_reduce_full(Sweep s, int nchunk, const double* __restrict__ pa
     const int r = (int)(rk / s.K), kk = (int)(rk % s.K);
     afull[t] = accum(s, nchunk, part, eacc, r, kk, node);
   }
-}
-
-struct LeafGeo {
-  int nlx, nly, p, q;
-  long long n_int, n_hseg;
-  const double* Dx;   // p x p row-major (scaled)
-  const double* Dy;
-  const double* Ex;   // q x q
-  const double* Ey;
-};
-
-__device__ __forceinline__ long long gnode(const LeafGeo& g, int a, int b, int k, int j) {
-  const int p = g.p, q = g.q;
-  const bool kin = k > 0 && k < p - 1, jin = j > 0 && j < p - 1;
-  if (kin && jin) return ((long long)b * g.nlx + a) * q * q + (long long)(j - 1) * q + (k - 1);
-  if (kin) return g.n_int + ((long long)(j == 0 ? b : b + 1) * g.nlx + a) * q + (k - 1);
-  if (jin) return g.n_int + (g.n_hseg + (long long)b * (g.nlx + 1) + (k == 0 ? a : a + 1)) * q + (j - 1);
-  return -1;
-}
-
-// derivatives of a leaf-local field f[j*p+k] (corners unused)
-__device__ __forceinline__ double ddx(const LeafGeo& g, const double* f, int k, int j) {
-  double s = 0;
-  for (int m = 0; m < g.p; ++m) s += g.Dx[k * g.p + m] * f[j * g.p + m];
-  return s;
-}
-__device__ __forceinline__ double ddy(const LeafGeo& g, const double* f, int k, int j) {
-  double s = 0;
-  for (int m = 0; m < g.p; ++m) s += g.Dy[j * g.p + m] * f[m * g.p + k];
-  return s;
 }
 
 // wave pre-map: A u = d/dx(c^2 du/dx) + d/dy(c^2 du/dy) at interior nodes by
@@ -657,6 +472,12 @@ __global__ void k_post_sw(LeafGeo g, int R, long long n_nodes, int K, const doub
   }
 }
 
+// E[pr][seg * q + o] = 0 for the listed segments (block x: segment, block y: pole x rhs)
+__global__ void k_zero_segments(const int* __restrict__ segs, int q, long long n_edge, cd* __restrict__ E) {
+  const long long base = (long long)blockIdx.y * n_edge + (long long)segs[blockIdx.x] * q;
+  for (int o = threadIdx.x; o < q; o += blockDim.x) E[base + o] = make_double2(0.0, 0.0);
+}
+
 // ---------------------------------------------------------------- host driver
 namespace {
 
@@ -671,22 +492,22 @@ int pick_nc(int shared, int R, int k, int rows) {
   return nc;
 }
 
-template <template <int, typename> class Launcher, typename... Args>
-eo_status dispatch(int fp32, int nc, Args&&... args) {
-  if (fp32) {
-    switch (nc) {
-      case 1: return Launcher<1, float2>::run(args...);
-      case 2: return Launcher<2, float2>::run(args...);
-      case 4: return Launcher<4, float2>::run(args...);
-      default: return Launcher<8, float2>::run(args...);
-    }
-  }
+template <template <int, typename> class Launcher, typename TA, typename... Args>
+eo_status dispatch_nc(int nc, Args&&... args) {
   switch (nc) {
-    case 1: return Launcher<1, double2>::run(args...);
-    case 2: return Launcher<2, double2>::run(args...);
-    case 4: return Launcher<4, double2>::run(args...);
-    default: return Launcher<8, double2>::run(args...);
+    case 1: return Launcher<1, TA>::run(args...);
+    case 2: return Launcher<2, TA>::run(args...);
+    case 4: return Launcher<4, TA>::run(args...);
+    default: return Launcher<8, TA>::run(args...);
   }
+}
+
+// prec: 0 FP64 blocks, 1 FP32 blocks, 2 FP32-pair blocks
+template <template <int, typename> class Launcher, typename... Args>
+eo_status dispatch(int prec, int nc, Args&&... args) {
+  if (prec == 1) return dispatch_nc<Launcher, float2>(nc, args...);
+  if (prec == 2) return dispatch_nc<Launcher, float4>(nc, args...);
+  return dispatch_nc<Launcher, double2>(nc, args...);
 }
 
 #define EO_SET_SMEM(kern, bytes)                                                              \
@@ -815,23 +636,29 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   for (int l = 1; l <= L; ++l) {
     MergeArgs m = merge_args(h, l);
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<UpMerge>(h.fp32, pick_nc(h.shared, R, m.n3, m.zu_rows), s, m, hcur, hnext, st))) return rc;
+    if ((rc = dispatch<UpMerge>(h.lv[l].fp32, pick_nc(h.shared, R, m.n3, m.zu_rows), s, m, hcur, hnext, st))) return rc;
     if ((rc = h.trace_end(TR_UP_MERGE, st))) return rc;
     std::swap(hcur, hnext);
   }
   // root
-  if (h.kind == EO_SW_WALLS) {
+  if (h.kind == EO_WAVE_DIRICHLET) {
+    // wall values are zero: reset them every step (other users of the edge
+    // workspace, such as the adjoint sweeps, leave data there)
+    const Level& rl = h.plan.lv[L];
+    k_zero_segments<<<dim3(rl.nseg, np * R), 64, 0, st>>>(h.lv[L].bseg, q, g.n_edge, h.E);
+    EO_CUDA_TRY(cudaGetLastError());
+  } else {
     const Level& rl = h.plan.lv[L];
     RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, uin, 3};
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<RootSW>(h.fp32, pick_nc(0, R, rl.nbd, rl.nbd), s, ra, hcur, h.E, st))) return rc;
+    if ((rc = dispatch<RootSW>(h.root_fp32, pick_nc(0, R, rl.nbd, rl.nbd), s, ra, hcur, h.E, st))) return rc;
     if ((rc = h.trace_end(TR_ROOT, st))) return rc;
   }
   // down: merges
   for (int l = L; l >= 1; --l) {
     MergeArgs m = merge_args(h, l);
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<DownMerge>(h.fp32, pick_nc(h.shared, R, m.nbd, m.n3), s, m, h.E, st))) return rc;
+    if ((rc = dispatch<DownMerge>(h.lv[l].fp32, pick_nc(h.shared, R, m.nbd, m.n3), s, m, h.E, st))) return rc;
     if ((rc = h.trace_end(TR_DOWN_MERGE, st))) return rc;
   }
   // down: leaves with the pole sum

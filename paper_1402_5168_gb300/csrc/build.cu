@@ -489,21 +489,33 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
   return EO_OK;
 }
 
-// ---------------------------------------------------------------- FP32 operator copies
+// ---------------------------------------------------------------- reduced-precision copies
 __global__ void to_float2(size_t n, const cd* __restrict__ x, float2* __restrict__ y) {
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x)
     y[t] = make_float2((float)x[t].x, (float)x[t].y);
 }
 
-// Replace every FP64 operator block by an FP32 copy (rounded to nearest); the
-// apply then multiplies in FP32 and keeps vectors, pole sums and maps in FP64.
-eo_status to_fp32(Handle& h, cudaStream_t st) {
+// FP64 value -> (hi, lo) FP32 pair with hi = fl32(x), lo = fl32(x - hi)
+__global__ void to_float_pair(size_t n, const cd* __restrict__ x, float4* __restrict__ y) {
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < n; t += (size_t)gridDim.x * blockDim.x) {
+    const cd v = x[t];
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    y[t] = make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+  }
+}
+
+// Replace FP64 operator blocks by FP32 (prec 1) or FP32-pair (prec 2) copies.
+// The top opts.fp64_top_levels merge levels (and then the root wall solve) keep
+// FP64.  Vectors, pole sums and pre/post maps stay FP64 in every case.
+eo_status to_reduced(Handle& h, int prec, cudaStream_t st) {
   auto conv = [&](cd*& src, size_t n, const void** view) -> eo_status {
     if (!src) { *view = nullptr; return EO_OK; }
-    float2* dst;
-    eo_status rc = h.alloc((void**)&dst, sizeof(float2) * n, true);
+    void* dst;
+    const size_t esz = prec == 1 ? sizeof(float2) : sizeof(float4);
+    eo_status rc = h.alloc(&dst, esz * n, true);
     if (rc) return rc;
-    to_float2<<<4096, 256, 0, st>>>(n, src, dst);
+    if (prec == 1) to_float2<<<4096, 256, 0, st>>>(n, src, (float2*)dst);
+    else to_float_pair<<<4096, 256, 0, st>>>(n, src, (float4*)dst);
     EO_CUDA_TRY(cudaGetLastError());
     EO_CUDA_TRY(cudaStreamSynchronize(st));
     h.release(src, sizeof(cd) * n, true);
@@ -515,13 +527,19 @@ eo_status to_fp32(Handle& h, cudaStream_t st) {
   const size_t P = h.P;
   if ((rc = conv(h.H, P * h.h_pstride, &h.aH))) return rc;
   if ((rc = conv(h.XY, P * h.xy_pstride, &h.aXY))) return rc;
-  for (size_t l = 1; l < h.lv.size(); ++l) {
+  h.fp32 = prec;
+  const int L = (int)h.lv.size() - 1;
+  const int keep = std::max(0, h.opts.fp64_top_levels);
+  for (int l = 1; l <= L - keep; ++l) {
     LevelDev& ld = h.lv[l];
     if ((rc = conv(ld.ZU, P * ld.zu_pstride, &ld.aZU))) return rc;
     if ((rc = conv(ld.S, P * ld.s_pstride, &ld.aS))) return rc;
+    ld.fp32 = prec;
   }
-  if ((rc = conv(h.Binv, P * (size_t)h.nroot * h.nroot, &h.aBinv))) return rc;
-  h.fp32 = 1;
+  if (keep == 0) {
+    if ((rc = conv(h.Binv, P * (size_t)h.nroot * h.nroot, &h.aBinv))) return rc;
+    h.root_fp32 = prec;
+  }
   return EO_OK;
 }
 

@@ -37,6 +37,7 @@ struct LevelDev {
   cd* w3 = nullptr;             // workspace [pole][rhs][nbox][n3]
   const void* aZU = nullptr;    // operators the apply reads (FP64 above, or FP32 copies)
   const void* aS = nullptr;
+  int fp32 = 0;                 // this level's blocks: 0 FP64, 1 FP32, 2 FP32 pairs
 };
 
 struct Handle {
@@ -60,7 +61,8 @@ struct Handle {
   // root oblique solve (EO_SW_WALLS): Binv [pole][nroot x nroot]
   cd* Binv = nullptr;
   int nroot = 0;
-  int fp32 = 0;                 // operators stored and multiplied in FP32
+  int fp32 = 0;                 // leaf blocks: 0 FP64, 1 FP32, 2 FP32 pairs
+  int root_fp32 = 0;            // root wall solve blocks, same code
   const void* aH = nullptr;     // operators the apply reads
   const void* aXY = nullptr;
   const void* aBinv = nullptr;
@@ -86,6 +88,7 @@ struct Handle {
   double* acoef = nullptr;      // wave: c^2 at every node (device)
   double* afull = nullptr;      // SW: accumulated fields at every node [rhs][K][n_nodes]
   double* ustate = nullptr;     // second state buffer [rhs][F][n_nodes]
+  cd* gbar = nullptr;           // adjoint: seeds on the leaf sources [pole][rhs][leaf][q^2]
   int64_t op_bytes = 0, ws_bytes = 0;
   // tracing: events around launches, per kernel class
   bool timing = false;
@@ -104,9 +107,10 @@ struct Handle {
 enum { TR_PRE = 0, TR_UP_LEAF, TR_UP_MERGE, TR_ROOT, TR_DOWN_MERGE, TR_DOWN_LEAF, TR_EDGE, TR_POST, TR_N };
 
 eo_status build(Handle& h, const double* coeff, cudaStream_t st);
-eo_status to_fp32(Handle& h, cudaStream_t st);
+eo_status to_reduced(Handle& h, int prec, cudaStream_t st);
 eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st);
 eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStream_t st);
+eo_status apply_adjoint(Handle& h, double* y, int n_rhs, int n_steps, cudaStream_t st);
 eo_status apply_resolvent_noalloc(Handle& h, int j, const double* u, double* x, cudaStream_t st);
 
 }  // namespace eo

@@ -1,0 +1,251 @@
+// Device helpers and argument structs shared by the forward sweeps (apply.cu)
+// and the transposed sweeps (adjoint.cu).
+#pragma once
+
+#include <cstdint>
+
+#include "handle.h"
+
+namespace eo {
+
+__device__ __forceinline__ cd cmul(cd a, cd b) {
+  return make_double2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ void cfma(cd& acc, cd a, cd b) {
+  acc.x = fma(a.x, b.x, acc.x);
+  acc.x = fma(-a.y, b.y, acc.x);
+  acc.y = fma(a.x, b.y, acc.y);
+  acc.y = fma(a.y, b.x, acc.y);
+}
+__device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
+  acc.x = fmaf(a.x, b.x, acc.x);
+  acc.x = fmaf(-a.y, b.y, acc.x);
+  acc.y = fmaf(a.x, b.y, acc.y);
+  acc.y = fmaf(a.y, b.x, acc.y);
+}
+
+// Operator storage type TA:
+//   double2 -- FP64 blocks, FP64 products;
+//   float2  -- FP32 blocks, FP32 products and sums;
+//   float4  -- FP32 pairs (re_hi, im_hi, re_lo, im_lo) holding an FP64 value to
+//              ~2^-48: products split exactly with fma (p = x_h y_h, e = fma(x_h,
+//              y_h, -p)), hi parts summed with an error-free two-sum, the small
+//              cross terms in a plain FP32 sum.  This runs on the FP32 pipe at
+//              near-FP64 accuracy (GB300's FP64 pipe is ~60x slower than FP32).
+// Vectors enter the products in the same type (Cv::from); Acc holds the sums
+// and returns them as FP64 (Cv::to).
+template <typename TA> struct Cv;
+template <> struct Cv<double2> {
+  typedef double2 Acc;
+  __device__ static double2 from(cd v) { return v; }
+  __device__ static cd to(const Acc& v) { return v; }
+  __device__ static Acc zero() { return make_double2(0.0, 0.0); }
+  __device__ static void mac(Acc& acc, const double2& a, const double2& b) { cfma(acc, a, b); }
+};
+template <> struct Cv<float2> {
+  typedef float2 Acc;
+  __device__ static float2 from(cd v) { return make_float2((float)v.x, (float)v.y); }
+  __device__ static cd to(const Acc& v) { return make_double2(v.x, v.y); }
+  __device__ static Acc zero() { return make_float2(0.f, 0.f); }
+  __device__ static void mac(Acc& acc, const float2& a, const float2& b) { cfma(acc, a, b); }
+};
+
+struct DFAcc {
+  float sr, cr, lr, si, ci, li;   // hi sum, two-sum compensation, cross-term sum (re, im)
+};
+__device__ __forceinline__ void df_two_sum(float& s, float& c, float p) {
+  const float t = __fadd_rn(s, p);
+  const float bp = __fsub_rn(t, s);
+  c = __fadd_rn(c, __fadd_rn(__fsub_rn(s, __fsub_rn(t, bp)), __fsub_rn(p, bp)));
+  s = t;
+}
+// x*y for x = xh + xl, y = yh + yl: p + lo with p = fl(xh yh) and lo the rest to ~2^-48
+__device__ __forceinline__ void df_prod(float xh, float xl, float yh, float yl, float& p, float& lo) {
+  p = __fmul_rn(xh, yh);
+  const float e = __fmaf_rn(xh, yh, -p);
+  lo = __fmaf_rn(xh, yl, __fmaf_rn(xl, yh, e));
+}
+template <> struct Cv<float4> {
+  typedef DFAcc Acc;
+  __device__ static float4 from(cd v) {
+    const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
+    return make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
+  }
+  __device__ static cd to(const Acc& a) {
+    return make_double2((double)a.sr + ((double)a.cr + (double)a.lr), (double)a.si + ((double)a.ci + (double)a.li));
+  }
+  __device__ static Acc zero() { return DFAcc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}; }
+  // re += a_re b_re - a_im b_im ; im += a_re b_im + a_im b_re
+  __device__ static void mac(Acc& acc, const float4& a, const float4& b) {
+    float p, lo;
+    df_prod(a.x, a.z, b.x, b.z, p, lo);
+    df_two_sum(acc.sr, acc.cr, p);
+    acc.lr = __fadd_rn(acc.lr, lo);
+    df_prod(a.y, a.w, b.y, b.w, p, lo);
+    df_two_sum(acc.sr, acc.cr, -p);
+    acc.lr = __fsub_rn(acc.lr, lo);
+    df_prod(a.x, a.z, b.y, b.w, p, lo);
+    df_two_sum(acc.si, acc.ci, p);
+    acc.li = __fadd_rn(acc.li, lo);
+    df_prod(a.y, a.w, b.x, b.z, p, lo);
+    df_two_sum(acc.si, acc.ci, p);
+    acc.li = __fadd_rn(acc.li, lo);
+  }
+};
+__device__ __forceinline__ float2 operator_ld(const float2* p) { return __ldg(p); }
+__device__ __forceinline__ double2 operator_ld(const double2* p) { return __ldg(p); }
+__device__ __forceinline__ float4 operator_ld(const float4* p) { return __ldg(p); }
+
+// 16-byte aligned pointer past n elements of T
+template <typename T>
+__device__ __forceinline__ cd* after(T* base, size_t n) {
+  return (cd*)(((uintptr_t)(base + n) + 15) & ~(uintptr_t)15);
+}
+
+// C[c][r] = sum_{j<k} A[r + j*lda] B[c][j]  for r < rows, c < NC.
+// Bs: shared [NC][kb]; Cs: shared [NC][rows]; red: shared [blockDim * NC].
+template <int NC, typename TA>
+__device__ void cmv(const TA* __restrict__ A, int lda, int rows, int k, const TA* Bs, int kb,
+                    cd* Cs, cd* red) {
+  const int nt = blockDim.x, t = threadIdx.x;
+  int rp = (rows + 31) & ~31;
+  if (rp > nt) rp = nt;
+  const int ks = nt / rp;
+  const int ri = t % rp, kg = t / rp;
+  for (int r0 = 0; r0 < rows; r0 += rp) {
+    const int r = r0 + ri;
+    typename Cv<TA>::Acc acc[NC];
+#pragma unroll
+    for (int c = 0; c < NC; ++c) acc[c] = Cv<TA>::zero();
+    if (kg < ks && r < rows) {
+      const TA* Ar = A + r;
+      int j = kg;
+      for (; j + 3 * ks < k; j += 4 * ks) {
+        const TA a0 = operator_ld(Ar + (size_t)j * lda);
+        const TA a1 = operator_ld(Ar + (size_t)(j + ks) * lda);
+        const TA a2 = operator_ld(Ar + (size_t)(j + 2 * ks) * lda);
+        const TA a3 = operator_ld(Ar + (size_t)(j + 3 * ks) * lda);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          Cv<TA>::mac(acc[c], a0, Bs[c * kb + j]);
+          Cv<TA>::mac(acc[c], a1, Bs[c * kb + j + ks]);
+          Cv<TA>::mac(acc[c], a2, Bs[c * kb + j + 2 * ks]);
+          Cv<TA>::mac(acc[c], a3, Bs[c * kb + j + 3 * ks]);
+        }
+      }
+      for (; j < k; j += ks) {
+        const TA a = operator_ld(Ar + (size_t)j * lda);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Cv<TA>::mac(acc[c], a, Bs[c * kb + j]);
+      }
+    }
+    if (ks == 1) {
+      if (r < rows)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Cs[c * rows + r] = Cv<TA>::to(acc[c]);
+    } else {
+      if (kg < ks)
+#pragma unroll
+        for (int c = 0; c < NC; ++c) red[(kg * NC + c) * rp + ri] = Cv<TA>::to(acc[c]);
+      __syncthreads();
+      if (kg == 0 && r < rows) {
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          cd s = red[c * rp + ri];
+          for (int g = 1; g < ks; ++g) {
+            const cd v = red[(g * NC + c) * rp + ri];
+            s.x += v.x;
+            s.y += v.y;
+          }
+          Cs[c * rows + r] = s;
+        }
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// Kernel arguments shared by the sweep kernels.
+struct Sweep {
+  int R;                 // right-hand sides in this call
+  int P;                 // poles in this call (local index pl, operator index p0 + pl)
+  int p0;
+  int q, ni, nb;
+  long long n_int, n_edge, n_nodes;
+  int shared;
+  // pre-map sources (real, per rhs stride), K of them, and coefficients [P][K]
+  int K;
+  const double* src[3];
+  long long src_rs[3];
+  const cd* coef;
+  const cd* wgt;
+};
+
+__device__ __forceinline__ void col_box(int c, int R, int& box, int& r) {
+  box = c / R;
+  r = c - box * R;
+}
+
+struct MergeArgs {
+  int nbox, nbx, nbx_c, nbox_c, dir, nbd, nbd_c, n3, zu_rows;
+  const int* par_child;
+  const int* par_idx;
+  const int* a3;
+  const int* b3;
+  const void* ZU;
+  long long zps, zbs;
+  const void* S;
+  long long sps, sbs;
+  const int* bseg;
+  const int* iseg;
+  int nseg;
+  cd* w3;
+};
+
+__device__ __forceinline__ void children(const MergeArgs& m, int box, int& ca, int& cb) {
+  const int bx = box % m.nbx, by = box / m.nbx;
+  if (m.dir == 0) { ca = by * m.nbx_c + 2 * bx; cb = ca + 1; }
+  else { ca = (2 * by) * m.nbx_c + bx; cb = ca + m.nbx_c; }
+}
+
+struct RootArgs {
+  int n, q, sxq, syq;
+  const int* bseg;
+  const void* Binv;
+  const cd* bcoef;   // [P][4][2]
+  const cd* nu;      // [P][4]
+  const double* state;
+  int F;
+};
+
+struct LeafGeo {
+  int nlx, nly, p, q;
+  long long n_int, n_hseg;
+  const double* Dx;   // p x p row-major (scaled)
+  const double* Dy;
+  const double* Ex;   // q x q
+  const double* Ey;
+};
+
+__device__ __forceinline__ long long gnode(const LeafGeo& g, int a, int b, int k, int j) {
+  const int p = g.p, q = g.q;
+  const bool kin = k > 0 && k < p - 1, jin = j > 0 && j < p - 1;
+  if (kin && jin) return ((long long)b * g.nlx + a) * q * q + (long long)(j - 1) * q + (k - 1);
+  if (kin) return g.n_int + ((long long)(j == 0 ? b : b + 1) * g.nlx + a) * q + (k - 1);
+  if (jin) return g.n_int + (g.n_hseg + (long long)b * (g.nlx + 1) + (k == 0 ? a : a + 1)) * q + (j - 1);
+  return -1;
+}
+
+// derivatives of a leaf-local field f[j*p+k] (corners unused)
+__device__ __forceinline__ double ddx(const LeafGeo& g, const double* f, int k, int j) {
+  double s = 0;
+  for (int m = 0; m < g.p; ++m) s += g.Dx[k * g.p + m] * f[j * g.p + m];
+  return s;
+}
+__device__ __forceinline__ double ddy(const LeafGeo& g, const double* f, int k, int j) {
+  double s = 0;
+  for (int m = 0; m < g.p; ++m) s += g.Dy[j * g.p + m] * f[m * g.p + k];
+  return s;
+}
+
+}  // namespace eo

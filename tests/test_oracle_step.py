@@ -169,3 +169,27 @@ def test_sw_rotating_energy_conserved(poles21):
     for _ in range(4):
         s = st.step(s)
     assert abs(energy(s) - e0) < 3e-4 * e0
+
+
+def test_wave_adjoint_equals_transpose_of_dense_step(poles21):
+    # the factor-by-factor transpose against G.T of the dense step matrix, and the
+    # dot-product identity <y, G u> = <G^T y, u> on a second grid
+    from oracle.resolvent import adjoint_step, step_matrix
+    alpha, b, X = poles21
+    g = sem.Grid(2, 2, 6)
+    c2 = (1 + 0.3 * np.sin(3 * g.x) * np.cos(2 * g.y)) ** 2
+    st = Stepper(Problem(g, "wave", 0.02, c2=c2), alpha, b)
+    G = step_matrix(st)
+    rng = np.random.default_rng(5)
+    y = rng.standard_normal((2, g.n_nodes))
+    got = adjoint_step(st, y).ravel()
+    want = G.T @ y.ravel()
+    assert np.abs(got - want).max() <= 1e-9 * np.abs(want).max()
+    g2 = sem.Grid(4, 2, 8)
+    c2 = (1 + 0.2 * np.cos(5 * g2.x)) ** 2
+    st2 = Stepper(Problem(g2, "wave", 0.01, c2=c2), alpha, b)
+    u = rng.standard_normal((2, g2.n_nodes))
+    y = rng.standard_normal((2, g2.n_nodes))
+    lhs = np.sum(y * st2.step(u))
+    rhs = np.sum(adjoint_step(st2, y) * u)
+    assert abs(lhs - rhs) <= 1e-9 * abs(lhs)
