@@ -147,8 +147,8 @@ eo_status eo_apply(eo_handle_t h, double *u_dev, int n_rhs, int n_steps, void *s
  * eo_apply step (transpose for the Euclidean inner product of the state vector):
  * the forward sweeps run backwards with every stored block transposed
  * (conjugate-pole form of Section 3.3 kept).  Layout, stream and errors as
- * eo_apply.  EO_WAVE_DIRICHLET only (EO_ERR_UNSUPPORTED otherwise).  The first
- * call allocates a seed buffer of P * max_rhs * n_interior complex values. */
+ * eo_apply.  The first call allocates seed buffers (P * max_rhs * n_interior
+ * complex values, plus wall and field seeds for EO_SW_WALLS). */
 eo_status eo_apply_adjoint(eo_handle_t h, double *y_dev, int n_rhs, int n_steps, void *stream);
 
 /* Same as eo_apply for a state in HOST memory (pinned or pageable): copies in,

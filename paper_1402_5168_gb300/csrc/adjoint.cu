@@ -349,14 +349,196 @@ __global__ void k_adj_init_wave(long long n_nodes, int R, double C0, const doubl
   }
 }
 
+// ---------------------------------------------------------------- shallow water
+// Transpose of k_post_sw.  Forward, at every node the leaf owns:
+//   U = C1 F1 + C2 F2 + tg (dx A1 + dy A2),  V = -C2 F1 + C1 F2 + tg (-dx A2 + dy A1),  h = A0,
+// dx, dy the node-gradient stencils (leaf rows / columns inside, mean of the
+// one-sided normal derivatives on interfaces, edge interpolant tangentially).
+// Here every stencil weight is scattered back onto the accumulated fields
+// abar[r][k][node] and the direct terms onto out (F1, F2 fields).
+__device__ __forceinline__ void scat_dx(const LeafGeo& g, double* f, int a, int b, int k, int j, double w) {
+  for (int m = 0; m < g.p; ++m) {
+    const long long id = gnode(g, a, b, m, j);
+    if (id >= 0) atomicAdd(&f[id], g.Dx[k * g.p + m] * w);
+  }
+}
+__device__ __forceinline__ void scat_dy(const LeafGeo& g, double* f, int a, int b, int k, int j, double w) {
+  for (int m = 0; m < g.p; ++m) {
+    const long long id = gnode(g, a, b, k, m);
+    if (id >= 0) atomicAdd(&f[id], g.Dy[j * g.p + m] * w);
+  }
+}
+
+__global__ void k_adj_post_sw(LeafGeo g, int R, long long n_nodes, const double* __restrict__ y,
+                              double* __restrict__ abar, double* __restrict__ out, double C1, double C2,
+                              double taug) {
+  const int leaf = blockIdx.x, r = blockIdx.y;
+  const int a = leaf % g.nlx, b = leaf / g.nlx, p = g.p, q = g.q;
+  const double* yr = y + (long long)r * 3 * n_nodes;
+  double* ab0 = abar + (long long)r * 3 * n_nodes;
+  double* ab1 = ab0 + n_nodes;
+  double* ab2 = ab1 + n_nodes;
+  double* o = out + (long long)r * 3 * n_nodes;
+  auto direct = [&](long long id, double& s1x, double& s1y, double& s2x, double& s2y) {
+    const double yU = yr[id], yV = yr[n_nodes + id], yh = yr[2 * n_nodes + id];
+    atomicAdd(&ab0[id], yh);
+    atomicAdd(&o[id], C1 * yU - C2 * yV);
+    atomicAdd(&o[n_nodes + id], C2 * yU + C1 * yV);
+    s1x = taug * yU;  // weight of dx A1
+    s1y = taug * yV;  // dy A1
+    s2x = -taug * yV; // dx A2
+    s2y = taug * yU;  // dy A2
+  };
+  for (int t = threadIdx.x; t < q * q; t += blockDim.x) {
+    const int k = t % q + 1, j = t / q + 1;
+    double s1x, s1y, s2x, s2y;
+    direct(gnode(g, a, b, k, j), s1x, s1y, s2x, s2y);
+    scat_dx(g, ab1, a, b, k, j, s1x);
+    scat_dy(g, ab1, a, b, k, j, s1y);
+    scat_dx(g, ab2, a, b, k, j, s2x);
+    scat_dy(g, ab2, a, b, k, j, s2y);
+  }
+  for (int t = threadIdx.x; t < 4 * q; t += blockDim.x) {
+    const int side = t / q, oo = t % q + 1;
+    if (side == 1 && a != g.nlx - 1) continue;
+    if (side == 2 && b != g.nly - 1) continue;
+    double s1x, s1y, s2x, s2y;
+    if (side == 0 || side == 2) {                // normal y, tangential x
+      const int j = side == 0 ? 0 : p - 1, k = oo;
+      direct(gnode(g, a, b, k, j), s1x, s1y, s2x, s2y);
+      const double wn = (side == 0 && b > 0) ? 0.5 : 1.0;
+      scat_dy(g, ab1, a, b, k, j, wn * s1y);
+      scat_dy(g, ab2, a, b, k, j, wn * s2y);
+      if (side == 0 && b > 0) {
+        scat_dy(g, ab1, a, b - 1, k, p - 1, 0.5 * s1y);
+        scat_dy(g, ab2, a, b - 1, k, p - 1, 0.5 * s2y);
+      }
+      for (int m = 1; m <= q; ++m) {
+        const long long id = gnode(g, a, b, m, j);
+        atomicAdd(&ab1[id], g.Ex[(k - 1) * q + (m - 1)] * s1x);
+        atomicAdd(&ab2[id], g.Ex[(k - 1) * q + (m - 1)] * s2x);
+      }
+    } else {                                     // normal x, tangential y
+      const int k = side == 3 ? 0 : p - 1, j = oo;
+      direct(gnode(g, a, b, k, j), s1x, s1y, s2x, s2y);
+      const double wn = (side == 3 && a > 0) ? 0.5 : 1.0;
+      scat_dx(g, ab1, a, b, k, j, wn * s1x);
+      scat_dx(g, ab2, a, b, k, j, wn * s2x);
+      if (side == 3 && a > 0) {
+        scat_dx(g, ab1, a - 1, b, p - 1, j, 0.5 * s1x);
+        scat_dx(g, ab2, a - 1, b, p - 1, j, 0.5 * s2x);
+      }
+      for (int m = 1; m <= q; ++m) {
+        const long long id = gnode(g, a, b, k, m);
+        atomicAdd(&ab1[id], g.Ey[(j - 1) * q + (m - 1)] * s1y);
+        atomicAdd(&ab2[id], g.Ey[(j - 1) * q + (m - 1)] * s2y);
+      }
+    }
+  }
+}
+
+// Root wall solve transposed: qbar = Binv^T e_bar(wall); h_bar_root = -nu qbar;
+// qbar kept per pole for the wall right-hand side's dependence on (F1, F2).
+template <int NC, typename TA>
+__global__ void __launch_bounds__(256) k_adj_root_sw(Sweep s, RootArgs ra, const cd* __restrict__ E,
+                                                     cd* __restrict__ hroot, cd* __restrict__ qbar) {
+  extern __shared__ cd smem[];
+  const int pl = blockIdx.y, p = s.p0 + pl;
+  const int c0 = blockIdx.x * NC;
+  const int n = ra.n;
+  TA* Xs = (TA*)smem;
+  cd* Out = after(Xs, (size_t)NC * n);
+  for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
+    const int c = e / n, i = e - c * n;
+    cd v = make_double2(0.0, 0.0);
+    if (c0 + c < s.R) v = E[((long long)pl * s.R + c0 + c) * s.n_edge + (long long)ra.bseg[i / ra.q] * ra.q + (i % ra.q)];
+    Xs[e] = Cv<TA>::from(v);
+  }
+  __syncthreads();
+  cmvT<NC, TA>((const TA*)ra.Binv + (long long)p * n * n, n, n, n, Xs, n, Out);
+  for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
+    const int c = e / n, j = e - c * n;
+    const int r = c0 + c;
+    if (r >= s.R) continue;
+    int side;
+    if (j < ra.sxq) side = 0;
+    else if (j < ra.sxq + ra.syq) side = 1;
+    else if (j < 2 * ra.sxq + ra.syq) side = 2;
+    else side = 3;
+    const cd qv = Out[e];
+    const cd nu = ra.nu[p * 4 + side];
+    const cd hv = cmul(nu, qv);
+    const long long o = ((long long)pl * s.R + r) * n + j;
+    qbar[o] = qv;
+    hroot[o] = make_double2(-hv.x, -hv.y);
+  }
+}
+
+// wall right-hand side transposed, summed over poles in order:
+// F1 += Re sum_p b0_p qbar_p, F2 += Re sum_p b1_p qbar_p at wall nodes
+__global__ void k_adj_root_rhs(Sweep s, RootArgs ra, const cd* __restrict__ qbar, double* __restrict__ out) {
+  const int n = ra.n;
+  const long long tot = (long long)s.R * n;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const int r = (int)(t / n), j = (int)(t % n);
+    int side;
+    if (j < ra.sxq) side = 0;
+    else if (j < ra.sxq + ra.syq) side = 1;
+    else if (j < 2 * ra.sxq + ra.syq) side = 2;
+    else side = 3;
+    double f1 = 0, f2 = 0;
+    for (int pl = 0; pl < s.P; ++pl) {
+      const int p = s.p0 + pl;
+      const cd qv = qbar[((long long)pl * s.R + r) * n + j];
+      const cd b0 = ra.bcoef[(p * 4 + side) * 2], b1 = ra.bcoef[(p * 4 + side) * 2 + 1];
+      f1 += b0.x * qv.x - b0.y * qv.y;
+      f2 += b1.x * qv.x - b1.y * qv.y;
+    }
+    const long long node = s.n_int + (long long)ra.bseg[j / ra.q] * ra.q + (j % ra.q);
+    atomicAdd(&out[(long long)r * 3 * s.n_nodes + node], f1);
+    atomicAdd(&out[((long long)r * 3 + 1) * s.n_nodes + node], f2);
+  }
+}
+
+// Pre-map transposed: r_bar = P0 at interior; div F and curl F are leaf
+// derivatives at interior nodes, so F1 += dx^T P1 - dy^T P2, F2 += dy^T P1 + dx^T P2.
+__global__ void k_adj_pre_sw(LeafGeo g, int R, long long n_nodes, int K, int nchunk,
+                             const double* __restrict__ part, double* __restrict__ out) {
+  const int leaf = blockIdx.x, r = blockIdx.y;
+  const int a = leaf % g.nlx, b = leaf / g.nlx, q = g.q;
+  const long long ni = (long long)q * q;
+  double* o1 = out + (long long)r * 3 * n_nodes;
+  double* o2 = o1 + n_nodes;
+  double* oh = o2 + n_nodes;
+  for (int t = threadIdx.x; t < q * q; t += blockDim.x) {
+    const int k = t % q + 1, j = t / q + 1;
+    const long long o = (long long)leaf * ni + t;
+    double P0 = 0, P1 = 0, P2 = 0;
+    for (int c = 0; c < nchunk; ++c) {
+      P0 += part[(((long long)c * R + r) * K + 0) * g.n_int + o];
+      P1 += part[(((long long)c * R + r) * K + 1) * g.n_int + o];
+      P2 += part[(((long long)c * R + r) * K + 2) * g.n_int + o];
+    }
+    atomicAdd(&oh[gnode(g, a, b, k, j)], P0);
+    scat_dx(g, o1, a, b, k, j, P1);
+    scat_dy(g, o1, a, b, k, j, -P2);
+    scat_dy(g, o2, a, b, k, j, P1);
+    scat_dx(g, o2, a, b, k, j, P2);
+  }
+}
+
 // ---------------------------------------------------------------- host driver
 namespace {
 
-int pick_nc_t(int shared, int R, int k, int rows) {
+int pick_nc_t(int shared, int R, int k, int rows, int nbox = 1 << 30) {
   int nc = 1;
-  if (shared) nc = 8;
-  else
+  if (shared) {
+    const long long ncols = (long long)nbox * R;
+    while (nc < 8 && 2 * nc <= ncols) nc *= 2;
+  } else {
     while (nc < 8 && R % (nc * 2) == 0) nc *= 2;
+  }
   while (nc > 1 && (size_t)nc * (k + rows + 64) * sizeof(cd) > 200 * 1024) nc /= 2;
   return nc;
 }
@@ -416,6 +598,18 @@ struct AdjUpLeaf {
   }
 };
 
+template <int NC, typename TA>
+struct AdjRootSW {
+  static eo_status run(const Sweep& s, const RootArgs& ra, const cd* E, cd* hroot, cd* qbar, cudaStream_t st) {
+    dim3 grid((s.R + NC - 1) / NC, s.P);
+    const size_t smem = sizeof(cd) * ((size_t)NC * 2 * ra.n) + 64;
+    EO_SET_SMEM_T((k_adj_root_sw<NC, TA>), smem);
+    k_adj_root_sw<NC, TA><<<grid, 256, smem, st>>>(s, ra, E, hroot, qbar);
+    EO_CUDA_TRY(cudaGetLastError());
+    return EO_OK;
+  }
+};
+
 template <template <int, typename> class Launcher, typename TA, typename... Args>
 eo_status dispatch_nc_t(int nc, Args&&... args) {
   switch (nc) {
@@ -456,12 +650,27 @@ eo_status adjoint_step(Handle& h, const double* yin, double* yout, int R, cudaSt
   s.R = R; s.P = h.P; s.p0 = 0; s.q = q; s.ni = ni; s.nb = nb;
   s.n_int = g.n_int; s.n_edge = g.n_edge; s.n_nodes = g.n_nodes; s.shared = h.shared;
   s.K = h.K; s.coef = h.coef; s.wgt = h.wgt;
-  // seeds: forward accumulators A0 -> v, A1 -> u
-  s.src[0] = yin + g.n_nodes; s.src_rs[0] = 2 * g.n_nodes;
-  s.src[1] = yin;             s.src_rs[1] = 2 * g.n_nodes;
+  LeafGeo geo{g.nlx, g.nly, g.p, q, g.n_int, g.n_hseg, h.dDx, h.dDx + g.p * g.p, h.dDx + 2 * g.p * g.p,
+              h.dDx + 2 * g.p * g.p + q * q};
+  const bool sw = h.kind == EO_SW_WALLS;
+  if (!sw) {
+    // seeds: forward accumulators A0 -> v, A1 -> u
+    s.src[0] = yin + g.n_nodes; s.src_rs[0] = 2 * g.n_nodes;
+    s.src[1] = yin;             s.src_rs[1] = 2 * g.n_nodes;
+  } else {
+    // post-map transposed onto the accumulated fields (abar) and the direct terms
+    EO_CUDA_TRY(cudaMemsetAsync(yout, 0, sizeof(double) * (size_t)R * 3 * g.n_nodes, st));
+    EO_CUDA_TRY(cudaMemsetAsync(h.abar, 0, sizeof(double) * (size_t)R * 3 * g.n_nodes, st));
+    if ((rc = h.trace_begin(st))) return rc;
+    k_adj_post_sw<<<dim3(nleaf, R), 128, 0, st>>>(geo, R, g.n_nodes, yin, h.abar, yout, h.C[0], h.C[1],
+                                                   h.tau * h.opts.sw_g);
+    EO_CUDA_TRY(cudaGetLastError());
+    if ((rc = h.trace_end(TR_POST, st))) return rc;
+    for (int k = 0; k < 3; ++k) { s.src[k] = h.abar + k * g.n_nodes; s.src_rs[k] = 3 * g.n_nodes; }
+  }
   cd* ybar = h.hB;
   if ((rc = h.trace_begin(st))) return rc;
-  if ((rc = dispatch_t<AdjDownLeaf>(h.fp32, pick_nc_t(h.shared, R, ni + nb, ni), s, h, nleaf, h.gbar, ybar, st)))
+  if ((rc = dispatch_t<AdjDownLeaf>(h.fp32, pick_nc_t(h.shared, R, ni + nb, ni, nleaf), s, h, nleaf, h.gbar, ybar, st)))
     return rc;
   if ((rc = h.trace_end(TR_DOWN_LEAF, st))) return rc;
   if ((rc = h.trace_begin(st))) return rc;
@@ -472,22 +681,34 @@ eo_status adjoint_step(Handle& h, const double* yin, double* yout, int R, cudaSt
   for (int l = 1; l <= L; ++l) {
     MergeArgs m = merge_args_t(h, l);
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch_t<AdjDownMerge>(h.lv[l].fp32, pick_nc_t(h.shared, R, m.nbd, m.n3), s, m, h.E, st))) return rc;
+    if ((rc = dispatch_t<AdjDownMerge>(h.lv[l].fp32, pick_nc_t(h.shared, R, m.nbd, m.n3, m.nbox), s, m, h.E, st))) return rc;
     if ((rc = h.trace_end(TR_DOWN_MERGE, st))) return rc;
   }
   cd* hpar = h.hA;
   cd* hch = h.hB;
-  if (L == 0)   // one leaf: its boundary is the wall, no flux seeds reach it
+  if (sw) {
+    // wall solve transposed: h_bar at the root and the wall rhs's dependence on F
+    const Level& rl = h.plan.lv[L];
+    RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, yin, 3};
+    if ((rc = h.trace_begin(st))) return rc;
+    if ((rc = dispatch_t<AdjRootSW>(h.root_fp32, pick_nc_t(0, R, rl.nbd, rl.nbd), s, ra, h.E, hpar, h.qbar, st)))
+      return rc;
+    k_adj_root_rhs<<<(unsigned)std::min<long long>(4096, ((long long)R * rl.nbd + 255) / 256), 256, 0, st>>>(
+        s, ra, h.qbar, yout);
+    EO_CUDA_TRY(cudaGetLastError());
+    if ((rc = h.trace_end(TR_ROOT, st))) return rc;
+  } else if (L == 0) {  // one leaf: its boundary is the wall, no flux seeds reach it
     EO_CUDA_TRY(cudaMemsetAsync(hpar, 0, sizeof(cd) * (size_t)h.P * R * nleaf * nb, st));
+  }
   for (int l = L; l >= 1; --l) {
     MergeArgs m = merge_args_t(h, l);
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch_t<AdjUpMerge>(h.lv[l].fp32, pick_nc_t(h.shared, R, m.n3, m.zu_rows), s, m, hpar, hch, st)))
+    if ((rc = dispatch_t<AdjUpMerge>(h.lv[l].fp32, pick_nc_t(h.shared, R, m.n3, m.zu_rows, m.nbox), s, m, hpar, hch, st)))
       return rc;
     if ((rc = h.trace_end(TR_UP_MERGE, st))) return rc;
     std::swap(hpar, hch);
   }
-  const int nc = pick_nc_t(h.shared, R, ni, nb);
+  const int nc = pick_nc_t(h.shared, R, ni, nb, nleaf);
   const int ncg = (nleaf * R + nc - 1) / nc;
   int nchunk = std::max(1, std::min(h.P, (608 + ncg - 1) / ncg));
   nchunk = std::min(nchunk, h.nchunk);
@@ -496,8 +717,13 @@ eo_status adjoint_step(Handle& h, const double* yin, double* yout, int R, cudaSt
   if ((rc = h.trace_begin(st))) return rc;
   if ((rc = dispatch_t<AdjUpLeaf>(h.fp32, nc, s, h, nleaf, nchunk, ppc, hpar, h.gbar, h.part, st))) return rc;
   if ((rc = h.trace_end(TR_UP_LEAF, st))) return rc;
-  LeafGeo geo{g.nlx, g.nly, g.p, q, g.n_int, g.n_hseg, h.dDx, h.dDx + g.p * g.p, h.dDx + 2 * g.p * g.p,
-              h.dDx + 2 * g.p * g.p + q * q};
+  if (sw) {
+    if ((rc = h.trace_begin(st))) return rc;
+    k_adj_pre_sw<<<dim3(nleaf, R), 128, 0, st>>>(geo, R, g.n_nodes, h.K, nchunk, h.part, yout);
+    EO_CUDA_TRY(cudaGetLastError());
+    if ((rc = h.trace_end(TR_PRE, st))) return rc;
+    return EO_OK;
+  }
   if ((rc = h.trace_begin(st))) return rc;
   k_adj_init_wave<<<(unsigned)std::min<long long>(8192, ((long long)R * g.n_nodes + 255) / 256), 256, 0, st>>>(
       g.n_nodes, R, h.C[0], yin, yout);
@@ -513,12 +739,15 @@ eo_status adjoint_step(Handle& h, const double* yin, double* yout, int R, cudaSt
 
 eo_status apply_adjoint(Handle& h, double* y, int n_rhs, int n_steps, cudaStream_t st) {
   if (!y) return fail(EO_ERR_INVALID_ARG, "null state");
-  if (h.kind != EO_WAVE_DIRICHLET) return fail(EO_ERR_UNSUPPORTED, "the adjoint is built for the wave kind");
   if (n_rhs < 1 || n_rhs > h.R) return fail(EO_ERR_INVALID_ARG, "n_rhs out of range [1, max_rhs]");
   if (n_steps < 0) return fail(EO_ERR_INVALID_ARG, "negative n_steps");
   if (!h.gbar) {
     eo_status rc = h.alloc((void**)&h.gbar, sizeof(cd) * (size_t)h.P * h.R * h.g.n_int, false);
     if (rc) return rc;
+    if (h.kind == EO_SW_WALLS) {
+      if ((rc = h.alloc((void**)&h.abar, sizeof(double) * (size_t)h.R * 3 * h.g.n_nodes, false))) return rc;
+      if ((rc = h.alloc((void**)&h.qbar, sizeof(cd) * (size_t)h.P * h.R * h.nroot, false))) return rc;
+    }
   }
   double* cur = y;
   double* nxt = h.ustate;

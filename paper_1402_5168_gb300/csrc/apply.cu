@@ -212,9 +212,7 @@ __global__ void __launch_bounds__(256) k_down_leaf(Sweep s, const void* XYv, lon
   const int chunk = blockIdx.y;
   const TA* XY = (const TA*)XYv;
   TA* Bs = (TA*)smem;
-  cd* Cs = after(Bs, (size_t)NC * k);
-  cd* red = Cs + NC * ni;
-  double* acc = (double*)(red + (size_t)blockDim.x * NC);   // [NC][K][ni]
+  double* acc = (double*)after(Bs, (size_t)NC * k);   // [NC][K][ni], each entry owned by one thread
   for (int e = threadIdx.x; e < NC * s.K * ni; e += blockDim.x) acc[e] = 0.0;
   int box0, r0;
   col_box(c0, s.R, box0, r0);
@@ -245,13 +243,39 @@ __global__ void __launch_bounds__(256) k_down_leaf(Sweep s, const void* XYv, lon
     }
     __syncthreads();
     const TA* A = XY + (long long)p * xps + (s.shared ? 0 : (long long)box0 * xbs);
-    cmv<NC, TA>(A, ni, ni, k, Bs, k, Cs, red);
     cd w[3];
     for (int kk = 0; kk < s.K; ++kk) w[kk] = s.wgt[p * s.K + kk];
-    for (int e = threadIdx.x; e < NC * ni; e += blockDim.x) {
-      const int c = e / ni, row = e - c * ni;
-      const cd x = Cs[e];
-      for (int kk = 0; kk < s.K; ++kk) acc[(c * s.K + kk) * ni + row] += w[kk].x * x.x - w[kk].y * x.y;
+    // one row per thread, NC columns in registers; the pole-sum update goes
+    // straight from registers to the thread's own entries of acc
+    for (int row = threadIdx.x; row < ni; row += blockDim.x) {
+      typename Cv<TA>::Acc av[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) av[c] = Cv<TA>::zero();
+      const TA* Ar = A + row;
+      int j = 0;
+      for (; j + 3 < k; j += 4) {
+        const TA a0 = operator_ld(Ar + (size_t)j * ni);
+        const TA a1 = operator_ld(Ar + (size_t)(j + 1) * ni);
+        const TA a2 = operator_ld(Ar + (size_t)(j + 2) * ni);
+        const TA a3 = operator_ld(Ar + (size_t)(j + 3) * ni);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) {
+          Cv<TA>::mac(av[c], a0, Bs[c * k + j]);
+          Cv<TA>::mac(av[c], a1, Bs[c * k + j + 1]);
+          Cv<TA>::mac(av[c], a2, Bs[c * k + j + 2]);
+          Cv<TA>::mac(av[c], a3, Bs[c * k + j + 3]);
+        }
+      }
+      for (; j < k; ++j) {
+        const TA a0 = operator_ld(Ar + (size_t)j * ni);
+#pragma unroll
+        for (int c = 0; c < NC; ++c) Cv<TA>::mac(av[c], a0, Bs[c * k + j]);
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c) {
+        const cd x = Cv<TA>::to(av[c]);
+        for (int kk = 0; kk < s.K; ++kk) acc[(c * s.K + kk) * ni + row] += w[kk].x * x.x - w[kk].y * x.y;
+      }
     }
   }
   __syncthreads();
@@ -481,10 +505,15 @@ __global__ void k_zero_segments(const int* __restrict__ segs, int q, long long n
 // ---------------------------------------------------------------- host driver
 namespace {
 
-int pick_nc(int shared, int R, int k, int rows) {
+// Columns per block: with shared operators any columns can share a block, but no
+// more than the launch has (nbox * R); with per-box operators the columns of a
+// block are right-hand sides of one box, so nc must divide R.
+int pick_nc(int shared, int R, int k, int rows, int nbox = 1 << 30) {
   int nc = 1;
-  if (shared) nc = 8;
-  else {
+  if (shared) {
+    const long long ncols = (long long)nbox * R;
+    while (nc < 8 && 2 * nc <= ncols) nc *= 2;
+  } else {
     while (nc < 8 && R % (nc * 2) == 0) nc *= 2;
   }
   // keep the shared-memory footprint under ~200 KB
@@ -570,8 +599,7 @@ struct DownLeaf {
   static eo_status run(const Sweep& s, const Handle& h, int nleaf, int nchunk, int ppc, const cd* E,
                        double* part, cudaStream_t st) {
     dim3 grid((nleaf * s.R + NC - 1) / NC, nchunk);
-    const size_t smem = sizeof(cd) * ((size_t)NC * (s.ni + s.nb + s.ni) + 256 * NC) +
-                        sizeof(double) * NC * s.K * s.ni + 64;
+    const size_t smem = sizeof(TA) * ((size_t)NC * (s.ni + s.nb)) + sizeof(double) * NC * s.K * s.ni + 64;
     EO_SET_SMEM((k_down_leaf<NC, TA>), smem);
     k_down_leaf<NC, TA><<<grid, 256, smem, st>>>(s, h.aXY, h.xy_pstride, h.xy_bstride, h.lv[0].bseg, nleaf, ppc,
                                             E, part);
@@ -630,13 +658,13 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   cd* hcur = h.hA;
   cd* hnext = h.hB;
   if ((rc = h.trace_begin(st))) return rc;
-  if ((rc = dispatch<UpLeaf>(h.fp32, pick_nc(h.shared, R, ni, nb), s, h, nleaf, hcur, st))) return rc;
+  if ((rc = dispatch<UpLeaf>(h.fp32, pick_nc(h.shared, R, ni, nb, nleaf), s, h, nleaf, hcur, st))) return rc;
   if ((rc = h.trace_end(TR_UP_LEAF, st))) return rc;
   // up: merges
   for (int l = 1; l <= L; ++l) {
     MergeArgs m = merge_args(h, l);
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<UpMerge>(h.lv[l].fp32, pick_nc(h.shared, R, m.n3, m.zu_rows), s, m, hcur, hnext, st))) return rc;
+    if ((rc = dispatch<UpMerge>(h.lv[l].fp32, pick_nc(h.shared, R, m.n3, m.zu_rows, m.nbox), s, m, hcur, hnext, st))) return rc;
     if ((rc = h.trace_end(TR_UP_MERGE, st))) return rc;
     std::swap(hcur, hnext);
   }
@@ -658,11 +686,11 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   for (int l = L; l >= 1; --l) {
     MergeArgs m = merge_args(h, l);
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<DownMerge>(h.lv[l].fp32, pick_nc(h.shared, R, m.nbd, m.n3), s, m, h.E, st))) return rc;
+    if ((rc = dispatch<DownMerge>(h.lv[l].fp32, pick_nc(h.shared, R, m.nbd, m.n3, m.nbox), s, m, h.E, st))) return rc;
     if ((rc = h.trace_end(TR_DOWN_MERGE, st))) return rc;
   }
   // down: leaves with the pole sum
-  const int nc = pick_nc(h.shared, R, ni + nb, ni);
+  const int nc = pick_nc(h.shared, R, ni + nb, ni, nleaf);
   const int ncg = (nleaf * R + nc - 1) / nc;
   int nchunk = std::max(1, std::min(np, (608 + ncg - 1) / ncg));
   nchunk = std::min(nchunk, h.nchunk);

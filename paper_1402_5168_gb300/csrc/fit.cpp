@@ -204,12 +204,15 @@ static void store(const std::vector<cplx>& al, const std::vector<cplx>& b, doubl
   out.X = X; out.sigma = sigma; out.s = s;
 }
 
+static eo_status fit_wide_poles(int N, double delta, Fit& out);
+
 static const double kS[] = {0.8, 0.9, 1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6};
 static const double kRatio[] = {3.75, 4.0, 4.5, 5.0};
 
 eo_status fit_for_poles(int N, double delta, Fit& out) {
   if (N < 3 || N % 2 == 0) return fail(EO_ERR_INVALID_ARG, "n_poles must be odd and >= 3");
-  if (N > 301) return fail(EO_ERR_UNSUPPORTED, "pole counts above 301 are not supported by this fitter");
+  // beyond ~100 poles the dense search is slow and the wide construction is as good
+  if (N > 101) return fit_wide_poles(N, delta, out);
   const int M = (N - 1) / 2;
   double bestX = 0;
   std::vector<cplx> al, b;
@@ -236,7 +239,7 @@ eo_status fit_for_poles(int N, double delta, Fit& out) {
         bestX = found;
       }
     }
-  if (bestX == 0) return fail(EO_ERR_FIT, "no admissible rational approximant for this pole count");
+  if (bestX == 0) return fit_wide_poles(N, delta, out);
   return EO_OK;
 }
 
@@ -368,6 +371,25 @@ eo_status fit_wide(double X, double delta, Fit& out) {
     }
   }
   return fail(EO_ERR_FIT, "no admissible wide-band rational approximant");
+}
+
+// Pole count given and beyond the dense search: the wide construction with the
+// band that count covers, X = s M - extra, for the first candidate accepted.
+static eo_status fit_wide_poles(int N, double delta, Fit& out) {
+  static const double cand[][4] = {{1.0, 4.5, 28, 32}, {1.0, 5.0, 24, 28}, {1.0, 5.0, 28, 32},
+                                   {1.2, 4.5, 16, 24}, {1.2, 4.5, 20, 28}, {1.0, 4.5, 20, 28}};
+  const int M = (N - 1) / 2;
+  std::vector<cplx> al, b;
+  for (const auto& c : cand) {
+    const double X = c[0] * M - c[3];
+    if (X < 8.0) continue;
+    double r = 0;
+    if (wide_candidate(X, delta, c[0], c[1], (int)c[2], c[3], al, b, &r) && (int)al.size() == N) {
+      store(al, b, r, X, c[1] * c[0], c[0], out);
+      return EO_OK;
+    }
+  }
+  return fail(EO_ERR_FIT, "no admissible rational approximant for this pole count");
 }
 
 eo_status fit_for_band(double X, double delta, int nmax, Fit& out) {

@@ -89,6 +89,8 @@ struct Handle {
   double* afull = nullptr;      // SW: accumulated fields at every node [rhs][K][n_nodes]
   double* ustate = nullptr;     // second state buffer [rhs][F][n_nodes]
   cd* gbar = nullptr;           // adjoint: seeds on the leaf sources [pole][rhs][leaf][q^2]
+  double* abar = nullptr;       // adjoint (SW): seeds on the accumulated fields [rhs][3][n_nodes]
+  cd* qbar = nullptr;           // adjoint (SW): transposed wall solve [pole][rhs][n_root]
   int64_t op_bytes = 0, ws_bytes = 0;
   // tracing: events around launches, per kernel class
   bool timing = false;

@@ -119,3 +119,44 @@ def test_forward_unchanged_by_adjoint_calls():
     b = torch.tensor(u, device="cuda")
     op.apply(b, 1)
     assert torch.equal(a, b)
+
+
+def sw_op(eo, nl, p, shared, precision="fp64"):
+    g = eo.Grid(nl, nl, p)
+    op = eo.Operator(g, eo.SW_WALLS, band=60.0, n_poles=21, f=10.0, g=1.0, H=1.0, shared_ops=shared,
+                     precision=precision)
+    return g, op
+
+
+def test_sw_adjoint_matches_dense_oracle_transpose():
+    # 2x2 leaves, p = 6: the oracle's dense step matrix G (column by column), G^T y
+    import paper_1402_5168_gb300 as eo
+    from oracle.resolvent import step_matrix
+    g, op = sw_op(eo, 2, 6, False)
+    st = Stepper(Problem(sem.Grid(2, 2, 6), "sw", op.tau, f=10.0, g=1.0, H=1.0), op.alpha, op.b)
+    G = step_matrix(st)
+    rng = np.random.default_rng(31)
+    y = rng.standard_normal((3, g.n_nodes))
+    t = torch.tensor(y, device="cuda")
+    op.apply_adjoint(t, 1)
+    e = rel(t.cpu().numpy().ravel(), G.T @ y.ravel())
+    print(f"sw adjoint vs dense oracle transpose: {e:.3e}")
+    assert e <= 1e-10
+
+
+@pytest.mark.parametrize("nl,p,shared,precision", [(4, 8, True, "fp64"), (4, 8, False, "fp64"),
+                                                   (2, 10, True, "df32")])
+def test_sw_dot_product_identity(nl, p, shared, precision):
+    import paper_1402_5168_gb300 as eo
+    g, op = sw_op(eo, nl, p, shared, precision)
+    rng = np.random.default_rng(32)
+    u = rng.standard_normal((3, g.n_nodes))
+    y = rng.standard_normal((3, g.n_nodes))
+    gu = torch.tensor(u, device="cuda")
+    op.apply(gu, 2)
+    gy = torch.tensor(y, device="cuda")
+    op.apply_adjoint(gy, 2)
+    lhs = float(np.sum(y * gu.cpu().numpy()))
+    rhs = float(np.sum(gy.cpu().numpy() * u))
+    print(f"sw {nl}x{nl}/p{p} shared={shared} {precision}: <y,G^2u> {lhs:.15e} <G^T^2y,u> {rhs:.15e}")
+    assert abs(lhs - rhs) <= 1e-11 * (abs(lhs) + np.linalg.norm(y) * np.linalg.norm(u))
