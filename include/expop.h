@@ -86,6 +86,9 @@ typedef struct {
   double mem_budget_gb;/* cap on operator storage in GB (0: no cap)               */
   int fp64_top_levels; /* EO_PREC_FP32/DF32: this many top merge levels, and then also the
                           root wall solve, keep FP64 operators (0: all FP32)       */
+  int use_graphs;      /* 1: eo_apply with n_steps >= 2 records a pair of steps as a
+                          CUDA graph (per state pointer and n_rhs) and replays it;
+                          the first such call must not itself be inside a capture */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.
@@ -138,6 +141,7 @@ eo_status eo_memory(eo_handle_t h, int64_t *operator_bytes, int64_t *workspace_b
 /* Apply phase: u <- R(tau L)^n_steps u for n_rhs states in DEVICE memory
  * (u_dev: [n_rhs][fields][n_nodes] FP64, caller-owned, updated in place).
  * Stream-ordered and asynchronous with respect to the host; n_rhs <= max_rhs.
+ * With opts.use_graphs, repeated steps replay a recorded CUDA graph.
  * Each step runs two tree sweeps per distinct pole and the b_m-weighted sum.
  * Errors: EO_ERR_INVALID_ARG, EO_ERR_CUDA (launch errors only; asynchronous
  * faults surface at the caller's next synchronisation). */

@@ -545,8 +545,13 @@ int pick_nc_t(int shared, int R, int k, int rows, int nbox = 1 << 30) {
 
 #define EO_SET_SMEM_T(kern, bytes)                                                            \
   do {                                                                                        \
-    if ((bytes) > 48 * 1024)                                                                  \
-      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes))); \
+    /* raise the dynamic shared-memory cap once per kernel (outside any capture) */          \
+    static size_t cap_ = 48 * 1024;                                                           \
+    if ((bytes) > cap_) {                                                                     \
+      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 8192)); \
+      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));     \
+      cap_ = 200 * 1024 + 8192;                                                               \
+    }                                                                                         \
   } while (0)
 
 template <int NC, typename TA>

@@ -30,6 +30,8 @@ namespace eo {
 Handle::~Handle() {
   for (void* p : allocs) cudaFree(p);
   for (cudaEvent_t e : ev_pool) cudaEventDestroy(e);
+  if (graph_exec) cudaGraphExecDestroy(graph_exec);
+  if (cap_st) cudaStreamDestroy(cap_st);
 }
 
 eo_status Handle::alloc(void** p, size_t bytes, bool op) {

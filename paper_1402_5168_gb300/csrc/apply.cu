@@ -539,10 +539,15 @@ eo_status dispatch(int prec, int nc, Args&&... args) {
   return dispatch_nc<Launcher, double2>(nc, args...);
 }
 
-#define EO_SET_SMEM(kern, bytes)                                                              \
+#define EO_SET_SMEM(kern, bytes)                                                            \
   do {                                                                                        \
-    if ((bytes) > 48 * 1024)                                                                  \
-      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)(bytes))); \
+    /* raise the dynamic shared-memory cap once per kernel (outside any capture) */          \
+    static size_t cap_ = 48 * 1024;                                                           \
+    if ((bytes) > cap_) {                                                                     \
+      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 8192)); \
+      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));     \
+      cap_ = 200 * 1024 + 8192;                                                               \
+    }                                                                                         \
   } while (0)
 
 template <int NC, typename TA>
@@ -751,6 +756,33 @@ eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st) {
   double* cur = u;
   double* nxt = h.ustate;
   eo_status rc;
+  // Two or more steps and no tracing: record a pair of steps (u -> work -> u)
+  // once as a CUDA graph for this (state, n_rhs) and replay it; the launch
+  // sequence of a step is fixed, so the graph stays valid until the state
+  // pointer or n_rhs changes.
+  if (n_steps >= 2 && !h.timing && h.opts.use_graphs) {
+    if (!h.graph_exec || h.graph_u != u || h.graph_R != n_rhs) {
+      if (h.graph_exec) { cudaGraphExecDestroy(h.graph_exec); h.graph_exec = nullptr; }
+      // record on a private stream (the legacy default stream cannot be
+      // captured); the graph is then launched on the caller's stream
+      if (!h.cap_st) EO_CUDA_TRY(cudaStreamCreateWithFlags(&h.cap_st, cudaStreamNonBlocking));
+      cudaGraph_t graph;
+      EO_CUDA_TRY(cudaStreamBeginCapture(h.cap_st, cudaStreamCaptureModeThreadLocal));
+      eo_status rc1 = run_step(h, u, h.ustate, n_rhs, 0, h.P, h.wgt, h.C, h.cap_st);
+      eo_status rc2 = rc1 ? rc1 : run_step(h, h.ustate, u, n_rhs, 0, h.P, h.wgt, h.C, h.cap_st);
+      cudaError_t e = cudaStreamEndCapture(h.cap_st, &graph);
+      if (rc2) return rc2;
+      if (e != cudaSuccess) return fail(EO_ERR_CUDA, std::string("stream capture: ") + cudaGetErrorString(e));
+      e = cudaGraphInstantiate(&h.graph_exec, graph, 0);
+      cudaGraphDestroy(graph);
+      if (e != cudaSuccess) return fail(EO_ERR_CUDA, std::string("graph instantiate: ") + cudaGetErrorString(e));
+      h.graph_u = u;
+      h.graph_R = n_rhs;
+    }
+    for (int i = 0; i + 1 < n_steps; i += 2) EO_CUDA_TRY(cudaGraphLaunch(h.graph_exec, st));
+    if (n_steps % 2 == 0) return EO_OK;
+    n_steps = 1;   // one more plain step below
+  }
   for (int i = 0; i < n_steps; ++i) {
     if ((rc = run_step(h, cur, nxt, n_rhs, 0, h.P, h.wgt, h.C, st))) return rc;
     std::swap(cur, nxt);

@@ -92,6 +92,11 @@ struct Handle {
   double* abar = nullptr;       // adjoint (SW): seeds on the accumulated fields [rhs][3][n_nodes]
   cd* qbar = nullptr;           // adjoint (SW): transposed wall solve [pole][rhs][n_root]
   int64_t op_bytes = 0, ws_bytes = 0;
+  // recorded step pair (CUDA graph) for repeated applies
+  cudaGraphExec_t graph_exec = nullptr;
+  cudaStream_t cap_st = nullptr;
+  const double* graph_u = nullptr;
+  int graph_R = 0;
   // tracing: events around launches, per kernel class
   bool timing = false;
   std::vector<cudaEvent_t> ev_pool;
