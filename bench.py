@@ -91,7 +91,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def build_operator(eo, w, g, x, y, R, precision, poles=0):
+def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False):
     if w.kind == "wave":
         c = W.wave_c(w, x, y)
         return eo.Operator(g, eo.WAVE_DIRICHLET, band=W.BAND[w.name], n_poles=poles or w.n_poles, c2=c * c,
@@ -99,7 +99,8 @@ def build_operator(eo, w, g, x, y, R, precision, poles=0):
     pr = w.params
     # a pole-count override (profiling cases) replaces the fixed step by tau = X(poles) / band
     return eo.Operator(g, eo.SW_WALLS, band=W.BAND[w.name], tau=0.0 if poles else w.tau, n_poles=poles,
-                       f=pr["f"], g=pr["g"], H=pr["H"], shared_ops=True, max_rhs=R, precision=precision)
+                       f=pr["f"], g=pr["g"], H=pr["H"], shared_ops=True, max_rhs=R, precision=precision,
+                       dense_leaves=dense_leaves)
 
 
 def timed_steps(torch, op, u, steps, stream, dist):
@@ -123,43 +124,117 @@ def timed_steps(torch, op, u, steps, stream, dist):
     return ms, tim
 
 
-def roofline(op, w, R, tim, prec, pk, pk_kind):
-    """k_down_leaf: [X|Y] blocks of every distinct pole read once, applied to R
-    columns per leaf (8 flops per complex multiply-add)."""
-    dl_n, dl_ms = tim["down_leaf"]
-    avg = dl_ms / max(dl_n, 1) / 1e3
+def plan_levels(nlx, nly, q):
+    """Boxes, interface and boundary sizes of every merge level (the library's
+    plan: pairs merged alternately along x and y, from the leaves to the root)."""
+    sx = sy = 1
+    nbx, nby = nlx, nly
+    out = []
+    d = 0
+    while nbx * nby > 1:
+        dr = d
+        if dr == 0 and nbx == 1:
+            dr = 1
+        if dr == 1 and nby == 1:
+            dr = 0
+        d = 1 - dr
+        n3 = (sy if dr == 0 else sx) * q
+        if dr == 0:
+            sx, nbx = 2 * sx, nbx // 2
+        else:
+            sy, nby = 2 * sy, nby // 2
+        out.append({"nbox": nbx * nby, "n3": n3, "nbd": 2 * (sx + sy) * q})
+    return out
+
+
+def class_work(op, w, R, prec, fd):
+    """Algorithmic FP64-equivalent flops (8 per complex multiply-add) and bytes
+    of one step, per kernel class, with the arithmetic precision of each."""
     q = w.p - 2
     ni, nb = q * q, 4 * q
     P = (op.alpha.size + 1) // 2
     nleaf = w.nlx * w.nly
+    K = 2 if w.kind == "wave" else 3
     shared = w.kind == "sw"
     nlo = 1 if shared else nleaf
     esz = 8 if prec == "fp32" else 16
-    alg_bytes = P * nlo * ni * (ni + nb) * esz + P * nleaf * R * (2 * ni * 8 + nb * 16)
-    alg_flops = 8.0 * P * nleaf * R * ni * (ni + nb)
-    tf = alg_flops / avg / 1e12
-    gbs = alg_bytes / avg / 1e9
-    # FP32-pair products cost 48 FP32 instructions per complex multiply-add
-    # (4 split products of 12), so their pipe bound in FP64-equivalent flops
-    # (8 per complex multiply-add) is FP32_peak / 2 / 48 * 8
-    alu_peak = {"fp32": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS,
-                "df32": FP32_PEAK_TFLOPS / 2 / 48 * 8}[prec]
-    src = {"fp32": "FP32 FMA microbenchmark", "fp64": "FP64 FMA microbenchmark",
-           "df32": "FP32 FMA microbenchmark, 48 FP32 instructions per FP32-pair complex multiply-add"}[prec]
-    # shared operators (one block per level, reused by every leaf) make the
-    # product compute-bound; per-box FP32 blocks are read once (HBM-bound);
-    # per-box FP64 blocks are limited by the FP64 pipe
-    if shared or prec != "fp32":
-        rf = {"bound": "alu", "achieved": tf, "peak": alu_peak,
-              "unit": "TFLOP/s" + (" (FP64-equivalent)" if prec == "df32" else ""), "frac": tf / alu_peak,
-              "peak_source": src + " on this pool's GB300 (DESIGN.md)"}
+    n_int = nleaf * ni
+    cols = P * nleaf * R
+    work = {}
+    if fd:
+        # per (pole, leaf, rhs): up 4K q^2 (sources) + 32 q^2 (contractions and
+        # 1-D transforms); down 32 q^2 (edge transforms, rank-one coupling) + 4K q^2
+        work["up_leaf"] = ((4 * K + 32) * ni * cols, cols * nb * 16 + P * K * ni * 16 + R * K * n_int * 8, "fp64")
+        work["down_leaf"] = ((4 * K + 32) * ni * cols, cols * nb * 16 + P * K * ni * 16, "fp64")
     else:
-        rf = {"bound": "hbm", "achieved": gbs, "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": gbs / pk["hbm_gbs"],
+        work["up_leaf"] = (8.0 * cols * nb * ni, P * nlo * nb * ni * esz + cols * nb * 16 + R * K * n_int * 8, prec)
+        work["down_leaf"] = (8.0 * cols * ni * (ni + nb),
+                             P * nlo * ni * (ni + nb) * esz + cols * (2 * ni * 8 + nb * 16), prec)
+    lv = plan_levels(w.nlx, w.nly, q)
+    uf = ub = df = db = 0.0
+    for i, l in enumerate(lv):
+        root = i == len(lv) - 1
+        par = not (root and w.kind == "wave")
+        zu = l["n3"] + (l["nbd"] if par else 0)
+        nbo = 1 if shared else l["nbox"]
+        uf += 8.0 * P * l["nbox"] * R * zu * l["n3"]
+        ub += P * nbo * zu * l["n3"] * esz + P * l["nbox"] * R * (2 * l["n3"] + zu) * 16
+        if par:
+            df += 8.0 * P * l["nbox"] * R * l["n3"] * l["nbd"]
+            db += P * nbo * l["n3"] * l["nbd"] * esz + P * l["nbox"] * R * (l["nbd"] + l["n3"]) * 16
+    work["up_merge"] = (uf, ub, prec)
+    work["down_merge"] = (df, db, prec)
+    if w.kind == "sw":
+        nr = lv[-1]["nbd"]
+        work["root"] = (8.0 * P * R * nr * nr, P * nr * nr * esz + P * R * 2 * nr * 16, prec)
+    return work
+
+
+def alu_peak(prec):
+    # FP32-pair products cost 48 FP32 instructions per complex multiply-add (4
+    # split products of 12): pipe bound in FP64-equivalent flops FP32_peak / 2 / 48 * 8
+    return {"fp32": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS, "df32": FP32_PEAK_TFLOPS / 2 / 48 * 8}[prec]
+
+
+def roofline(op, w, R, tim, prec, pk, pk_kind, fd):
+    """Per kernel class: algorithmic work of one step over that class's device
+    time per step (CUDA events around its launches), against the ALU peak of
+    its arithmetic and the measured HBM copy bandwidth; the class with the
+    largest time share is reported as the roofline of the step."""
+    work = class_work(op, w, R, prec, fd)
+    per = {}
+    for cls, (flops, nbytes, pr) in work.items():
+        n, ms = tim.get(cls, (0, 0.0))
+        if not n:
+            continue
+        steps = max(1, tim["post_map"][0])
+        t = ms / steps / 1e3
+        tf = flops / t / 1e12
+        gbs = nbytes / t / 1e9
+        fa, fh = tf / alu_peak(pr), gbs / pk["hbm_gbs"]
+        per[cls] = {"ms_per_step": t * 1e3, "launches_per_step": n / steps, "tflops": tf, "gbs": gbs,
+                    "precision": pr, "alu_frac": fa, "hbm_frac": fh, "bound": "alu" if fa >= fh else "hbm"}
+    top = max(per, key=lambda c: per[c]["ms_per_step"])
+    d = per[top]
+    kname = {"up_leaf": "k_fd_up_leaf" if fd else "k_up_leaf", "down_leaf": "k_fd_down_leaf" if fd else "k_down_leaf",
+             "up_merge": "k_up_merge", "down_merge": "k_down_merge", "root": "k_root_sw"}[top]
+    tname = {"fp32": "float2", "fp64": "double2", "df32": "float4"}[d["precision"]]
+    if not (fd and top in ("up_leaf", "down_leaf")):
+        kname += "<%s>" % tname
+    if d["bound"] == "alu":
+        rf = {"bound": "alu", "achieved": d["tflops"], "peak": alu_peak(d["precision"]),
+              "unit": "TFLOP/s" + (" (FP64-equivalent)" if d["precision"] == "df32" else ""),
+              "frac": d["alu_frac"],
+              "peak_source": {"fp32": "FP32 FMA microbenchmark", "fp64": "FP64 FMA microbenchmark",
+                              "df32": "FP32 FMA microbenchmark, 48 FP32 instructions per FP32-pair complex "
+                                      "multiply-add"}[d["precision"]] + " on this pool's GB300 (DESIGN.md)"}
+    else:
+        rf = {"bound": "hbm", "achieved": d["gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": d["hbm_frac"],
               "peak_source": pk_kind}
-    rf.update({"kernel": "k_down_leaf<%s>" % {"fp32": "float2", "fp64": "double2", "df32": "float4"}[prec],
-               "traffic": None,
-               "algorithmic_flops": alg_flops, "algorithmic_bytes": alg_bytes, "hbm_achieved_gbs": gbs,
-               "hbm_frac": gbs / pk["hbm_gbs"], "avg_launch_ms": avg * 1e3, "launches": dl_n})
+    rf.update({"kernel": kname, "class": top, "traffic": None,
+               "algorithmic_flops": work[top][0], "algorithmic_bytes": work[top][1],
+               "avg_launch_ms": d["ms_per_step"] / d["launches_per_step"],
+               "launches": tim[top][0], "per_class": per})
     return rf
 
 
@@ -185,7 +260,7 @@ def run_ours(args):
     g = eo.Grid(w.nlx, w.nly, w.p)
     x, y = g.nodes()
     t0 = time.time()
-    op = build_operator(eo, w, g, x, y, R, args.precision, args.poles)
+    op = build_operator(eo, w, g, x, y, R, args.precision, args.poles, args.dense_leaves)
     torch.cuda.synchronize()
     build_s = time.time() - t0
     U0 = np.stack([np.stack(W.initial_fields(w, x, y, r)) for r in range(R)])
@@ -213,7 +288,7 @@ def run_ours(args):
     # the mixed path's error after the same number of steps from the same input
     fp64 = None
     if reduced and args.compare_fp64:
-        op64 = build_operator(eo, w, g, x, y, R, "fp64", args.poles)
+        op64 = build_operator(eo, w, g, x, y, R, "fp64", args.poles, args.dense_leaves)
         u64 = torch.tensor(U0, device=dev)
         for _ in range(args.warmup):
             op64.apply(u64, 1)
@@ -254,7 +329,7 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(U0.nbytes)},
         "gpu_launches": int(launches),
         "kernel_share": shares,
-        "roofline": roofline(op, w, R, tim, args.precision, pk, pk_kind),
+        "roofline": roofline(op, w, R, tim, args.precision, pk, pk_kind, fd=(w.kind == "sw" and not args.dense_leaves)),
         "clocks": clocks,
     }
     if args.cpu_baseline:
@@ -370,6 +445,8 @@ def main():
     ap.add_argument("--poles", type=int, default=0, help="override the pole count (profiling cases)")
     ap.add_argument("--leaves", type=int, default=0, help="override leaves per side (profiling cases)")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--dense-leaves", action="store_true",
+                    help="dense leaf solution operators instead of the separable leaf eigenbasis")
     ap.add_argument("--precision", default="df32", choices=["df32", "fp32", "fp64"])
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")

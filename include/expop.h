@@ -89,6 +89,11 @@ typedef struct {
   int use_graphs;      /* 1: eo_apply with n_steps >= 2 records a pair of steps as a
                           CUDA graph (per state pointer and n_rhs) and replays it;
                           the first such call must not itself be inside a capture */
+  int dense_leaves;    /* 0: with shared_ops (constant coefficient), leaf solves use
+                          the leaf's separable eigenbasis (fast diagonalisation, see
+                          eo_leaf_basis; FP64 in every precision mode); 1: the dense
+                          leaf solution operators of Section 2.3 (always used for
+                          per-box operators and by eo_apply_adjoint)              */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.
@@ -134,6 +139,18 @@ eo_status eo_fit(int n_poles, double X, double delta, int cap, double *alpha, do
  * Pass alpha = b = NULL to query n only.  Poles are ordered m = -M..M. */
 eo_status eo_get_poles(eo_handle_t h, double *alpha, double *b, int *n, double *tau,
                        double *X);
+
+/* Host-only: the separable eigenbasis of a constant-coefficient leaf.  For p
+ * Chebyshev-Lobatto points on an interval of length len and coefficient a > 0,
+ * M = a (D D)_ii, the interior (q x q, q = p - 2) block of the squared scaled
+ * differentiation matrix (the 1-D factor of the collocated div(a grad) of
+ * Section 2.2), is factored as M = V diag(lam) Vinv with real lam in descending
+ * order and unit-norm columns of V.  Caller-owned HOST arrays: lam (q doubles),
+ * V and Vinv (q*q doubles, row-major).  The leaf solve of a pole is then
+ * (V_y (x) V_x) diag(1 / (lx_a + ly_b - kappa^2)) (V_y (x) V_x)^{-1}.
+ * Errors: EO_ERR_INVALID_ARG; EO_ERR_UNSUPPORTED if the factorisation fails
+ * its residual checks. */
+eo_status eo_leaf_basis(int p, double len, double a, double *lam, double *V, double *Vinv);
 
 /* Bytes of device memory held for operators and for the apply workspace. */
 eo_status eo_memory(eo_handle_t h, int64_t *operator_bytes, int64_t *workspace_bytes);

@@ -16,7 +16,7 @@ import numpy as np
 from . import _capi
 from ._capi import SW_WALLS, WAVE_DIRICHLET, ExpopError, Opts, check
 
-__all__ = ["Grid", "Operator", "fit", "WAVE_DIRICHLET", "SW_WALLS", "ExpopError"]
+__all__ = ["Grid", "Operator", "fit", "leaf_basis", "WAVE_DIRICHLET", "SW_WALLS", "ExpopError"]
 
 
 def fit(n_poles: int = 0, X: float = 0.0, delta: float = 1e-10, cap: int = 20001):
@@ -29,6 +29,20 @@ def fit(n_poles: int = 0, X: float = 0.0, delta: float = 1e-10, cap: int = 20001
                              C.byref(Xo)))
     k = n.value
     return a[0:2 * k:2] + 1j * a[1:2 * k:2], b[0:2 * k:2] + 1j * b[1:2 * k:2], Xo.value
+
+
+def leaf_basis(p: int, length: float = 2.0, a: float = 1.0):
+    """Separable eigenbasis of a constant-coefficient leaf (host only): returns
+    (lam, V, Vinv) with a (D D)_ii = V diag(lam) Vinv on p Chebyshev-Lobatto
+    points of an interval of the given length (q = p - 2 interior points)."""
+    q = p - 2
+    lam = np.zeros(q)
+    V = np.zeros((q, q))
+    Vi = np.zeros((q, q))
+    dp = C.POINTER(C.c_double)
+    check(_capi.lib().eo_leaf_basis(p, length, a, lam.ctypes.data_as(dp), V.ctypes.data_as(dp),
+                                    Vi.ctypes.data_as(dp)))
+    return lam, V, Vi
 
 
 def _stream_ptr(stream):
@@ -70,12 +84,13 @@ class Operator:
 
     def __init__(self, grid: Grid, kind: int, band: float, n_poles: int = 0, tau: float = 0.0,
                  c2=None, f=0.0, g=1.0, H=1.0, delta=1e-10, shared_ops=False, max_rhs=1,
-                 mem_budget_gb=0.0, precision="fp64", fp64_top_levels=0, use_graphs=True, stream=None):
+                 mem_budget_gb=0.0, precision="fp64", fp64_top_levels=0, use_graphs=True, dense_leaves=False,
+                 stream=None):
         L = _capi.lib()
         prec = {"fp64": 0, "fp32": 1, "df32": 2}[precision]
         o = Opts(n_poles=n_poles, band=band, tau=tau, delta=delta, sw_f=f, sw_g=g, sw_H=H, precision=prec,
                  shared_ops=int(shared_ops), max_rhs=max_rhs, mem_budget_gb=mem_budget_gb,
-                 fp64_top_levels=fp64_top_levels, use_graphs=int(use_graphs))
+                 fp64_top_levels=fp64_top_levels, use_graphs=int(use_graphs), dense_leaves=int(dense_leaves))
         coeff = None
         if c2 is not None:
             self._c2 = np.ascontiguousarray(c2, dtype=np.float64)

@@ -15,14 +15,14 @@ WAVE_DIRICHLET, SW_WALLS = 0, 1
 # every symbol include/expop.h declares
 SYMBOLS = ("eo_fit", "eo_grid_create", "eo_grid_info", "eo_grid_nodes", "eo_grid_destroy", "eo_build_operator",
            "eo_get_poles", "eo_memory", "eo_apply", "eo_apply_adjoint", "eo_apply_host", "eo_apply_resolvent", "eo_apply_resolvent_noalloc", "eo_set_timing", "eo_get_timing", "eo_destroy",
-           "eo_last_error")
+           "eo_last_error", "eo_leaf_basis")
 
 
 class Opts(C.Structure):
     _fields_ = [("n_poles", C.c_int), ("band", C.c_double), ("tau", C.c_double), ("delta", C.c_double),
                 ("sw_f", C.c_double), ("sw_g", C.c_double), ("sw_H", C.c_double), ("precision", C.c_int),
                 ("shared_ops", C.c_int), ("max_rhs", C.c_int), ("mem_budget_gb", C.c_double),
-                ("fp64_top_levels", C.c_int), ("use_graphs", C.c_int)]
+                ("fp64_top_levels", C.c_int), ("use_graphs", C.c_int), ("dense_leaves", C.c_int)]
 
 
 _lib = None
@@ -55,6 +55,7 @@ def lib() -> C.CDLL:
         "eo_set_timing": [vp, C.c_int],
         "eo_get_timing": [vp, C.POINTER(C.c_int), C.POINTER(C.c_char_p), i64p, dp],
         "eo_destroy": [vp],
+        "eo_leaf_basis": [C.c_int, C.c_double, C.c_double, dp, dp, dp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -98,6 +98,7 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   }
   h.R = std::max(1, o.max_rhs);
   h.shared = o.shared_ops ? 1 : 0;
+  h.fd = (h.shared && !o.dense_leaves) ? 1 : 0;   // shared operators: constant coefficient
   const double tau = h.tau;
   // ---- per-pole tables
   std::vector<cd> coef, wgt, bcoef, nu;
@@ -232,6 +233,14 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   if ((rc = h.alloc((void**)&h.eacc, sizeof(double) * R * h.K * g.n_edge, false))) return rc;
   if ((rc = h.alloc((void**)&h.ustate, sizeof(double) * R * h.F * g.n_nodes, false))) return rc;
   if ((rc = h.alloc((void**)&h.pre, sizeof(double) * R * 2 * g.n_int, false))) return rc;
+  if (h.fd) {
+    if ((rc = h.alloc((void**)&h.fd_c, sizeof(double) * (4 * ni + 10 * q), true))) return rc;
+    if ((rc = h.alloc((void**)&h.fd_dinv, sizeof(cd) * P * ni, true))) return rc;
+    if ((rc = h.alloc((void**)&h.fd_dc, sizeof(cd) * P * h.K * ni, true))) return rc;
+    if ((rc = h.alloc((void**)&h.fd_wd, sizeof(cd) * P * h.K * ni, false))) return rc;
+    if ((rc = h.alloc((void**)&h.fd_gsum, sizeof(double) * h.K * h.K * ni, false))) return rc;
+    if ((rc = h.alloc((void**)&h.fd_ghat, sizeof(double) * R * h.K * g.n_int, false))) return rc;
+  }
   if (h.kind == EO_SW_WALLS) {
     if ((rc = h.alloc((void**)&h.afull, sizeof(double) * R * h.K * g.n_nodes, false))) return rc;
   } else {

@@ -663,7 +663,11 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   cd* hcur = h.hA;
   cd* hnext = h.hB;
   if ((rc = h.trace_begin(st))) return rc;
-  if ((rc = dispatch<UpLeaf>(h.fp32, pick_nc(h.shared, R, ni, nb, nleaf), s, h, nleaf, hcur, st))) return rc;
+  if (h.fd) {
+    if ((rc = fd_up_leaf(h, s, nleaf, hcur, st))) return rc;
+  } else if ((rc = dispatch<UpLeaf>(h.fp32, pick_nc(h.shared, R, ni, nb, nleaf), s, h, nleaf, hcur, st))) {
+    return rc;
+  }
   if ((rc = h.trace_end(TR_UP_LEAF, st))) return rc;
   // up: merges
   for (int l = 1; l <= L; ++l) {
@@ -695,14 +699,19 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
     if ((rc = h.trace_end(TR_DOWN_MERGE, st))) return rc;
   }
   // down: leaves with the pole sum
-  const int nc = pick_nc(h.shared, R, ni + nb, ni, nleaf);
-  const int ncg = (nleaf * R + nc - 1) / nc;
-  int nchunk = std::max(1, std::min(np, (608 + ncg - 1) / ncg));
-  nchunk = std::min(nchunk, h.nchunk);
-  const int ppc = (np + nchunk - 1) / nchunk;
-  nchunk = (np + ppc - 1) / ppc;
+  int nchunk = 1;
   if ((rc = h.trace_begin(st))) return rc;
-  if ((rc = dispatch<DownLeaf>(h.fp32, nc, s, h, nleaf, nchunk, ppc, h.E, h.part, st))) return rc;
+  if (h.fd) {
+    if ((rc = fd_down_leaf(h, s, nleaf, nchunk, st))) return rc;
+  } else {
+    const int nc = pick_nc(h.shared, R, ni + nb, ni, nleaf);
+    const int ncg = (nleaf * R + nc - 1) / nc;
+    nchunk = std::max(1, std::min(np, (608 + ncg - 1) / ncg));
+    nchunk = std::min(nchunk, h.nchunk);
+    const int ppc = (np + nchunk - 1) / nchunk;
+    nchunk = (np + ppc - 1) / ppc;
+    if ((rc = dispatch<DownLeaf>(h.fp32, nc, s, h, nleaf, nchunk, ppc, h.E, h.part, st))) return rc;
+  }
   if ((rc = h.trace_end(TR_DOWN_LEAF, st))) return rc;
   if ((rc = h.trace_begin(st))) return rc;
   k_edge_acc<<<(unsigned)std::max<long long>(1, std::min<long long>(4096, (R * g.n_edge + 255) / 256)), 256, 0, st>>>(

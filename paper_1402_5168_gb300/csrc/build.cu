@@ -327,6 +327,7 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
   leaf_real_ops<<<nlo, 256, sizeof(double) * p * p, st>>>(g.nlx, g.nly, p, g.n_int, g.n_hseg, dDx, dDy,
                                                         acoef, Aii0, Aib, Fbi, Fbb);
   EO_CUDA_TRY(cudaGetLastError());
+  if (h.fd && (rc = fd_setup(h, Aii0, Aib, Fbi, st))) return rc;
   cd* Fbi_c;
   if ((rc = talloc((void**)&Fbi_c, sizeof(cd) * nlo * nb * ni))) return rc;
   real_to_complex<<<1024, 256, 0, st>>>((size_t)nlo * nb * ni, Fbi, Fbi_c);
@@ -371,10 +372,7 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
     std::vector<cd> hk(g), ha(g);
     for (int gi = 0; gi < g; ++gi) {
       const std::complex<double> al = h.alpha[p0 + gi];
-      std::complex<double> k2;
-      if (h.kind == EO_WAVE_DIRICHLET) k2 = (al / h.tau) * (al / h.tau);
-      else k2 = (al * al + (h.tau * h.opts.sw_f) * (h.tau * h.opts.sw_f)) /
-                (h.tau * h.tau * h.opts.sw_g * h.opts.sw_H);
+      const std::complex<double> k2 = kappa2(h, p0 + gi);
       hk[gi] = make_double2(k2.real(), k2.imag());
       ha[gi] = make_double2(al.real(), al.imag());
     }

@@ -70,4 +70,10 @@ eo_status fit_for_poles(int n_poles, double delta, Fit& out);
 // Smallest pole count covering band X (n_poles <= nmax).
 eo_status fit_for_band(double X, double delta, int nmax, Fit& out);
 
+// ---------------------------------------------------------------- leaf eigenbasis
+// Real eigen-decomposition M = V diag(lam) Vinv (row-major n x n) of a matrix
+// with real, distinct eigenvalues; EO_ERR_UNSUPPORTED otherwise.
+eo_status real_eigen(int n, const std::vector<double>& M, std::vector<double>& lam, std::vector<double>& V,
+                     std::vector<double>& Vinv);
+
 }  // namespace eo

@@ -1,0 +1,539 @@
+// Leaf level by fast diagonalisation (constant-coefficient leaves, shared
+// per-level operators).
+//
+// On such a leaf the interior block of the collocated div(grad) (Section 2.2)
+// is the Kronecker sum I (x) M_x + M_y (x) I, so for every pole
+//     (A_ii - kappa_p^2)^{-1} = (V_y (x) V_x) diag(dinv_p) (V_y (x) V_x)^{-1},
+//     dinv_p(a, b) = 1 / (lx_a + ly_b - kappa_p^2),
+// and the boundary coupling A_ib and the flux rows F_bi are sums of outer
+// products of 1-D vectors.  The two leaf stages of the apply (Section 2.3)
+// then become, per pole and leaf, q-point transforms and a pointwise scaling:
+//   up:   z^ = dinv_p * sum_k coef_pk g^_k (g^ = sources in the eigenbasis),
+//         outward fluxes h_S = V_x (z^ rS^), h_N = V_x (z^ rN^),
+//                        h_E = V_y (z^T rE^), h_W = V_y (z^T rW^);
+//   down: the interior solution z_p = X g_p + Y u_b of Section 2.3 in the
+//         eigenbasis is dinv_p * (g^_p - (A_ib u_b)^), with
+//         (A_ib u_b)^(a, b) = cW^_a uW^_b + cE^_a uE^_b + uS^_a cS^_b + uN^_a cN^_b,
+//         u^ the edge values in the 1-D eigenbases; the weighted pole sum of
+//         the particular part, sum_p Re(w_pk coef_pk' dinv_p), does not depend
+//         on the leaf and is formed once per call (gsum); each chunk of poles
+//         maps its partial sum back with V_y (x) V_x.
+// All of it is FP64.  Results equal the dense leaf operators up to rounding;
+// the dense operators stay built for the adjoint sweeps.
+#include <algorithm>
+#include <cmath>
+#include <string>
+#include <vector>
+
+#include "sweep.cuh"
+
+namespace eo {
+
+// offsets (in doubles) inside the constant block h.fd_c
+struct FdLayout {
+  int q, qq;
+  __host__ __device__ int Vx() const { return 0; }
+  __host__ __device__ int Vxi() const { return qq; }
+  __host__ __device__ int Vy() const { return 2 * qq; }
+  __host__ __device__ int Vyi() const { return 3 * qq; }
+  __host__ __device__ int lx() const { return 4 * qq; }
+  __host__ __device__ int ly() const { return 4 * qq + q; }
+  __host__ __device__ int cW() const { return 4 * qq + 2 * q; }
+  __host__ __device__ int cE() const { return 4 * qq + 3 * q; }
+  __host__ __device__ int cS() const { return 4 * qq + 4 * q; }
+  __host__ __device__ int cN() const { return 4 * qq + 5 * q; }
+  __host__ __device__ int rS() const { return 4 * qq + 6 * q; }
+  __host__ __device__ int rN() const { return 4 * qq + 7 * q; }
+  __host__ __device__ int rE() const { return 4 * qq + 8 * q; }
+  __host__ __device__ int rW() const { return 4 * qq + 9 * q; }
+  __host__ __device__ int size() const { return 4 * qq + 10 * q; }   // even
+};
+
+struct FdArgs {
+  int q, K, ncol, nleaf;
+  const double* c;       // constants, FdLayout
+  const cd* dc;          // [P][K][q*q] coef[p][k] * dinv_p   (global pole index)
+  const cd* wd;          // [np][K][q*q] wgt[p][k] * dinv_p   (local pole index of the call)
+  const double* gsum;    // [K][K][q*q] sum over the call's poles of Re(wgt[p][k] coef[p][k'] dinv_p)
+  const double* ghat;    // [R][K][n_int] sources in the leaf eigenbasis
+};
+
+__host__ __device__ __forceinline__ size_t even_up(size_t n) { return (n + 1) & ~(size_t)1; }
+
+// ---------------------------------------------------------------- sources -> eigenbasis
+// ghat[r][k][leaf](a, b) = sum_{k', j} Vxi[a][k'] Vyi[b][j] src_k(leaf, r)(k', j)
+__global__ void __launch_bounds__(256) k_fd_src(Sweep s, FdArgs f, double* __restrict__ ghat) {
+  extern __shared__ double fsm[];
+  const int q = f.q, qq = q * q;
+  const int box = blockIdx.x, r = blockIdx.y;
+  const FdLayout Lo{q, qq};
+  double* Vxi = fsm;
+  double* Vyi = Vxi + qq;
+  double* G = Vyi + qq;
+  double* T = G + qq;
+  for (int e = threadIdx.x; e < qq; e += blockDim.x) {
+    Vxi[e] = f.c[Lo.Vxi() + e];
+    Vyi[e] = f.c[Lo.Vyi() + e];
+  }
+  for (int kk = 0; kk < s.K; ++kk) {
+    __syncthreads();
+    for (int e = threadIdx.x; e < qq; e += blockDim.x)
+      G[e] = s.src[kk][r * s.src_rs[kk] + (long long)box * qq + e];   // e = j q + k
+    __syncthreads();
+    for (int e = threadIdx.x; e < qq; e += blockDim.x) {
+      const int a = e % q, j = e / q;
+      double t = 0.0;
+      for (int k = 0; k < q; ++k) t += Vxi[a * q + k] * G[j * q + k];
+      T[j * q + a] = t;
+    }
+    __syncthreads();
+    for (int e = threadIdx.x; e < qq; e += blockDim.x) {
+      const int a = e % q, b = e / q;
+      double t = 0.0;
+      for (int j = 0; j < q; ++j) t += T[j * q + a] * Vyi[b * q + j];
+      ghat[((long long)(r * s.K + kk) * f.nleaf + box) * qq + e] = t;   // e = b q + a
+    }
+  }
+}
+
+// ---------------------------------------------------------------- up: leaf fluxes
+// Block: ncol columns (leaf, rhs) x q threads; thread (c, a) owns eigen row a of
+// column c.  Blocks along y take consecutive chunks of ppc poles.
+__global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, int ppc, cd* __restrict__ h0) {
+  extern __shared__ double fsm[];
+  const int q = f.q, qq = q * q, K = s.K, ncol = f.ncol;
+  const FdLayout Lo{q, qq};
+  const int c = threadIdx.x / q, a = threadIdx.x - c * q;
+  const int ncols = f.nleaf * s.R;
+  const int col = blockIdx.x * ncol + c;
+  const bool valid = col < ncols;
+  int box = 0, r = 0;
+  if (valid) col_box(col, s.R, box, r);
+  double* cst = fsm;
+  double* gs = cst + Lo.size();
+  cd* zs = (cd*)(gs + even_up((size_t)ncol * K * qq));
+  cd* ts = zs + (size_t)ncol * qq;   // [2][ncol][4][q]
+  for (int e = threadIdx.x; e < Lo.size(); e += blockDim.x) cst[e] = f.c[e];
+  for (int e = threadIdx.x; e < ncol * K * qq; e += blockDim.x) {
+    const int cc = e / (K * qq), rem = e - cc * K * qq, kk = rem / qq, idx = rem - kk * qq;
+    const int colc = blockIdx.x * ncol + cc;
+    double v = 0.0;
+    if (colc < ncols) {
+      int bx, rr;
+      col_box(colc, s.R, bx, rr);
+      v = f.ghat[((long long)(rr * K + kk) * f.nleaf + bx) * qq + idx];
+    }
+    gs[e] = v;
+  }
+  __syncthreads();
+  const double* Vx = cst + Lo.Vx();
+  const double* Vy = cst + Lo.Vy();
+  const double* rS = cst + Lo.rS();
+  const double* rN = cst + Lo.rN();
+  const double* rE = cst + Lo.rE();
+  const double* rW = cst + Lo.rW();
+  const double* g = gs + (size_t)c * K * qq;
+  cd* zc = zs + (size_t)c * qq;
+  const int pbeg = blockIdx.y * ppc, pend = min(s.P, pbeg + ppc);
+  int buf = 0;
+  for (int pl = pbeg; pl < pend; ++pl) {
+    const cd* DC = f.dc + (size_t)(s.p0 + pl) * K * qq;
+    cd* tb = ts + (size_t)(buf * ncol + c) * 4 * q;
+    // z^(a, b) = sum_k dc_k(a, b) g^_k(a, b); row contractions with rS^, rN^
+    double sr = 0, si = 0, nr = 0, ni_ = 0;
+    for (int b = 0; b < q; ++b) {
+      const int idx = b * q + a;
+      double zr = 0, zi = 0;
+      for (int kk = 0; kk < K; ++kk) {
+        const cd d = __ldg(DC + kk * qq + idx);
+        const double gv = g[kk * qq + idx];
+        zr = fma(d.x, gv, zr);
+        zi = fma(d.y, gv, zi);
+      }
+      sr = fma(zr, rS[b], sr); si = fma(zi, rS[b], si);
+      nr = fma(zr, rN[b], nr); ni_ = fma(zi, rN[b], ni_);
+      zc[idx] = make_double2(zr, zi);
+    }
+    tb[a] = make_double2(sr, si);
+    tb[2 * q + a] = make_double2(nr, ni_);
+    __syncthreads();
+    // column contractions with rE^, rW^ (thread a takes column b = a)
+    {
+      double er = 0, ei = 0, wr = 0, wi = 0;
+      for (int m = 0; m < q; ++m) {
+        const cd z = zc[a * q + m];
+        er = fma(z.x, rE[m], er); ei = fma(z.y, rE[m], ei);
+        wr = fma(z.x, rW[m], wr); wi = fma(z.y, rW[m], wi);
+      }
+      tb[q + a] = make_double2(er, ei);
+      tb[3 * q + a] = make_double2(wr, wi);
+    }
+    __syncthreads();
+    // back to nodal edge values: h_S, h_N through V_x; h_E, h_W through V_y
+    if (valid) {
+      double hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int m = 0; m < q; ++m) {
+        const double vx = Vx[a * q + m], vy = Vy[a * q + m];
+        const cd t0 = tb[m], t1 = tb[q + m], t2 = tb[2 * q + m], t3 = tb[3 * q + m];
+        hs[0] = fma(vx, t0.x, hs[0]); hs[1] = fma(vx, t0.y, hs[1]);
+        hs[2] = fma(vy, t1.x, hs[2]); hs[3] = fma(vy, t1.y, hs[3]);
+        hs[4] = fma(vx, t2.x, hs[4]); hs[5] = fma(vx, t2.y, hs[5]);
+        hs[6] = fma(vy, t3.x, hs[6]); hs[7] = fma(vy, t3.y, hs[7]);
+      }
+      cd* out = h0 + (((size_t)pl * s.R + r) * f.nleaf + box) * s.nb;
+      out[a] = make_double2(hs[0], hs[1]);           // S
+      out[q + a] = make_double2(hs[2], hs[3]);       // E
+      out[2 * q + a] = make_double2(hs[4], hs[5]);   // N
+      out[3 * q + a] = make_double2(hs[6], hs[7]);   // W
+    }
+    buf ^= 1;
+  }
+}
+
+// ---------------------------------------------------------------- down: leaf interiors + pole sum
+__global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const int* __restrict__ bseg, int ppc,
+                                                      const cd* __restrict__ E, double* __restrict__ part) {
+  extern __shared__ double fsm[];
+  const int q = f.q, qq = q * q, K = s.K, ncol = f.ncol;
+  const FdLayout Lo{q, qq};
+  const int c = threadIdx.x / q, a = threadIdx.x - c * q;
+  const int ncols = f.nleaf * s.R;
+  const int col = blockIdx.x * ncol + c;
+  const bool valid = col < ncols;
+  const int chunk = blockIdx.y;
+  int box = 0, r = 0;
+  if (valid) col_box(col, s.R, box, r);
+  double* cst = fsm;
+  double* acc = cst + Lo.size();                                  // [ncol][K][qq]
+  double* T = acc + even_up((size_t)ncol * K * qq);               // [ncol][qq]
+  cd* ub = (cd*)(T + even_up((size_t)ncol * qq));                 // [ncol][4][q]
+  cd* uh = ub + (size_t)ncol * 4 * q;                             // [ncol][4][q]
+  for (int e = threadIdx.x; e < Lo.size(); e += blockDim.x) cst[e] = f.c[e];
+  // chunk 0 starts from the pole-summed particular part, sum_k' gsum[k][k'] g^_k'
+  for (int e = threadIdx.x; e < ncol * K * qq; e += blockDim.x) {
+    const int cc = e / (K * qq), rem = e - cc * K * qq, kk = rem / qq, idx = rem - kk * qq;
+    const int colc = blockIdx.x * ncol + cc;
+    double v = 0.0;
+    if (chunk == 0 && colc < ncols) {
+      int bx, rr;
+      col_box(colc, s.R, bx, rr);
+      for (int k2 = 0; k2 < K; ++k2)
+        v = fma(f.gsum[(kk * K + k2) * qq + idx], f.ghat[((long long)(rr * K + k2) * f.nleaf + bx) * qq + idx], v);
+    }
+    acc[e] = v;
+  }
+  const double* Vxi = cst + Lo.Vxi();
+  const double* Vyi = cst + Lo.Vyi();
+  const double* cS = cst + Lo.cS();
+  const double* cN = cst + Lo.cN();
+  const double cWa = f.c[Lo.cW() + a], cEa = f.c[Lo.cE() + a];
+  cd* ubc = ub + (size_t)c * 4 * q;
+  cd* uhc = uh + (size_t)c * 4 * q;
+  double* ac = acc + (size_t)c * K * qq;
+  const int pbeg = chunk * ppc, pend = min(s.P, pbeg + ppc);
+  for (int pl = pbeg; pl < pend; ++pl) {
+    // edge values of this leaf, sides S, E, N, W
+    const cd* Ep = E + ((size_t)pl * s.R + r) * s.n_edge;
+    for (int side = 0; side < 4; ++side)
+      ubc[side * q + a] = valid ? Ep[(size_t)bseg[box * 4 + side] * q + a] : make_double2(0.0, 0.0);
+    __syncthreads();
+    // to the 1-D eigenbases: S, N along x (Vxi); E, W along y (Vyi)
+    {
+      double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      for (int m = 0; m < q; ++m) {
+        const double vx = Vxi[a * q + m], vy = Vyi[a * q + m];
+        const cd u0 = ubc[m], u1 = ubc[q + m], u2 = ubc[2 * q + m], u3 = ubc[3 * q + m];
+        v[0] = fma(vx, u0.x, v[0]); v[1] = fma(vx, u0.y, v[1]);
+        v[2] = fma(vy, u1.x, v[2]); v[3] = fma(vy, u1.y, v[3]);
+        v[4] = fma(vx, u2.x, v[4]); v[5] = fma(vx, u2.y, v[5]);
+        v[6] = fma(vy, u3.x, v[6]); v[7] = fma(vy, u3.y, v[7]);
+      }
+      uhc[a] = make_double2(v[0], v[1]);
+      uhc[q + a] = make_double2(v[2], v[3]);
+      uhc[2 * q + a] = make_double2(v[4], v[5]);
+      uhc[3 * q + a] = make_double2(v[6], v[7]);
+    }
+    __syncthreads();
+    // acc_k(a, b) -= Re(wd_k(a, b) (A_ib u_b)^(a, b))
+    const cd uSa = uhc[a], uNa = uhc[2 * q + a];
+    const cd* W = f.wd + (size_t)pl * K * qq;
+    for (int b = 0; b < q; ++b) {
+      const int idx = b * q + a;
+      const cd uE = uhc[q + b], uW = uhc[3 * q + b];
+      const double cs = cS[b], cn = cN[b];
+      double br = cWa * uW.x;
+      double bi = cWa * uW.y;
+      br = fma(cEa, uE.x, br); bi = fma(cEa, uE.y, bi);
+      br = fma(uSa.x, cs, br); bi = fma(uSa.y, cs, bi);
+      br = fma(uNa.x, cn, br); bi = fma(uNa.y, cn, bi);
+      for (int kk = 0; kk < K; ++kk) {
+        const cd w = __ldg(W + kk * qq + idx);
+        ac[kk * qq + idx] -= fma(w.x, br, -w.y * bi);
+      }
+    }
+  }
+  // partial sums back to nodal values: Z = V_x acc V_y^T
+  const double* Vx = cst + Lo.Vx();
+  const double* Vy = cst + Lo.Vy();
+  double* Tc = T + (size_t)c * qq;
+  for (int kk = 0; kk < K; ++kk) {
+    __syncthreads();
+    const double* ak = ac + kk * qq;
+    for (int j = 0; j < q; ++j) {
+      double t = 0.0;
+      for (int b = 0; b < q; ++b) t = fma(ak[b * q + a], Vy[j * q + b], t);
+      Tc[j * q + a] = t;
+    }
+    __syncthreads();
+    if (valid) {
+      double* out = part + (((size_t)chunk * s.R + r) * K + kk) * s.n_int + (size_t)box * qq;
+      for (int j = 0; j < q; ++j) {
+        double z = 0.0;
+        for (int m = 0; m < q; ++m) z = fma(Vx[a * q + m], Tc[j * q + m], z);
+        out[j * q + a] = z;
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- per-call tables
+__global__ void k_fd_wd(int np, int p0, int K, int qq, const cd* __restrict__ wgt, const cd* __restrict__ dinv,
+                        cd* __restrict__ wd) {
+  const size_t tot = (size_t)np * K * qq;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const int pl = (int)(t / ((size_t)K * qq));
+    const int rem = (int)(t - (size_t)pl * K * qq), kk = rem / qq, idx = rem - kk * qq;
+    const cd w = wgt[(p0 + pl) * K + kk], d = dinv[(size_t)(p0 + pl) * qq + idx];
+    wd[t] = make_double2(w.x * d.x - w.y * d.y, w.x * d.y + w.y * d.x);
+  }
+}
+
+__global__ void k_fd_gsum(int np, int p0, int K, int qq, const cd* __restrict__ wgt, const cd* __restrict__ coef,
+                          const cd* __restrict__ dinv, double* __restrict__ gsum) {
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= K * K * qq) return;
+  const int kk = t / (K * qq), k2 = (t / qq) % K, idx = t % qq;
+  double sum = 0.0;
+  for (int pl = 0; pl < np; ++pl) {
+    const int p = p0 + pl;
+    const cd w = wgt[p * K + kk], cf = coef[p * K + k2], d = dinv[(size_t)p * qq + idx];
+    const double wr = w.x * cf.x - w.y * cf.y, wi = w.x * cf.y + w.y * cf.x;
+    sum += wr * d.x - wi * d.y;
+  }
+  gsum[t] = sum;
+}
+
+__global__ void k_fd_dc(int P, int K, int qq, const cd* __restrict__ coef, const cd* __restrict__ dinv,
+                        cd* __restrict__ dc) {
+  const size_t tot = (size_t)P * K * qq;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
+    const int p = (int)(t / ((size_t)K * qq));
+    const int rem = (int)(t - (size_t)p * K * qq), kk = rem / qq, idx = rem - kk * qq;
+    const cd w = coef[p * K + kk], d = dinv[(size_t)p * qq + idx];
+    dc[t] = make_double2(w.x * d.x - w.y * d.y, w.x * d.y + w.y * d.x);
+  }
+}
+
+namespace {
+
+int fd_ncol(int q) { return std::max(1, 128 / q); }
+
+FdArgs fd_args(const Handle& h, int nleaf) {
+  FdArgs f;
+  f.q = h.g.q; f.K = h.K; f.ncol = fd_ncol(h.g.q); f.nleaf = nleaf;
+  f.c = h.fd_c; f.dc = h.fd_dc; f.wd = h.fd_wd; f.gsum = h.fd_gsum; f.ghat = h.fd_ghat;
+  return f;
+}
+
+template <typename Kern>
+eo_status raise_smem(Kern k, size_t bytes) {
+  if (bytes > 48 * 1024) EO_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+  return EO_OK;
+}
+
+}  // namespace
+
+size_t fd_up_smem(int q, int K) {
+  const int qq = q * q, ncol = fd_ncol(q);
+  return sizeof(double) * ((size_t)4 * qq + 10 * q + even_up((size_t)ncol * K * qq)) +
+         sizeof(cd) * ((size_t)ncol * qq + (size_t)2 * ncol * 4 * q);
+}
+
+size_t fd_down_smem(int q, int K) {
+  const int qq = q * q, ncol = fd_ncol(q);
+  return sizeof(double) * ((size_t)4 * qq + 10 * q + even_up((size_t)ncol * K * qq) + even_up((size_t)ncol * qq)) +
+         sizeof(cd) * ((size_t)2 * ncol * 4 * q);
+}
+
+eo_status fd_up_leaf(Handle& h, const Sweep& s, int nleaf, cd* h0, cudaStream_t st) {
+  const int q = h.g.q, qq = q * q;
+  FdArgs f = fd_args(h, nleaf);
+  k_fd_src<<<dim3(nleaf, s.R), 256, sizeof(double) * 4 * qq, st>>>(s, f, h.fd_ghat);
+  EO_CUDA_TRY(cudaGetLastError());
+  const int ncols = nleaf * s.R;
+  const int ngroups = (ncols + f.ncol - 1) / f.ncol;
+  int nchunk = std::max(1, std::min(s.P, (608 + ngroups - 1) / ngroups));
+  const int ppc = (s.P + nchunk - 1) / nchunk;
+  nchunk = (s.P + ppc - 1) / ppc;
+  const size_t smem = fd_up_smem(q, s.K);
+  static size_t cap = 0;
+  if (smem > cap) {
+    eo_status rc = raise_smem(k_fd_up_leaf, smem);
+    if (rc) return rc;
+    cap = smem;
+  }
+  k_fd_up_leaf<<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, ppc, h0);
+  EO_CUDA_TRY(cudaGetLastError());
+  return EO_OK;
+}
+
+eo_status fd_down_leaf(Handle& h, const Sweep& s, int nleaf, int& nchunk, cudaStream_t st) {
+  const int q = h.g.q, qq = q * q;
+  FdArgs f = fd_args(h, nleaf);
+  {
+    const size_t tot = (size_t)s.P * s.K * qq;
+    k_fd_wd<<<(unsigned)std::min<size_t>(4096, (tot + 255) / 256), 256, 0, st>>>(s.P, s.p0, s.K, qq, s.wgt,
+                                                                                 h.fd_dinv, h.fd_wd);
+    EO_CUDA_TRY(cudaGetLastError());
+    const int ng = s.K * s.K * qq;
+    k_fd_gsum<<<(ng + 127) / 128, 128, 0, st>>>(s.P, s.p0, s.K, qq, s.wgt, s.coef, h.fd_dinv, h.fd_gsum);
+    EO_CUDA_TRY(cudaGetLastError());
+  }
+  const int ncols = nleaf * s.R;
+  const int ngroups = (ncols + f.ncol - 1) / f.ncol;
+  nchunk = std::max(1, std::min(s.P, (608 + ngroups - 1) / ngroups));
+  nchunk = std::min(nchunk, h.nchunk);
+  const int ppc = (s.P + nchunk - 1) / nchunk;
+  nchunk = (s.P + ppc - 1) / ppc;
+  const size_t smem = fd_down_smem(q, s.K);
+  static size_t cap = 0;
+  if (smem > cap) {
+    eo_status rc = raise_smem(k_fd_down_leaf, smem);
+    if (rc) return rc;
+    cap = smem;
+  }
+  k_fd_down_leaf<<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, h.lv[0].bseg, ppc, h.E, h.part);
+  EO_CUDA_TRY(cudaGetLastError());
+  return EO_OK;
+}
+
+// Build-time setup from the leaf-0 real matrices the dense build assembled
+// (device, column-major: Aii0 ni x ni, Aib ni x nb, Fbi nb x ni).  Checks that
+// they are the separable forms this path assumes, then uploads the basis, the
+// 1-D coupling and flux vectors in that basis, dinv for every pole and
+// coef * dinv.
+eo_status fd_setup(Handle& h, const double* dAii0, const double* dAib, const double* dFbi, cudaStream_t st) {
+  const int p = h.g.p, q = h.g.q, qq = q * q, ni = qq, nb = 4 * q;
+  std::vector<double> Aii0((size_t)ni * ni), Aib((size_t)ni * nb), Fbi((size_t)nb * ni);
+  EO_CUDA_TRY(cudaMemcpyAsync(Aii0.data(), dAii0, sizeof(double) * Aii0.size(), cudaMemcpyDeviceToHost, st));
+  EO_CUDA_TRY(cudaMemcpyAsync(Aib.data(), dAib, sizeof(double) * Aib.size(), cudaMemcpyDeviceToHost, st));
+  EO_CUDA_TRY(cudaMemcpyAsync(Fbi.data(), dFbi, sizeof(double) * Fbi.size(), cudaMemcpyDeviceToHost, st));
+  EO_CUDA_TRY(cudaStreamSynchronize(st));
+  const double* Dx = h.Dx;
+  const double* Dy = h.Dy;
+  std::vector<double> DDx((size_t)p * p, 0.0), DDy((size_t)p * p, 0.0);
+  for (int i = 0; i < p; ++i)
+    for (int j = 0; j < p; ++j)
+      for (int l = 0; l < p; ++l) {
+        DDx[i * p + j] += Dx[i * p + l] * Dx[l * p + j];
+        DDy[i * p + j] += Dy[i * p + l] * Dy[l * p + j];
+      }
+  std::vector<double> Mx((size_t)qq), My((size_t)qq);
+  for (int i = 0; i < q; ++i)
+    for (int j = 0; j < q; ++j) {
+      Mx[i * q + j] = DDx[(i + 1) * p + (j + 1)];
+      My[i * q + j] = DDy[(i + 1) * p + (j + 1)];
+    }
+  // 1-D boundary coupling (interior row k or j) and flux (outward normal) vectors
+  std::vector<double> cW(q), cE(q), cS(q), cN(q), rS(q), rN(q), rE(q), rW(q);
+  for (int i = 0; i < q; ++i) {
+    cW[i] = DDx[(i + 1) * p + 0];
+    cE[i] = DDx[(i + 1) * p + (p - 1)];
+    cS[i] = DDy[(i + 1) * p + 0];
+    cN[i] = DDy[(i + 1) * p + (p - 1)];
+    rS[i] = -Dy[0 * p + (i + 1)];
+    rN[i] = Dy[(p - 1) * p + (i + 1)];
+    rE[i] = Dx[(p - 1) * p + (i + 1)];
+    rW[i] = -Dx[0 * p + (i + 1)];
+  }
+  // the assembled leaf must be exactly these separable forms
+  double amax = 0.0, err = 0.0;
+  for (int c = 0; c < ni; ++c)
+    for (int r = 0; r < ni; ++r) {
+      const int k = r % q, j = r / q, k2 = c % q, j2 = c / q;
+      const double v = (j == j2 ? Mx[k * q + k2] : 0.0) + (k == k2 ? My[j * q + j2] : 0.0);
+      amax = std::max(amax, std::fabs(Aii0[r + (size_t)c * ni]));
+      err = std::max(err, std::fabs(Aii0[r + (size_t)c * ni] - v));
+    }
+  for (int bi = 0; bi < nb; ++bi)
+    for (int r = 0; r < ni; ++r) {
+      const int k = r % q, j = r / q, side = bi / q, o = bi % q;
+      double v = 0.0;
+      if (side == 0) v = (k == o) ? cS[j] : 0.0;
+      else if (side == 1) v = (j == o) ? cE[k] : 0.0;
+      else if (side == 2) v = (k == o) ? cN[j] : 0.0;
+      else v = (j == o) ? cW[k] : 0.0;
+      err = std::max(err, std::fabs(Aib[r + (size_t)bi * ni] - v));
+    }
+  double fmax = 0.0, ferr = 0.0;
+  for (int r = 0; r < ni; ++r)
+    for (int t = 0; t < nb; ++t) {
+      const int k = r % q, j = r / q, side = t / q, o = t % q;
+      double v = 0.0;
+      if (side == 0) v = (k == o) ? rS[j] : 0.0;
+      else if (side == 1) v = (j == o) ? rE[k] : 0.0;
+      else if (side == 2) v = (k == o) ? rN[j] : 0.0;
+      else v = (j == o) ? rW[k] : 0.0;
+      fmax = std::max(fmax, std::fabs(Fbi[t + (size_t)r * nb]));
+      ferr = std::max(ferr, std::fabs(Fbi[t + (size_t)r * nb] - v));
+    }
+  if (err > 1e-12 * amax || ferr > 1e-12 * fmax)
+    return fail(EO_ERR_UNSUPPORTED, "fast-diagonal leaves: the leaf operator is not separable (" +
+                                        std::to_string(err / amax) + ", " + std::to_string(ferr / fmax) + ")");
+  std::vector<double> lx, Vx, Vxi, ly, Vy, Vyi;
+  eo_status rc = real_eigen(q, Mx, lx, Vx, Vxi);
+  if (rc) return rc;
+  if ((rc = real_eigen(q, My, ly, Vy, Vyi))) return rc;
+  const FdLayout Lo{q, qq};
+  std::vector<double> cst(Lo.size(), 0.0);
+  std::copy(Vx.begin(), Vx.end(), cst.begin() + Lo.Vx());
+  std::copy(Vxi.begin(), Vxi.end(), cst.begin() + Lo.Vxi());
+  std::copy(Vy.begin(), Vy.end(), cst.begin() + Lo.Vy());
+  std::copy(Vyi.begin(), Vyi.end(), cst.begin() + Lo.Vyi());
+  std::copy(lx.begin(), lx.end(), cst.begin() + Lo.lx());
+  std::copy(ly.begin(), ly.end(), cst.begin() + Lo.ly());
+  for (int a = 0; a < q; ++a) {
+    double w = 0, e = 0, s = 0, n = 0, rs = 0, rn = 0, re = 0, rw = 0;
+    for (int m = 0; m < q; ++m) {
+      w += Vxi[a * q + m] * cW[m];
+      e += Vxi[a * q + m] * cE[m];
+      s += Vyi[a * q + m] * cS[m];
+      n += Vyi[a * q + m] * cN[m];
+      rs += rS[m] * Vy[m * q + a];
+      rn += rN[m] * Vy[m * q + a];
+      re += rE[m] * Vx[m * q + a];
+      rw += rW[m] * Vx[m * q + a];
+    }
+    cst[Lo.cW() + a] = w; cst[Lo.cE() + a] = e; cst[Lo.cS() + a] = s; cst[Lo.cN() + a] = n;
+    cst[Lo.rS() + a] = rs; cst[Lo.rN() + a] = rn; cst[Lo.rE() + a] = re; cst[Lo.rW() + a] = rw;
+  }
+  EO_CUDA_TRY(cudaMemcpyAsync(h.fd_c, cst.data(), sizeof(double) * cst.size(), cudaMemcpyHostToDevice, st));
+  std::vector<cd> dinv((size_t)h.P * qq);
+  for (int j = 0; j < h.P; ++j) {
+    const std::complex<double> k2 = kappa2(h, j);
+    for (int b = 0; b < q; ++b)
+      for (int a = 0; a < q; ++a) {
+        const std::complex<double> d = 1.0 / (lx[a] + ly[b] - k2);
+        dinv[(size_t)j * qq + b * q + a] = make_double2(d.real(), d.imag());
+      }
+  }
+  EO_CUDA_TRY(cudaMemcpyAsync(h.fd_dinv, dinv.data(), sizeof(cd) * dinv.size(), cudaMemcpyHostToDevice, st));
+  const size_t tot = (size_t)h.P * h.K * qq;
+  k_fd_dc<<<(unsigned)std::min<size_t>(4096, (tot + 255) / 256), 256, 0, st>>>(h.P, h.K, qq, h.coef, h.fd_dinv,
+                                                                              h.fd_dc);
+  EO_CUDA_TRY(cudaGetLastError());
+  EO_CUDA_TRY(cudaStreamSynchronize(st));
+  return EO_OK;
+}
+
+}  // namespace eo

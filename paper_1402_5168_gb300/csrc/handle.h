@@ -91,6 +91,14 @@ struct Handle {
   cd* gbar = nullptr;           // adjoint: seeds on the leaf sources [pole][rhs][leaf][q^2]
   double* abar = nullptr;       // adjoint (SW): seeds on the accumulated fields [rhs][3][n_nodes]
   cd* qbar = nullptr;           // adjoint (SW): transposed wall solve [pole][rhs][n_root]
+  // fast-diagonalisation leaves (shared constant-coefficient operators)
+  int fd = 0;
+  double* fd_c = nullptr;       // leaf eigenbases and 1-D vectors (layout in fd.cu)
+  cd* fd_dinv = nullptr;        // [P][q*q] 1 / (lx_a + ly_b - kappa_p^2), index b*q + a
+  cd* fd_dc = nullptr;          // [P][K][q*q] coef[p][k] * dinv_p
+  cd* fd_wd = nullptr;          // workspace [P][K][q*q] pole-sum weight * dinv_p
+  double* fd_gsum = nullptr;    // workspace [K][K][q*q] pole-summed particular part
+  double* fd_ghat = nullptr;    // workspace [rhs][K][n_int] sources in the eigenbasis
   int64_t op_bytes = 0, ws_bytes = 0;
   // recorded step pair (CUDA graph) for repeated applies
   cudaGraphExec_t graph_exec = nullptr;
@@ -113,11 +121,25 @@ struct Handle {
 
 enum { TR_PRE = 0, TR_UP_LEAF, TR_UP_MERGE, TR_ROOT, TR_DOWN_MERGE, TR_DOWN_LEAF, TR_EDGE, TR_POST, TR_N };
 
+// kappa^2 of the elliptic equation div grad w - kappa^2 w = s of distinct pole j
+// (wave: (alpha/tau)^2; shallow water: (alpha^2 + (tau f)^2) / (tau^2 g H))
+inline std::complex<double> kappa2(const Handle& h, int j) {
+  const std::complex<double> al = h.alpha[j];
+  if (h.kind == EO_WAVE_DIRICHLET) return (al / h.tau) * (al / h.tau);
+  const double tf = h.tau * h.opts.sw_f;
+  return (al * al + tf * tf) / (h.tau * h.tau * h.opts.sw_g * h.opts.sw_H);
+}
+
 eo_status build(Handle& h, const double* coeff, cudaStream_t st);
 eo_status to_reduced(Handle& h, int prec, cudaStream_t st);
 eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st);
 eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStream_t st);
 eo_status apply_adjoint(Handle& h, double* y, int n_rhs, int n_steps, cudaStream_t st);
 eo_status apply_resolvent_noalloc(Handle& h, int j, const double* u, double* x, cudaStream_t st);
+// fast-diagonalisation leaves (fd.cu)
+eo_status fd_setup(Handle& h, const double* dAii0, const double* dAib, const double* dFbi, cudaStream_t st);
+struct Sweep;
+eo_status fd_up_leaf(Handle& h, const Sweep& s, int nleaf, cd* h0, cudaStream_t st);
+eo_status fd_down_leaf(Handle& h, const Sweep& s, int nleaf, int& nchunk, cudaStream_t st);
 
 }  // namespace eo
