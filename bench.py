@@ -295,11 +295,16 @@ def run_ours(args):
         ms64, _ = timed_steps(torch, op64, u64, args.steps, stream, dist)
         a = torch.tensor(U0, device=dev)
         b = torch.tensor(U0, device=dev)
-        op.apply(a, args.steps)
-        op64.apply(b, args.steps)
+        op.apply(a, 1)
+        op64.apply(b, 1)
+        err1 = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+        op.apply(a, args.steps - 1)
+        op64.apply(b, args.steps - 1)
         err = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
+        growth = float(torch.linalg.vector_norm(b) / torch.linalg.vector_norm(torch.tensor(U0, device=dev)))
         fp64 = {"value": world * R * args.steps / (ms64 / 1e3), "ms_per_step": ms64 / args.steps,
-                "mixed_vs_fp64_rel_l2": err, "after_steps": args.steps}
+                "mixed_vs_fp64_rel_l2_one_step": err1, "mixed_vs_fp64_rel_l2": err, "after_steps": args.steps,
+                "fp64_state_norm_growth": growth}
         del op64
     if rank != 0:
         dist.destroy_process_group()

@@ -99,6 +99,7 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   h.R = std::max(1, o.max_rhs);
   h.shared = o.shared_ops ? 1 : 0;
   h.fd = (h.shared && !o.dense_leaves) ? 1 : 0;   // shared operators: constant coefficient
+  h.fd_pair = (h.fd && o.precision == EO_PREC_DF32) ? 1 : 0;
   const double tau = h.tau;
   // ---- per-pole tables
   std::vector<cd> coef, wgt, bcoef, nu;

@@ -288,23 +288,35 @@ __global__ void __launch_bounds__(256) k_down_leaf(Sweep s, const void* XYv, lon
   }
 }
 
-// edge-node pole sums: eacc[r][k][e] = sum_p Re(w[p][k] E_p[r][e])
-__global__ void k_edge_acc(Sweep s, const cd* __restrict__ E, double* __restrict__ eacc) {
+// edge-node pole sums: eacc[r][k][e] = sum_p Re(w[p][k] E_p[r][e]).  A block
+// takes 32 consecutive (rhs, edge node) entries; its 8 warps stride over the
+// poles (coalesced 32-entry rows of E) and the warp partials are added in a
+// fixed order, so the sum is deterministic.
+__global__ void __launch_bounds__(256) k_edge_acc(Sweep s, const cd* __restrict__ E, double* __restrict__ eacc) {
+  __shared__ double red[8][3][32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const long long tot = (long long)s.R * s.n_edge;
-  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
-       t += (long long)gridDim.x * blockDim.x) {
-    const int r = (int)(t / s.n_edge);
-    const long long e = t - (long long)r * s.n_edge;
-    double a[3] = {0, 0, 0};
-    for (int pl = 0; pl < s.P; ++pl) {
+  const long long t = (long long)blockIdx.x * 32 + lane;
+  const bool ok = t < tot;
+  const int r = ok ? (int)(t / s.n_edge) : 0;
+  const long long e = ok ? t - (long long)r * s.n_edge : 0;
+  double a[3] = {0, 0, 0};
+  if (ok)
+    for (int pl = wp; pl < s.P; pl += 8) {
       const cd x = E[((long long)pl * s.R + r) * s.n_edge + e];
       for (int kk = 0; kk < s.K; ++kk) {
         const cd w = s.wgt[(s.p0 + pl) * s.K + kk];
-        a[kk] += w.x * x.x - w.y * x.y;
+        a[kk] = fma(w.x, x.x, fma(-w.y, x.y, a[kk]));
       }
     }
-    for (int kk = 0; kk < s.K; ++kk) eacc[((long long)r * s.K + kk) * s.n_edge + e] = a[kk];
-  }
+  for (int kk = 0; kk < s.K; ++kk) red[wp][kk][lane] = a[kk];
+  __syncthreads();
+  if (wp == 0 && ok)
+    for (int kk = 0; kk < s.K; ++kk) {
+      double v = 0.0;
+      for (int w = 0; w < 8; ++w) v += red[w][kk][lane];
+      eacc[((long long)r * s.K + kk) * s.n_edge + e] = v;
+    }
 }
 
 // accumulated field kk at node (r) from the chunk partials / edge sums
@@ -569,7 +581,7 @@ struct UpMerge {
     dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
     const size_t smem = sizeof(cd) * ((size_t)NC * (m.n3 + m.zu_rows) + 256 * NC) + 64;
     EO_SET_SMEM((k_up_merge<NC, TA>), smem);
-    k_up_merge<NC, TA><<<grid, 256, smem, st>>>(s, m, hin, hout);
+    k_up_merge<NC, TA><<<grid, cmv_threads(m.zu_rows), smem, st>>>(s, m, hin, hout);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
@@ -581,7 +593,7 @@ struct DownMerge {
     dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
     const size_t smem = sizeof(cd) * ((size_t)NC * (m.nbd + m.n3) + 256 * NC) + 64;
     EO_SET_SMEM((k_down_merge<NC, TA>), smem);
-    k_down_merge<NC, TA><<<grid, 256, smem, st>>>(s, m, E);
+    k_down_merge<NC, TA><<<grid, m.S ? cmv_threads(m.n3) : 256, smem, st>>>(s, m, E);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
@@ -593,7 +605,7 @@ struct RootSW {
     dim3 grid((s.R + NC - 1) / NC, s.P);
     const size_t smem = sizeof(cd) * ((size_t)NC * 2 * ra.n + 256 * NC) + 64;
     EO_SET_SMEM((k_root_sw<NC, TA>), smem);
-    k_root_sw<NC, TA><<<grid, 256, smem, st>>>(s, ra, hroot, E);
+    k_root_sw<NC, TA><<<grid, cmv_threads(ra.n), smem, st>>>(s, ra, hroot, E);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
@@ -714,8 +726,7 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   }
   if ((rc = h.trace_end(TR_DOWN_LEAF, st))) return rc;
   if ((rc = h.trace_begin(st))) return rc;
-  k_edge_acc<<<(unsigned)std::max<long long>(1, std::min<long long>(4096, (R * g.n_edge + 255) / 256)), 256, 0, st>>>(
-      s, h.E, h.eacc);
+  k_edge_acc<<<(unsigned)((R * g.n_edge + 31) / 32), 256, 0, st>>>(s, h.E, h.eacc);
   EO_CUDA_TRY(cudaGetLastError());
   if ((rc = h.trace_end(TR_EDGE, st))) return rc;
   if ((rc = h.trace_begin(st))) return rc;

@@ -51,9 +51,7 @@ struct FdLayout {
 
 struct FdArgs {
   int q, K, ncol, nleaf;
-  const double* c;       // constants, FdLayout
-  const cd* dc;          // [P][K][q*q] coef[p][k] * dinv_p   (global pole index)
-  const cd* wd;          // [np][K][q*q] wgt[p][k] * dinv_p   (local pole index of the call)
+  const double* c;       // constants, FdLayout (FP64)
   const double* gsum;    // [K][K][q*q] sum over the call's poles of Re(wgt[p][k] coef[p][k'] dinv_p)
   const double* ghat;    // [R][K][n_int] sources in the leaf eigenbasis
 };
@@ -96,10 +94,92 @@ __global__ void __launch_bounds__(256) k_fd_src(Sweep s, FdArgs f, double* __res
   }
 }
 
+// ---------------------------------------------------------------- arithmetic
+// The leaf kernels are written once over an arithmetic policy:
+//  - F64:  FP64 values and FMA accumulation (FP64 pipe);
+//  - Pair: FP32 (hi, lo) pairs on the FP32 pipe: every product x*y of two
+//          pairs is split exactly (p = fl(xh yh), e = fma(xh, yh, -p)) plus the
+//          cross terms xh yl + xl yh, and accumulated with an error-free
+//          two-sum into (s, c), c collecting the rounding errors and low parts
+//          (~2^-48 relative, like the FP32-pair merge products).
+// Shared-memory footprints are the same for both (8-byte reals, 16-byte complex).
+struct F64 {
+  typedef double R;
+  typedef double A;
+  typedef double2 CT;
+  __device__ static R from(double x) { return x; }
+  __device__ static double to(R x) { return x; }
+  __device__ static A zero() { return 0.0; }
+  __device__ static void mac(A& a, R x, R y) { a = fma(x, y, a); }
+  __device__ static void msub(A& a, R x, R y) { a = fma(-x, y, a); }
+  __device__ static R norm(A a) { return a; }
+  __device__ static A acc_from(double v) { return v; }
+  __device__ static double acc_to(A a) { return a; }
+  __device__ static void ldc(const CT* p, R& re, R& im) { const CT v = __ldg(p); re = v.x; im = v.y; }
+  __device__ static CT mkc(double re, double im) { return make_double2(re, im); }
+};
+
+struct PairAcc { float s, c; };
+
+struct Pair {
+  typedef float2 R;      // (hi, lo)
+  typedef PairAcc A;
+  typedef float4 CT;     // (re hi, im hi, re lo, im lo)
+  __device__ static R from(double x) {
+    const float h = __double2float_rn(x);
+    return make_float2(h, __double2float_rn(x - (double)h));
+  }
+  __device__ static double to(R x) { return (double)x.x + (double)x.y; }
+  __device__ static A zero() { return PairAcc{0.f, 0.f}; }
+  __device__ static void acc_prod(A& a, float xh, float xl, float yh, float yl) {
+    const float p = __fmul_rn(xh, yh);
+    const float e = __fmaf_rn(xh, yh, -p);
+    const float lo = __fmaf_rn(xh, yl, __fmaf_rn(xl, yh, e));
+    const float t = __fadd_rn(a.s, p);
+    const float bp = __fsub_rn(t, a.s);
+    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(p, bp));
+    a.s = t;
+    a.c = __fadd_rn(a.c, __fadd_rn(err, lo));
+  }
+  __device__ static void mac(A& a, R x, R y) { acc_prod(a, x.x, x.y, y.x, y.y); }
+  __device__ static void msub(A& a, R x, R y) { acc_prod(a, -x.x, -x.y, y.x, y.y); }
+  __device__ static R norm(A a) {
+    const float h = __fadd_rn(a.s, a.c);
+    return make_float2(h, __fsub_rn(a.c, __fsub_rn(h, a.s)));
+  }
+  __device__ static A acc_from(double v) {
+    const float h = __double2float_rn(v);
+    return PairAcc{h, __double2float_rn(v - (double)h)};
+  }
+  __device__ static double acc_to(A a) { return (double)a.s + (double)a.c; }
+  __device__ static void ldc(const CT* p, R& re, R& im) {
+    const CT v = __ldg(p);
+    re = make_float2(v.x, v.z);
+    im = make_float2(v.y, v.w);
+  }
+  __device__ static CT mkc(double re, double im) {
+    const float rh = __double2float_rn(re), ih = __double2float_rn(im);
+    return make_float4(rh, ih, __double2float_rn(re - (double)rh), __double2float_rn(im - (double)ih));
+  }
+};
+
+template <class M>
+struct Cx { typename M::R re, im; };
+
+// FP64 constants (FdLayout) -> the policy's reals
+template <class M>
+__device__ __forceinline__ void load_consts(const double* c, typename M::R* cst, int n) {
+  for (int e = threadIdx.x; e < n; e += blockDim.x) cst[e] = M::from(c[e]);
+}
+
 // ---------------------------------------------------------------- up: leaf fluxes
 // Block: ncol columns (leaf, rhs) x q threads; thread (c, a) owns eigen row a of
 // column c.  Blocks along y take consecutive chunks of ppc poles.
-__global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, int ppc, cd* __restrict__ h0) {
+template <class M>
+__global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typename M::CT* __restrict__ dct,
+                                                    int ppc, cd* __restrict__ h0) {
+  typedef typename M::R R;
+  typedef typename M::A A;
   extern __shared__ double fsm[];
   const int q = f.q, qq = q * q, K = s.K, ncol = f.ncol;
   const FdLayout Lo{q, qq};
@@ -109,11 +189,11 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, int ppc, 
   const bool valid = col < ncols;
   int box = 0, r = 0;
   if (valid) col_box(col, s.R, box, r);
-  double* cst = fsm;
-  double* gs = cst + Lo.size();
-  cd* zs = (cd*)(gs + even_up((size_t)ncol * K * qq));
-  cd* ts = zs + (size_t)ncol * qq;   // [2][ncol][4][q]
-  for (int e = threadIdx.x; e < Lo.size(); e += blockDim.x) cst[e] = f.c[e];
+  R* cst = (R*)fsm;
+  R* gs = cst + Lo.size();
+  Cx<M>* zs = (Cx<M>*)(gs + even_up((size_t)ncol * K * qq));
+  Cx<M>* ts = zs + (size_t)ncol * qq;   // [2][ncol][4][q]
+  load_consts<M>(f.c, cst, Lo.size());
   for (int e = threadIdx.x; e < ncol * K * qq; e += blockDim.x) {
     const int cc = e / (K * qq), rem = e - cc * K * qq, kk = rem / qq, idx = rem - kk * qq;
     const int colc = blockIdx.x * ncol + cc;
@@ -123,76 +203,84 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, int ppc, 
       col_box(colc, s.R, bx, rr);
       v = f.ghat[((long long)(rr * K + kk) * f.nleaf + bx) * qq + idx];
     }
-    gs[e] = v;
+    gs[e] = M::from(v);
   }
   __syncthreads();
-  const double* Vx = cst + Lo.Vx();
-  const double* Vy = cst + Lo.Vy();
-  const double* rS = cst + Lo.rS();
-  const double* rN = cst + Lo.rN();
-  const double* rE = cst + Lo.rE();
-  const double* rW = cst + Lo.rW();
-  const double* g = gs + (size_t)c * K * qq;
-  cd* zc = zs + (size_t)c * qq;
+  const R* Vx = cst + Lo.Vx();
+  const R* Vy = cst + Lo.Vy();
+  const R* rS = cst + Lo.rS();
+  const R* rN = cst + Lo.rN();
+  const R* rE = cst + Lo.rE();
+  const R* rW = cst + Lo.rW();
+  const R* g = gs + (size_t)c * K * qq;
+  Cx<M>* zc = zs + (size_t)c * qq;
   const int pbeg = blockIdx.y * ppc, pend = min(s.P, pbeg + ppc);
   int buf = 0;
   for (int pl = pbeg; pl < pend; ++pl) {
-    const cd* DC = f.dc + (size_t)(s.p0 + pl) * K * qq;
-    cd* tb = ts + (size_t)(buf * ncol + c) * 4 * q;
+    const typename M::CT* DC = dct + (size_t)(s.p0 + pl) * K * qq;
+    Cx<M>* tb = ts + (size_t)(buf * ncol + c) * 4 * q;
     // z^(a, b) = sum_k dc_k(a, b) g^_k(a, b); row contractions with rS^, rN^
-    double sr = 0, si = 0, nr = 0, ni_ = 0;
+    A sr = M::zero(), si = M::zero(), nr = M::zero(), ni_ = M::zero();
     for (int b = 0; b < q; ++b) {
       const int idx = b * q + a;
-      double zr = 0, zi = 0;
+      A zr = M::zero(), zi = M::zero();
       for (int kk = 0; kk < K; ++kk) {
-        const cd d = __ldg(DC + kk * qq + idx);
-        const double gv = g[kk * qq + idx];
-        zr = fma(d.x, gv, zr);
-        zi = fma(d.y, gv, zi);
+        R dr, di;
+        M::ldc(DC + kk * qq + idx, dr, di);
+        const R gv = g[kk * qq + idx];
+        M::mac(zr, dr, gv);
+        M::mac(zi, di, gv);
       }
-      sr = fma(zr, rS[b], sr); si = fma(zi, rS[b], si);
-      nr = fma(zr, rN[b], nr); ni_ = fma(zi, rN[b], ni_);
-      zc[idx] = make_double2(zr, zi);
+      const R zre = M::norm(zr), zim = M::norm(zi);
+      M::mac(sr, zre, rS[b]); M::mac(si, zim, rS[b]);
+      M::mac(nr, zre, rN[b]); M::mac(ni_, zim, rN[b]);
+      zc[idx] = Cx<M>{zre, zim};
     }
-    tb[a] = make_double2(sr, si);
-    tb[2 * q + a] = make_double2(nr, ni_);
+    tb[a] = Cx<M>{M::norm(sr), M::norm(si)};
+    tb[2 * q + a] = Cx<M>{M::norm(nr), M::norm(ni_)};
     __syncthreads();
     // column contractions with rE^, rW^ (thread a takes column b = a)
     {
-      double er = 0, ei = 0, wr = 0, wi = 0;
+      A er = M::zero(), ei = M::zero(), wr = M::zero(), wi = M::zero();
       for (int m = 0; m < q; ++m) {
-        const cd z = zc[a * q + m];
-        er = fma(z.x, rE[m], er); ei = fma(z.y, rE[m], ei);
-        wr = fma(z.x, rW[m], wr); wi = fma(z.y, rW[m], wi);
+        const Cx<M> z = zc[a * q + m];
+        M::mac(er, z.re, rE[m]); M::mac(ei, z.im, rE[m]);
+        M::mac(wr, z.re, rW[m]); M::mac(wi, z.im, rW[m]);
       }
-      tb[q + a] = make_double2(er, ei);
-      tb[3 * q + a] = make_double2(wr, wi);
+      tb[q + a] = Cx<M>{M::norm(er), M::norm(ei)};
+      tb[3 * q + a] = Cx<M>{M::norm(wr), M::norm(wi)};
     }
     __syncthreads();
     // back to nodal edge values: h_S, h_N through V_x; h_E, h_W through V_y
     if (valid) {
-      double hs[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      A hs[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) hs[i] = M::zero();
       for (int m = 0; m < q; ++m) {
-        const double vx = Vx[a * q + m], vy = Vy[a * q + m];
-        const cd t0 = tb[m], t1 = tb[q + m], t2 = tb[2 * q + m], t3 = tb[3 * q + m];
-        hs[0] = fma(vx, t0.x, hs[0]); hs[1] = fma(vx, t0.y, hs[1]);
-        hs[2] = fma(vy, t1.x, hs[2]); hs[3] = fma(vy, t1.y, hs[3]);
-        hs[4] = fma(vx, t2.x, hs[4]); hs[5] = fma(vx, t2.y, hs[5]);
-        hs[6] = fma(vy, t3.x, hs[6]); hs[7] = fma(vy, t3.y, hs[7]);
+        const R vx = Vx[a * q + m], vy = Vy[a * q + m];
+        const Cx<M> t0 = tb[m], t1 = tb[q + m], t2 = tb[2 * q + m], t3 = tb[3 * q + m];
+        M::mac(hs[0], vx, t0.re); M::mac(hs[1], vx, t0.im);
+        M::mac(hs[2], vy, t1.re); M::mac(hs[3], vy, t1.im);
+        M::mac(hs[4], vx, t2.re); M::mac(hs[5], vx, t2.im);
+        M::mac(hs[6], vy, t3.re); M::mac(hs[7], vy, t3.im);
       }
       cd* out = h0 + (((size_t)pl * s.R + r) * f.nleaf + box) * s.nb;
-      out[a] = make_double2(hs[0], hs[1]);           // S
-      out[q + a] = make_double2(hs[2], hs[3]);       // E
-      out[2 * q + a] = make_double2(hs[4], hs[5]);   // N
-      out[3 * q + a] = make_double2(hs[6], hs[7]);   // W
+      out[a] = make_double2(M::acc_to(hs[0]), M::acc_to(hs[1]));           // S
+      out[q + a] = make_double2(M::acc_to(hs[2]), M::acc_to(hs[3]));       // E
+      out[2 * q + a] = make_double2(M::acc_to(hs[4]), M::acc_to(hs[5]));   // N
+      out[3 * q + a] = make_double2(M::acc_to(hs[6]), M::acc_to(hs[7]));   // W
     }
     buf ^= 1;
   }
 }
 
 // ---------------------------------------------------------------- down: leaf interiors + pole sum
-__global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const int* __restrict__ bseg, int ppc,
+template <class M>
+__global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const typename M::CT* __restrict__ wdt,
+                                                      const int* __restrict__ bseg, int ppc,
                                                       const cd* __restrict__ E, double* __restrict__ part) {
+  typedef typename M::R R;
+  typedef typename M::A A;
   extern __shared__ double fsm[];
   const int q = f.q, qq = q * q, K = s.K, ncol = f.ncol;
   const FdLayout Lo{q, qq};
@@ -203,12 +291,12 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const i
   const int chunk = blockIdx.y;
   int box = 0, r = 0;
   if (valid) col_box(col, s.R, box, r);
-  double* cst = fsm;
-  double* acc = cst + Lo.size();                                  // [ncol][K][qq]
-  double* T = acc + even_up((size_t)ncol * K * qq);               // [ncol][qq]
-  cd* ub = (cd*)(T + even_up((size_t)ncol * qq));                 // [ncol][4][q]
-  cd* uh = ub + (size_t)ncol * 4 * q;                             // [ncol][4][q]
-  for (int e = threadIdx.x; e < Lo.size(); e += blockDim.x) cst[e] = f.c[e];
+  R* cst = (R*)fsm;
+  A* acc = (A*)(cst + Lo.size());                                  // [ncol][K][qq]
+  R* T = (R*)(acc + even_up((size_t)ncol * K * qq));               // [ncol][qq]
+  Cx<M>* ub = (Cx<M>*)(T + even_up((size_t)ncol * qq));            // [ncol][4][q]
+  Cx<M>* uh = ub + (size_t)ncol * 4 * q;                           // [ncol][4][q]
+  load_consts<M>(f.c, cst, Lo.size());
   // chunk 0 starts from the pole-summed particular part, sum_k' gsum[k][k'] g^_k'
   for (int e = threadIdx.x; e < ncol * K * qq; e += blockDim.x) {
     const int cc = e / (K * qq), rem = e - cc * K * qq, kk = rem / qq, idx = rem - kk * qq;
@@ -220,117 +308,143 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const i
       for (int k2 = 0; k2 < K; ++k2)
         v = fma(f.gsum[(kk * K + k2) * qq + idx], f.ghat[((long long)(rr * K + k2) * f.nleaf + bx) * qq + idx], v);
     }
-    acc[e] = v;
+    acc[e] = M::acc_from(v);
   }
-  const double* Vxi = cst + Lo.Vxi();
-  const double* Vyi = cst + Lo.Vyi();
-  const double* cS = cst + Lo.cS();
-  const double* cN = cst + Lo.cN();
-  const double cWa = f.c[Lo.cW() + a], cEa = f.c[Lo.cE() + a];
-  cd* ubc = ub + (size_t)c * 4 * q;
-  cd* uhc = uh + (size_t)c * 4 * q;
-  double* ac = acc + (size_t)c * K * qq;
+  const R* Vxi = cst + Lo.Vxi();
+  const R* Vyi = cst + Lo.Vyi();
+  const R* cS = cst + Lo.cS();
+  const R* cN = cst + Lo.cN();
+  const R cWa = M::from(f.c[Lo.cW() + a]), cEa = M::from(f.c[Lo.cE() + a]);
+  Cx<M>* ubc = ub + (size_t)c * 4 * q;
+  Cx<M>* uhc = uh + (size_t)c * 4 * q;
+  A* ac = acc + (size_t)c * K * qq;
   const int pbeg = chunk * ppc, pend = min(s.P, pbeg + ppc);
   for (int pl = pbeg; pl < pend; ++pl) {
     // edge values of this leaf, sides S, E, N, W
     const cd* Ep = E + ((size_t)pl * s.R + r) * s.n_edge;
-    for (int side = 0; side < 4; ++side)
-      ubc[side * q + a] = valid ? Ep[(size_t)bseg[box * 4 + side] * q + a] : make_double2(0.0, 0.0);
+    for (int side = 0; side < 4; ++side) {
+      const cd u = valid ? Ep[(size_t)bseg[box * 4 + side] * q + a] : make_double2(0.0, 0.0);
+      ubc[side * q + a] = Cx<M>{M::from(u.x), M::from(u.y)};
+    }
     __syncthreads();
     // to the 1-D eigenbases: S, N along x (Vxi); E, W along y (Vyi)
     {
-      double v[8] = {0, 0, 0, 0, 0, 0, 0, 0};
+      A v[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) v[i] = M::zero();
       for (int m = 0; m < q; ++m) {
-        const double vx = Vxi[a * q + m], vy = Vyi[a * q + m];
-        const cd u0 = ubc[m], u1 = ubc[q + m], u2 = ubc[2 * q + m], u3 = ubc[3 * q + m];
-        v[0] = fma(vx, u0.x, v[0]); v[1] = fma(vx, u0.y, v[1]);
-        v[2] = fma(vy, u1.x, v[2]); v[3] = fma(vy, u1.y, v[3]);
-        v[4] = fma(vx, u2.x, v[4]); v[5] = fma(vx, u2.y, v[5]);
-        v[6] = fma(vy, u3.x, v[6]); v[7] = fma(vy, u3.y, v[7]);
+        const R vx = Vxi[a * q + m], vy = Vyi[a * q + m];
+        const Cx<M> u0 = ubc[m], u1 = ubc[q + m], u2 = ubc[2 * q + m], u3 = ubc[3 * q + m];
+        M::mac(v[0], vx, u0.re); M::mac(v[1], vx, u0.im);
+        M::mac(v[2], vy, u1.re); M::mac(v[3], vy, u1.im);
+        M::mac(v[4], vx, u2.re); M::mac(v[5], vx, u2.im);
+        M::mac(v[6], vy, u3.re); M::mac(v[7], vy, u3.im);
       }
-      uhc[a] = make_double2(v[0], v[1]);
-      uhc[q + a] = make_double2(v[2], v[3]);
-      uhc[2 * q + a] = make_double2(v[4], v[5]);
-      uhc[3 * q + a] = make_double2(v[6], v[7]);
+      uhc[a] = Cx<M>{M::norm(v[0]), M::norm(v[1])};
+      uhc[q + a] = Cx<M>{M::norm(v[2]), M::norm(v[3])};
+      uhc[2 * q + a] = Cx<M>{M::norm(v[4]), M::norm(v[5])};
+      uhc[3 * q + a] = Cx<M>{M::norm(v[6]), M::norm(v[7])};
     }
     __syncthreads();
     // acc_k(a, b) -= Re(wd_k(a, b) (A_ib u_b)^(a, b))
-    const cd uSa = uhc[a], uNa = uhc[2 * q + a];
-    const cd* W = f.wd + (size_t)pl * K * qq;
+    const Cx<M> uSa = uhc[a], uNa = uhc[2 * q + a];
+    const typename M::CT* W = wdt + (size_t)pl * K * qq;
     for (int b = 0; b < q; ++b) {
       const int idx = b * q + a;
-      const cd uE = uhc[q + b], uW = uhc[3 * q + b];
-      const double cs = cS[b], cn = cN[b];
-      double br = cWa * uW.x;
-      double bi = cWa * uW.y;
-      br = fma(cEa, uE.x, br); bi = fma(cEa, uE.y, bi);
-      br = fma(uSa.x, cs, br); bi = fma(uSa.y, cs, bi);
-      br = fma(uNa.x, cn, br); bi = fma(uNa.y, cn, bi);
+      const Cx<M> uE = uhc[q + b], uW = uhc[3 * q + b];
+      const R cs = cS[b], cn = cN[b];
+      A br = M::zero(), bi = M::zero();
+      M::mac(br, cWa, uW.re); M::mac(bi, cWa, uW.im);
+      M::mac(br, cEa, uE.re); M::mac(bi, cEa, uE.im);
+      M::mac(br, uSa.re, cs); M::mac(bi, uSa.im, cs);
+      M::mac(br, uNa.re, cn); M::mac(bi, uNa.im, cn);
+      const R brn = M::norm(br), bin = M::norm(bi);
       for (int kk = 0; kk < K; ++kk) {
-        const cd w = __ldg(W + kk * qq + idx);
-        ac[kk * qq + idx] -= fma(w.x, br, -w.y * bi);
+        R wr, wi;
+        M::ldc(W + kk * qq + idx, wr, wi);
+        A t = ac[kk * qq + idx];
+        M::msub(t, wr, brn);
+        M::mac(t, wi, bin);
+        ac[kk * qq + idx] = t;
       }
     }
   }
   // partial sums back to nodal values: Z = V_x acc V_y^T
-  const double* Vx = cst + Lo.Vx();
-  const double* Vy = cst + Lo.Vy();
-  double* Tc = T + (size_t)c * qq;
+  const R* Vx = cst + Lo.Vx();
+  const R* Vy = cst + Lo.Vy();
+  R* Tc = T + (size_t)c * qq;
   for (int kk = 0; kk < K; ++kk) {
     __syncthreads();
-    const double* ak = ac + kk * qq;
+    const A* ak = ac + kk * qq;
     for (int j = 0; j < q; ++j) {
-      double t = 0.0;
-      for (int b = 0; b < q; ++b) t = fma(ak[b * q + a], Vy[j * q + b], t);
-      Tc[j * q + a] = t;
+      A t = M::zero();
+      for (int b = 0; b < q; ++b) M::mac(t, M::norm(ak[b * q + a]), Vy[j * q + b]);
+      Tc[j * q + a] = M::norm(t);
     }
     __syncthreads();
     if (valid) {
       double* out = part + (((size_t)chunk * s.R + r) * K + kk) * s.n_int + (size_t)box * qq;
       for (int j = 0; j < q; ++j) {
-        double z = 0.0;
-        for (int m = 0; m < q; ++m) z = fma(Vx[a * q + m], Tc[j * q + m], z);
-        out[j * q + a] = z;
+        A z = M::zero();
+        for (int m = 0; m < q; ++m) M::mac(z, Vx[a * q + m], Tc[j * q + m]);
+        out[j * q + a] = M::acc_to(z);
       }
     }
   }
 }
 
 // ---------------------------------------------------------------- per-call tables
+// wd[pl][k] = wgt[p0 + pl][k] * dinv_p (FP64 product, stored in the policy's format)
+template <class M>
 __global__ void k_fd_wd(int np, int p0, int K, int qq, const cd* __restrict__ wgt, const cd* __restrict__ dinv,
-                        cd* __restrict__ wd) {
+                        typename M::CT* __restrict__ wd) {
   const size_t tot = (size_t)np * K * qq;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
     const int pl = (int)(t / ((size_t)K * qq));
     const int rem = (int)(t - (size_t)pl * K * qq), kk = rem / qq, idx = rem - kk * qq;
     const cd w = wgt[(p0 + pl) * K + kk], d = dinv[(size_t)(p0 + pl) * qq + idx];
-    wd[t] = make_double2(w.x * d.x - w.y * d.y, w.x * d.y + w.y * d.x);
+    wd[t] = M::mkc(w.x * d.x - w.y * d.y, w.x * d.y + w.y * d.x);
   }
 }
 
-__global__ void k_fd_gsum(int np, int p0, int K, int qq, const cd* __restrict__ wgt, const cd* __restrict__ coef,
-                          const cd* __restrict__ dinv, double* __restrict__ gsum) {
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  if (t >= K * K * qq) return;
-  const int kk = t / (K * qq), k2 = (t / qq) % K, idx = t % qq;
+// gsum[k][k'](a, b) = sum_p Re(wgt[p][k] coef[p][k'] dinv_p(a, b)).  A block takes
+// 32 consecutive outputs; its 8 warps stride over the poles and the warp partials
+// are added in a fixed order (deterministic).
+__global__ void __launch_bounds__(256) k_fd_gsum(int np, int p0, int K, int qq, const cd* __restrict__ wgt,
+                                                 const cd* __restrict__ coef, const cd* __restrict__ dinv,
+                                                 double* __restrict__ gsum) {
+  __shared__ double red[8][32];
+  const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
+  const int t = blockIdx.x * 32 + lane;
+  const bool ok = t < K * K * qq;
+  const int kk = ok ? t / (K * qq) : 0, k2 = ok ? (t / qq) % K : 0, idx = ok ? t % qq : 0;
   double sum = 0.0;
-  for (int pl = 0; pl < np; ++pl) {
-    const int p = p0 + pl;
-    const cd w = wgt[p * K + kk], cf = coef[p * K + k2], d = dinv[(size_t)p * qq + idx];
-    const double wr = w.x * cf.x - w.y * cf.y, wi = w.x * cf.y + w.y * cf.x;
-    sum += wr * d.x - wi * d.y;
+  if (ok)
+    for (int pl = wp; pl < np; pl += 8) {
+      const int p = p0 + pl;
+      const cd w = wgt[p * K + kk], cf = coef[p * K + k2], d = dinv[(size_t)p * qq + idx];
+      const double wr = w.x * cf.x - w.y * cf.y, wi = w.x * cf.y + w.y * cf.x;
+      sum = fma(wr, d.x, fma(-wi, d.y, sum));
+    }
+  red[wp][lane] = sum;
+  __syncthreads();
+  if (wp == 0 && ok) {
+    double v = 0.0;
+    for (int w = 0; w < 8; ++w) v += red[w][lane];
+    gsum[t] = v;
   }
-  gsum[t] = sum;
 }
 
+// dc[p][k] = coef[p][k] * dinv_p (build time)
+template <class M>
 __global__ void k_fd_dc(int P, int K, int qq, const cd* __restrict__ coef, const cd* __restrict__ dinv,
-                        cd* __restrict__ dc) {
+                        typename M::CT* __restrict__ dc) {
   const size_t tot = (size_t)P * K * qq;
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot; t += (size_t)gridDim.x * blockDim.x) {
     const int p = (int)(t / ((size_t)K * qq));
     const int rem = (int)(t - (size_t)p * K * qq), kk = rem / qq, idx = rem - kk * qq;
     const cd w = coef[p * K + kk], d = dinv[(size_t)p * qq + idx];
-    dc[t] = make_double2(w.x * d.x - w.y * d.y, w.x * d.y + w.y * d.x);
+    dc[t] = M::mkc(w.x * d.x - w.y * d.y, w.x * d.y + w.y * d.x);
   }
 }
 
@@ -341,17 +455,19 @@ int fd_ncol(int q) { return std::max(1, 128 / q); }
 FdArgs fd_args(const Handle& h, int nleaf) {
   FdArgs f;
   f.q = h.g.q; f.K = h.K; f.ncol = fd_ncol(h.g.q); f.nleaf = nleaf;
-  f.c = h.fd_c; f.dc = h.fd_dc; f.wd = h.fd_wd; f.gsum = h.fd_gsum; f.ghat = h.fd_ghat;
+  f.c = h.fd_c; f.gsum = h.fd_gsum; f.ghat = h.fd_ghat;
   return f;
 }
 
 template <typename Kern>
-eo_status raise_smem(Kern k, size_t bytes) {
-  if (bytes > 48 * 1024) EO_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+eo_status raise_smem(Kern k, size_t bytes, size_t& cap) {
+  if (bytes > cap) {
+    if (bytes > 48 * 1024)
+      EO_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
+    cap = bytes;
+  }
   return EO_OK;
 }
-
-}  // namespace
 
 size_t fd_up_smem(int q, int K) {
   const int qq = q * q, ncol = fd_ncol(q);
@@ -365,56 +481,62 @@ size_t fd_down_smem(int q, int K) {
          sizeof(cd) * ((size_t)2 * ncol * 4 * q);
 }
 
-eo_status fd_up_leaf(Handle& h, const Sweep& s, int nleaf, cd* h0, cudaStream_t st) {
-  const int q = h.g.q, qq = q * q;
-  FdArgs f = fd_args(h, nleaf);
-  k_fd_src<<<dim3(nleaf, s.R), 256, sizeof(double) * 4 * qq, st>>>(s, f, h.fd_ghat);
-  EO_CUDA_TRY(cudaGetLastError());
-  const int ncols = nleaf * s.R;
+template <class M>
+eo_status up_leaf_t(Handle& h, const Sweep& s, const FdArgs& f, cd* h0, cudaStream_t st) {
+  const int q = f.q;
+  const int ncols = f.nleaf * s.R;
   const int ngroups = (ncols + f.ncol - 1) / f.ncol;
   int nchunk = std::max(1, std::min(s.P, (608 + ngroups - 1) / ngroups));
   const int ppc = (s.P + nchunk - 1) / nchunk;
   nchunk = (s.P + ppc - 1) / ppc;
   const size_t smem = fd_up_smem(q, s.K);
-  static size_t cap = 0;
-  if (smem > cap) {
-    eo_status rc = raise_smem(k_fd_up_leaf, smem);
-    if (rc) return rc;
-    cap = smem;
-  }
-  k_fd_up_leaf<<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, ppc, h0);
+  static size_t cap = 48 * 1024;
+  eo_status rc = raise_smem(k_fd_up_leaf<M>, smem, cap);
+  if (rc) return rc;
+  k_fd_up_leaf<M><<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, (const typename M::CT*)h.fd_dc, ppc, h0);
   EO_CUDA_TRY(cudaGetLastError());
   return EO_OK;
 }
 
-eo_status fd_down_leaf(Handle& h, const Sweep& s, int nleaf, int& nchunk, cudaStream_t st) {
-  const int q = h.g.q, qq = q * q;
-  FdArgs f = fd_args(h, nleaf);
-  {
-    const size_t tot = (size_t)s.P * s.K * qq;
-    k_fd_wd<<<(unsigned)std::min<size_t>(4096, (tot + 255) / 256), 256, 0, st>>>(s.P, s.p0, s.K, qq, s.wgt,
-                                                                                 h.fd_dinv, h.fd_wd);
-    EO_CUDA_TRY(cudaGetLastError());
-    const int ng = s.K * s.K * qq;
-    k_fd_gsum<<<(ng + 127) / 128, 128, 0, st>>>(s.P, s.p0, s.K, qq, s.wgt, s.coef, h.fd_dinv, h.fd_gsum);
-    EO_CUDA_TRY(cudaGetLastError());
-  }
-  const int ncols = nleaf * s.R;
+template <class M>
+eo_status down_leaf_t(Handle& h, const Sweep& s, const FdArgs& f, int& nchunk, cudaStream_t st) {
+  const int q = f.q, qq = q * q;
+  typename M::CT* wd = (typename M::CT*)h.fd_wd;
+  const size_t tot = (size_t)s.P * s.K * qq;
+  k_fd_wd<M><<<(unsigned)std::min<size_t>(4096, (tot + 255) / 256), 256, 0, st>>>(s.P, s.p0, s.K, qq, s.wgt,
+                                                                                 h.fd_dinv, wd);
+  EO_CUDA_TRY(cudaGetLastError());
+  const int ng = s.K * s.K * qq;
+  k_fd_gsum<<<(ng + 31) / 32, 256, 0, st>>>(s.P, s.p0, s.K, qq, s.wgt, s.coef, h.fd_dinv, h.fd_gsum);
+  EO_CUDA_TRY(cudaGetLastError());
+  const int ncols = f.nleaf * s.R;
   const int ngroups = (ncols + f.ncol - 1) / f.ncol;
   nchunk = std::max(1, std::min(s.P, (608 + ngroups - 1) / ngroups));
   nchunk = std::min(nchunk, h.nchunk);
   const int ppc = (s.P + nchunk - 1) / nchunk;
   nchunk = (s.P + ppc - 1) / ppc;
   const size_t smem = fd_down_smem(q, s.K);
-  static size_t cap = 0;
-  if (smem > cap) {
-    eo_status rc = raise_smem(k_fd_down_leaf, smem);
-    if (rc) return rc;
-    cap = smem;
-  }
-  k_fd_down_leaf<<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, h.lv[0].bseg, ppc, h.E, h.part);
+  static size_t cap = 48 * 1024;
+  eo_status rc = raise_smem(k_fd_down_leaf<M>, smem, cap);
+  if (rc) return rc;
+  k_fd_down_leaf<M><<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, wd, h.lv[0].bseg, ppc, h.E, h.part);
   EO_CUDA_TRY(cudaGetLastError());
   return EO_OK;
+}
+
+}  // namespace
+
+eo_status fd_up_leaf(Handle& h, const Sweep& s, int nleaf, cd* h0, cudaStream_t st) {
+  const int qq = h.g.q * h.g.q;
+  FdArgs f = fd_args(h, nleaf);
+  k_fd_src<<<dim3(nleaf, s.R), 256, sizeof(double) * 4 * qq, st>>>(s, f, h.fd_ghat);
+  EO_CUDA_TRY(cudaGetLastError());
+  return h.fd_pair ? up_leaf_t<Pair>(h, s, f, h0, st) : up_leaf_t<F64>(h, s, f, h0, st);
+}
+
+eo_status fd_down_leaf(Handle& h, const Sweep& s, int nleaf, int& nchunk, cudaStream_t st) {
+  FdArgs f = fd_args(h, nleaf);
+  return h.fd_pair ? down_leaf_t<Pair>(h, s, f, nchunk, st) : down_leaf_t<F64>(h, s, f, nchunk, st);
 }
 
 // Build-time setup from the leaf-0 real matrices the dense build assembled
@@ -529,8 +651,9 @@ eo_status fd_setup(Handle& h, const double* dAii0, const double* dAib, const dou
   }
   EO_CUDA_TRY(cudaMemcpyAsync(h.fd_dinv, dinv.data(), sizeof(cd) * dinv.size(), cudaMemcpyHostToDevice, st));
   const size_t tot = (size_t)h.P * h.K * qq;
-  k_fd_dc<<<(unsigned)std::min<size_t>(4096, (tot + 255) / 256), 256, 0, st>>>(h.P, h.K, qq, h.coef, h.fd_dinv,
-                                                                              h.fd_dc);
+  const unsigned nbk = (unsigned)std::min<size_t>(4096, (tot + 255) / 256);
+  if (h.fd_pair) k_fd_dc<Pair><<<nbk, 256, 0, st>>>(h.P, h.K, qq, h.coef, h.fd_dinv, (float4*)h.fd_dc);
+  else k_fd_dc<F64><<<nbk, 256, 0, st>>>(h.P, h.K, qq, h.coef, h.fd_dinv, h.fd_dc);
   EO_CUDA_TRY(cudaGetLastError());
   EO_CUDA_TRY(cudaStreamSynchronize(st));
   return EO_OK;

@@ -93,9 +93,10 @@ struct Handle {
   cd* qbar = nullptr;           // adjoint (SW): transposed wall solve [pole][rhs][n_root]
   // fast-diagonalisation leaves (shared constant-coefficient operators)
   int fd = 0;
+  int fd_pair = 0;              // leaf arithmetic: 0 FP64, 1 FP32 pairs (tables dc, wd then hold float4)
   double* fd_c = nullptr;       // leaf eigenbases and 1-D vectors (layout in fd.cu)
   cd* fd_dinv = nullptr;        // [P][q*q] 1 / (lx_a + ly_b - kappa_p^2), index b*q + a
-  cd* fd_dc = nullptr;          // [P][K][q*q] coef[p][k] * dinv_p
+  cd* fd_dc = nullptr;          // [P][K][q*q] coef[p][k] * dinv_p (FP64 or FP32-pair complex)
   cd* fd_wd = nullptr;          // workspace [P][K][q*q] pole-sum weight * dinv_p
   double* fd_gsum = nullptr;    // workspace [K][K][q*q] pole-summed particular part
   double* fd_ghat = nullptr;    // workspace [rhs][K][n_int] sources in the eigenbasis

@@ -102,14 +102,26 @@ __device__ __forceinline__ cd* after(T* base, size_t n) {
   return (cd*)(((uintptr_t)(base + n) + 15) & ~(uintptr_t)15);
 }
 
+// Rows per pass of cmv: the rows split into the fewest passes of at most 256,
+// each rounded up to a multiple of 16 (half-warps stay on one k group).
+__host__ __device__ __forceinline__ int cmv_rp(int rows) {
+  const int npass = (rows + 255) / 256;
+  return (((rows + npass - 1) / npass) + 15) & ~15;
+}
+// Threads of a block that runs cmv over `rows`: rp rows times the k groups that fit in 256.
+inline int cmv_threads(int rows) {
+  const int rp = cmv_rp(rows);
+  return rp * (256 / rp);
+}
+
 // C[c][r] = sum_{j<k} A[r + j*lda] B[c][j]  for r < rows, c < NC.
-// Bs: shared [NC][kb]; Cs: shared [NC][rows]; red: shared [blockDim * NC].
+// Bs: shared [NC][kb]; Cs: shared [NC][rows]; red: shared [256 * NC].
+// blockDim.x >= cmv_rp(rows); threads beyond rp * (blockDim.x / rp) idle.
 template <int NC, typename TA>
 __device__ void cmv(const TA* __restrict__ A, int lda, int rows, int k, const TA* Bs, int kb,
                     cd* Cs, cd* red) {
   const int nt = blockDim.x, t = threadIdx.x;
-  int rp = (rows + 31) & ~31;
-  if (rp > nt) rp = nt;
+  const int rp = cmv_rp(rows);
   const int ks = nt / rp;
   const int ri = t % rp, kg = t / rp;
   for (int r0 = 0; r0 < rows; r0 += rp) {

@@ -99,3 +99,27 @@ def test_fd_resolvents_match_oracle(eo):
         e = rel(xg.cpu().numpy(), st.resolvent(j, u0))
         print(f"fd resolvent j={j}: {e:.3e}")
         assert e <= 1e-10
+
+
+@pytest.mark.parametrize("nlx,nly,p", [(4, 4, 10), (2, 4, 16)])
+def test_fd_pair_arithmetic_matches_oracle(eo, nlx, nly, p):
+    """FP32-pair leaf arithmetic (precision df32): FP64-class agreement with the
+    oracle after one step and with the FP64 leaf path after four."""
+    g = eo.Grid(nlx, nly, p)
+    x, y = g.nodes()
+    kw = dict(band=60.0, n_poles=21, f=10.0, g=1.0, H=1.0, shared_ops=True)
+    op_pair = eo.Operator(g, eo.SW_WALLS, precision="df32", **kw)
+    op_64 = eo.Operator(g, eo.SW_WALLS, precision="fp64", **kw)
+    _, _, u0 = case(eo, nlx, nly, p)
+    prob = Problem(sem.Grid(nlx, nly, p), "sw", op_64.tau, f=10.0, g=1.0, H=1.0)
+    want = Stepper(prob, op_64.alpha, op_64.b).step(u0)
+    a = torch.tensor(u0, device="cuda")
+    op_pair.apply(a, 1)
+    e1 = rel(a.cpu().numpy(), want)
+    a = torch.tensor(u0, device="cuda")
+    b = torch.tensor(u0, device="cuda")
+    op_pair.apply(a, 4)
+    op_64.apply(b, 4)
+    e4 = rel(a.cpu().numpy(), b.cpu().numpy())
+    print(f"fd pair leaves {nlx}x{nly} p{p}: one step vs oracle {e1:.3e}, four steps vs fp64 {e4:.3e}")
+    assert e1 <= 1e-10 and e4 <= 1e-10
