@@ -163,9 +163,11 @@ def class_work(op, w, R, prec, fd):
     work = {}
     if fd:
         # per (pole, leaf, rhs): up 4K q^2 (sources) + 32 q^2 (contractions and
-        # 1-D transforms); down 32 q^2 (edge transforms, rank-one coupling) + 4K q^2
-        work["up_leaf"] = ((4 * K + 32) * ni * cols, cols * nb * 16 + P * K * ni * 16 + R * K * n_int * 8, "fp64")
-        work["down_leaf"] = ((4 * K + 32) * ni * cols, cols * nb * 16 + P * K * ni * 16, "fp64")
+        # 1-D transforms); down 32 q^2 (edge transforms, rank-one coupling) + 4K q^2.
+        # Arithmetic: FP32 pairs with the FP32-pair precision, FP64 otherwise
+        fp = "df32" if prec == "df32" else "fp64"
+        work["up_leaf"] = ((4 * K + 32) * ni * cols, cols * nb * 16 + P * K * ni * 16 + R * K * n_int * 8, fp)
+        work["down_leaf"] = ((4 * K + 32) * ni * cols, cols * nb * 16 + P * K * ni * 16, fp)
     else:
         work["up_leaf"] = (8.0 * cols * nb * ni, P * nlo * nb * ni * esz + cols * nb * 16 + R * K * n_int * 8, prec)
         work["down_leaf"] = (8.0 * cols * ni * (ni + nb),

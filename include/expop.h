@@ -94,6 +94,11 @@ typedef struct {
                           eo_leaf_basis; FP64 in every precision mode); 1: the dense
                           leaf solution operators of Section 2.3 (always used for
                           per-box operators and by eo_apply_adjoint)              */
+  int autotune;        /* 1: the first eo_apply (and the first with a new n_rhs) times
+                          the candidate launch shapes of every merge level and the
+                          root solve on this handle's operators and keeps the
+                          fastest (synchronises the stream once; skipped inside a
+                          stream capture); 0: fixed heuristic shapes             */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.

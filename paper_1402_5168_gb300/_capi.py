@@ -22,7 +22,8 @@ class Opts(C.Structure):
     _fields_ = [("n_poles", C.c_int), ("band", C.c_double), ("tau", C.c_double), ("delta", C.c_double),
                 ("sw_f", C.c_double), ("sw_g", C.c_double), ("sw_H", C.c_double), ("precision", C.c_int),
                 ("shared_ops", C.c_int), ("max_rhs", C.c_int), ("mem_budget_gb", C.c_double),
-                ("fp64_top_levels", C.c_int), ("use_graphs", C.c_int), ("dense_leaves", C.c_int)]
+                ("fp64_top_levels", C.c_int), ("use_graphs", C.c_int), ("dense_leaves", C.c_int),
+                ("autotune", C.c_int)]
 
 
 _lib = None

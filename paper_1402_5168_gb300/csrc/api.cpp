@@ -223,16 +223,21 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   for (int l = 0; l <= L; ++l) hmax = std::max<int64_t>(hmax, (int64_t)plan.lv[l].nbox * plan.lv[l].nbd);
   if ((rc = h.alloc((void**)&h.hA, sizeof(cd) * P * R * hmax, false))) return rc;
   if ((rc = h.alloc((void**)&h.hB, sizeof(cd) * P * R * hmax, false))) return rc;
+  // finite contents for the launch-shape autotuner, which runs on this workspace
+  EO_CUDA_TRY(cudaMemsetAsync(h.hA, 0, sizeof(cd) * P * R * hmax, st));
+  EO_CUDA_TRY(cudaMemsetAsync(h.hB, 0, sizeof(cd) * P * R * hmax, st));
   if ((rc = h.alloc((void**)&h.E, sizeof(cd) * P * R * g.n_edge, false))) return rc;
   EO_CUDA_TRY(cudaMemsetAsync(h.E, 0, sizeof(cd) * P * R * g.n_edge, st));
   for (int l = 1; l <= L; ++l) {
     LevelDev& ld = h.lv[l];
     if ((rc = h.alloc((void**)&ld.w3, sizeof(cd) * P * R * ld.nbox * ld.n3, false))) return rc;
+    EO_CUDA_TRY(cudaMemsetAsync(ld.w3, 0, sizeof(cd) * P * R * ld.nbox * ld.n3, st));
   }
   h.nchunk = (int)std::min<int64_t>(P, 64);
   if ((rc = h.alloc((void**)&h.part, sizeof(double) * h.nchunk * R * h.K * g.n_int, false))) return rc;
   if ((rc = h.alloc((void**)&h.eacc, sizeof(double) * R * h.K * g.n_edge, false))) return rc;
   if ((rc = h.alloc((void**)&h.ustate, sizeof(double) * R * h.F * g.n_nodes, false))) return rc;
+  EO_CUDA_TRY(cudaMemsetAsync(h.ustate, 0, sizeof(double) * R * h.F * g.n_nodes, st));
   if ((rc = h.alloc((void**)&h.pre, sizeof(double) * R * 2 * g.n_int, false))) return rc;
   if (h.fd) {
     if ((rc = h.alloc((void**)&h.fd_c, sizeof(double) * (4 * ni + 10 * q), true))) return rc;

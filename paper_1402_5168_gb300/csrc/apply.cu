@@ -577,11 +577,11 @@ struct UpLeaf {
 
 template <int NC, typename TA>
 struct UpMerge {
-  static eo_status run(const Sweep& s, const MergeArgs& m, const cd* hin, cd* hout, cudaStream_t st) {
+  static eo_status run(const Sweep& s, const MergeArgs& m, const cd* hin, cd* hout, int nt, cudaStream_t st) {
     dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
     const size_t smem = sizeof(cd) * ((size_t)NC * (m.n3 + m.zu_rows) + 256 * NC) + 64;
     EO_SET_SMEM((k_up_merge<NC, TA>), smem);
-    k_up_merge<NC, TA><<<grid, cmv_threads(m.zu_rows), smem, st>>>(s, m, hin, hout);
+    k_up_merge<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(m.zu_rows), smem, st>>>(s, m, hin, hout);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
@@ -589,11 +589,11 @@ struct UpMerge {
 
 template <int NC, typename TA>
 struct DownMerge {
-  static eo_status run(const Sweep& s, const MergeArgs& m, cd* E, cudaStream_t st) {
+  static eo_status run(const Sweep& s, const MergeArgs& m, cd* E, int nt, cudaStream_t st) {
     dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
     const size_t smem = sizeof(cd) * ((size_t)NC * (m.nbd + m.n3) + 256 * NC) + 64;
     EO_SET_SMEM((k_down_merge<NC, TA>), smem);
-    k_down_merge<NC, TA><<<grid, m.S ? cmv_threads(m.n3) : 256, smem, st>>>(s, m, E);
+    k_down_merge<NC, TA><<<grid, nt > 0 ? nt : (m.S ? cmv_threads(m.n3) : 256), smem, st>>>(s, m, E);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
@@ -601,11 +601,11 @@ struct DownMerge {
 
 template <int NC, typename TA>
 struct RootSW {
-  static eo_status run(const Sweep& s, const RootArgs& ra, const cd* hroot, cd* E, cudaStream_t st) {
+  static eo_status run(const Sweep& s, const RootArgs& ra, const cd* hroot, cd* E, int nt, cudaStream_t st) {
     dim3 grid((s.R + NC - 1) / NC, s.P);
     const size_t smem = sizeof(cd) * ((size_t)NC * 2 * ra.n + 256 * NC) + 64;
     EO_SET_SMEM((k_root_sw<NC, TA>), smem);
-    k_root_sw<NC, TA><<<grid, cmv_threads(ra.n), smem, st>>>(s, ra, hroot, E);
+    k_root_sw<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(ra.n), smem, st>>>(s, ra, hroot, E);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
@@ -638,6 +638,15 @@ MergeArgs merge_args(const Handle& h, int l) {
   return m;
 }
 
+Sweep base_sweep(const Handle& h, int R, int p0, int np, const cd* wgt) {
+  const Grid& g = h.g;
+  Sweep s{};
+  s.R = R; s.P = np; s.p0 = p0; s.q = g.q; s.ni = g.q * g.q; s.nb = 4 * g.q;
+  s.n_int = g.n_int; s.n_edge = g.n_edge; s.n_nodes = g.n_nodes; s.shared = h.shared;
+  s.K = h.K; s.coef = h.coef; s.wgt = wgt;
+  return s;
+}
+
 // One application of sum_p c_p (tau L - alpha_p)^{-1} restricted to poles
 // [p0, p0 + np) with accumulation weights wgt (device [P][K]) and post constants C.
 eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, int np, const cd* wgt,
@@ -647,10 +656,7 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   const int nleaf = g.nlx * g.nly;
   const int L = h.plan.L();
   eo_status rc;
-  Sweep s;
-  s.R = R; s.P = np; s.p0 = p0; s.q = q; s.ni = ni; s.nb = nb;
-  s.n_int = g.n_int; s.n_edge = g.n_edge; s.n_nodes = g.n_nodes; s.shared = h.shared;
-  s.K = h.K; s.coef = h.coef; s.wgt = wgt;
+  Sweep s = base_sweep(h, R, p0, np, wgt);
   LeafGeo geo{g.nlx, g.nly, g.p, q, g.n_int, g.n_hseg, h.dDx, h.dDx + g.p * g.p, h.dDx + 2 * g.p * g.p,
               h.dDx + 2 * g.p * g.p + q * q};
   if (h.kind == EO_WAVE_DIRICHLET) {
@@ -685,7 +691,9 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   for (int l = 1; l <= L; ++l) {
     MergeArgs m = merge_args(h, l);
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<UpMerge>(h.lv[l].fp32, pick_nc(h.shared, R, m.n3, m.zu_rows, m.nbox), s, m, hcur, hnext, st))) return rc;
+    const Tuned tu = h.lv[l].up;
+    const int nc = tu.nc ? tu.nc : pick_nc(h.shared, R, m.n3, m.zu_rows, m.nbox);
+    if ((rc = dispatch<UpMerge>(h.lv[l].fp32, nc, s, m, hcur, hnext, tu.nt, st))) return rc;
     if ((rc = h.trace_end(TR_UP_MERGE, st))) return rc;
     std::swap(hcur, hnext);
   }
@@ -700,14 +708,17 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
     const Level& rl = h.plan.lv[L];
     RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, uin, 3};
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<RootSW>(h.root_fp32, pick_nc(0, R, rl.nbd, rl.nbd), s, ra, hcur, h.E, st))) return rc;
+    const int nc = h.root_tuned.nc ? h.root_tuned.nc : pick_nc(0, R, rl.nbd, rl.nbd);
+    if ((rc = dispatch<RootSW>(h.root_fp32, nc, s, ra, hcur, h.E, h.root_tuned.nt, st))) return rc;
     if ((rc = h.trace_end(TR_ROOT, st))) return rc;
   }
   // down: merges
   for (int l = L; l >= 1; --l) {
     MergeArgs m = merge_args(h, l);
     if ((rc = h.trace_begin(st))) return rc;
-    if ((rc = dispatch<DownMerge>(h.lv[l].fp32, pick_nc(h.shared, R, m.nbd, m.n3, m.nbox), s, m, h.E, st))) return rc;
+    const Tuned tu = h.lv[l].down;
+    const int nc = tu.nc ? tu.nc : pick_nc(h.shared, R, m.nbd, m.n3, m.nbox);
+    if ((rc = dispatch<DownMerge>(h.lv[l].fp32, nc, s, m, h.E, tu.nt, st))) return rc;
     if ((rc = h.trace_end(TR_DOWN_MERGE, st))) return rc;
   }
   // down: leaves with the pole sum
@@ -769,10 +780,92 @@ eo_status Handle::trace_end(int cls, cudaStream_t st) {
   return EO_OK;
 }
 
+// Launch-shape autotuner.  For every merge level (both sweeps) and the root wall
+// solve it times each candidate shape -- columns per block (1, 2, 4, 8) times
+// k groups per row pass -- on the handle's own operators and workspace (three
+// timed launches after one warm-up, CUDA events on the stream) and keeps the
+// fastest.  It runs once per handle and n_rhs, before the first step; what it
+// leaves in the workspace is overwritten by that step.
+eo_status autotune(Handle& h, int R, cudaStream_t st) {
+  if (h.tuned_R == R || !h.opts.autotune) return EO_OK;
+  cudaStreamCaptureStatus cs;
+  EO_CUDA_TRY(cudaStreamIsCapturing(st, &cs));
+  if (cs != cudaStreamCaptureStatusNone) return EO_OK;   // keep the defaults inside a capture
+  struct Ev {
+    cudaEvent_t a = nullptr, b = nullptr;
+    ~Ev() { if (a) cudaEventDestroy(a); if (b) cudaEventDestroy(b); }
+  } ev;
+  EO_CUDA_TRY(cudaEventCreate(&ev.a));
+  EO_CUDA_TRY(cudaEventCreate(&ev.b));
+  Sweep s = base_sweep(h, R, 0, h.P, h.wgt);
+  const int L = h.plan.L();
+  // time one launch function; returns ms per launch or a negative value on error
+  auto timeit = [&](auto&& launch) -> float {
+    if (launch()) return -1.f;
+    if (cudaEventRecord(ev.a, st) != cudaSuccess) return -1.f;
+    for (int i = 0; i < 3; ++i)
+      if (launch()) return -1.f;
+    if (cudaEventRecord(ev.b, st) != cudaSuccess || cudaEventSynchronize(ev.b) != cudaSuccess) return -1.f;
+    float ms = 0.f;
+    if (cudaEventElapsedTime(&ms, ev.a, ev.b) != cudaSuccess) return -1.f;
+    return ms / 3.f;
+  };
+  auto nc_list = [&](int nbox, int k, int rows) {
+    std::vector<int> v;
+    for (int nc = 1; nc <= 8; nc *= 2) {
+      if (h.shared ? (nc > 1 && (long long)nbox * R < nc) : (R % nc != 0)) continue;
+      if ((size_t)nc * (k + rows + 256) * sizeof(cd) > 200 * 1024) continue;
+      v.push_back(nc);
+    }
+    return v;
+  };
+  auto nt_list = [&](int rows) {
+    std::vector<int> v;
+    const int rp = cmv_rp(rows);
+    for (int ks = 1; ks <= 16 && rp * ks <= 256; ks *= 2) v.push_back(rp * ks);
+    return v;
+  };
+  for (int l = 1; l <= L; ++l) {
+    MergeArgs m = merge_args(h, l);
+    LevelDev& ld = h.lv[l];
+    float best = 1e30f;
+    for (int nc : nc_list(m.nbox, m.n3, m.zu_rows))
+      for (int nt : nt_list(m.zu_rows)) {
+        const float t = timeit([&] { return dispatch<UpMerge>(ld.fp32, nc, s, m, h.hA, h.hB, nt, st); });
+        if (t < 0) return fail(EO_ERR_CUDA, "autotune: merge launch failed");
+        if (t < best) { best = t; ld.up = Tuned{nc, nt}; }
+      }
+    if (!m.S) continue;
+    best = 1e30f;
+    for (int nc : nc_list(m.nbox, m.nbd, m.n3))
+      for (int nt : nt_list(m.n3)) {
+        const float t = timeit([&] { return dispatch<DownMerge>(ld.fp32, nc, s, m, h.E, nt, st); });
+        if (t < 0) return fail(EO_ERR_CUDA, "autotune: merge launch failed");
+        if (t < best) { best = t; ld.down = Tuned{nc, nt}; }
+      }
+  }
+  if (h.kind == EO_SW_WALLS) {
+    const Level& rl = h.plan.lv[L];
+    RootArgs ra{rl.nbd, h.g.q, rl.sx * h.g.q, rl.sy * h.g.q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, h.ustate, 3};
+    float best = 1e30f;
+    for (int nc = 1; nc <= 8 && nc <= R; nc *= 2)
+      for (int nt : nt_list(rl.nbd)) {
+        if ((size_t)nc * (2 * rl.nbd + 256) * sizeof(cd) > 200 * 1024) continue;
+        const float t = timeit([&] { return dispatch<RootSW>(h.root_fp32, nc, s, ra, h.hA, h.E, nt, st); });
+        if (t < 0) return fail(EO_ERR_CUDA, "autotune: root launch failed");
+        if (t < best) { best = t; h.root_tuned = Tuned{nc, nt}; }
+      }
+  }
+  h.tuned_R = R;
+  return EO_OK;
+}
+
 eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st) {
   if (!u) return fail(EO_ERR_INVALID_ARG, "null state");
   if (n_rhs < 1 || n_rhs > h.R) return fail(EO_ERR_INVALID_ARG, "n_rhs out of range [1, max_rhs]");
   if (n_steps < 0) return fail(EO_ERR_INVALID_ARG, "negative n_steps");
+  eo_status rc0 = autotune(h, n_rhs, st);
+  if (rc0) return rc0;
   double* cur = u;
   double* nxt = h.ustate;
   eo_status rc;

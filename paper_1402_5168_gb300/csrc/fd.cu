@@ -58,6 +58,15 @@ struct FdArgs {
 
 __host__ __device__ __forceinline__ size_t even_up(size_t n) { return (n + 1) & ~(size_t)1; }
 
+// 16-byte asynchronous global -> shared copies (per-pole tables and edge values
+// of the next pole are fetched while the current pole computes)
+__device__ __forceinline__ void cp_async16(void* smem_dst, const void* gsrc) {
+  const unsigned d = (unsigned)__cvta_generic_to_shared(smem_dst);
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d), "l"(gsrc) : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::: "memory"); }
+
 // ---------------------------------------------------------------- sources -> eigenbasis
 // ghat[r][k][leaf](a, b) = sum_{k', j} Vxi[a][k'] Vyi[b][j] src_k(leaf, r)(k', j)
 __global__ void __launch_bounds__(256) k_fd_src(Sweep s, FdArgs f, double* __restrict__ ghat) {
@@ -116,6 +125,7 @@ struct F64 {
   __device__ static A acc_from(double v) { return v; }
   __device__ static double acc_to(A a) { return a; }
   __device__ static void ldc(const CT* p, R& re, R& im) { const CT v = __ldg(p); re = v.x; im = v.y; }
+  __device__ static void lds(const CT* p, R& re, R& im) { const CT v = *p; re = v.x; im = v.y; }
   __device__ static CT mkc(double re, double im) { return make_double2(re, im); }
 };
 
@@ -157,6 +167,11 @@ struct Pair {
     re = make_float2(v.x, v.z);
     im = make_float2(v.y, v.w);
   }
+  __device__ static void lds(const CT* p, R& re, R& im) {
+    const CT v = *p;
+    re = make_float2(v.x, v.z);
+    im = make_float2(v.y, v.w);
+  }
   __device__ static CT mkc(double re, double im) {
     const float rh = __double2float_rn(re), ih = __double2float_rn(im);
     return make_float4(rh, ih, __double2float_rn(re - (double)rh), __double2float_rn(im - (double)ih));
@@ -193,6 +208,7 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typ
   R* gs = cst + Lo.size();
   Cx<M>* zs = (Cx<M>*)(gs + even_up((size_t)ncol * K * qq));
   Cx<M>* ts = zs + (size_t)ncol * qq;   // [2][ncol][4][q]
+  typename M::CT* dcs = (typename M::CT*)(ts + (size_t)2 * ncol * 4 * q);   // [2][K][qq] pole tables
   load_consts<M>(f.c, cst, Lo.size());
   for (int e = threadIdx.x; e < ncol * K * qq; e += blockDim.x) {
     const int cc = e / (K * qq), rem = e - cc * K * qq, kk = rem / qq, idx = rem - kk * qq;
@@ -215,9 +231,21 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typ
   const R* g = gs + (size_t)c * K * qq;
   Cx<M>* zc = zs + (size_t)c * qq;
   const int pbeg = blockIdx.y * ppc, pend = min(s.P, pbeg + ppc);
+  auto prefetch = [&](int pl, int bf) {
+    const typename M::CT* src = dct + (size_t)(s.p0 + pl) * K * qq;
+    typename M::CT* dst = dcs + (size_t)bf * K * qq;
+    for (int e = threadIdx.x; e < K * qq; e += blockDim.x) cp_async16(dst + e, src + e);
+    cp_async_commit();
+  };
+  if (pbeg < pend) prefetch(pbeg, 0);
   int buf = 0;
   for (int pl = pbeg; pl < pend; ++pl) {
-    const typename M::CT* DC = dct + (size_t)(s.p0 + pl) * K * qq;
+    // this pole's table has landed; every thread is past the previous pole,
+    // so the other buffer can take the next pole's table
+    cp_async_wait_all();
+    __syncthreads();
+    if (pl + 1 < pend) prefetch(pl + 1, buf ^ 1);
+    const typename M::CT* DC = dcs + (size_t)buf * K * qq;
     Cx<M>* tb = ts + (size_t)(buf * ncol + c) * 4 * q;
     // z^(a, b) = sum_k dc_k(a, b) g^_k(a, b); row contractions with rS^, rN^
     A sr = M::zero(), si = M::zero(), nr = M::zero(), ni_ = M::zero();
@@ -226,7 +254,7 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typ
       A zr = M::zero(), zi = M::zero();
       for (int kk = 0; kk < K; ++kk) {
         R dr, di;
-        M::ldc(DC + kk * qq + idx, dr, di);
+        M::lds(DC + kk * qq + idx, dr, di);
         const R gv = g[kk * qq + idx];
         M::mac(zr, dr, gv);
         M::mac(zi, di, gv);
@@ -296,6 +324,8 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const t
   R* T = (R*)(acc + even_up((size_t)ncol * K * qq));               // [ncol][qq]
   Cx<M>* ub = (Cx<M>*)(T + even_up((size_t)ncol * qq));            // [ncol][4][q]
   Cx<M>* uh = ub + (size_t)ncol * 4 * q;                           // [ncol][4][q]
+  typename M::CT* wds = (typename M::CT*)(uh + (size_t)ncol * 4 * q);   // [2][K][qq] pole tables
+  cd* rb = (cd*)(wds + (size_t)2 * K * qq);                        // [2][ncol][4][q] raw edge values
   load_consts<M>(f.c, cst, Lo.size());
   // chunk 0 starts from the pole-summed particular part, sum_k' gsum[k][k'] g^_k'
   for (int e = threadIdx.x; e < ncol * K * qq; e += blockDim.x) {
@@ -319,11 +349,29 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const t
   Cx<M>* uhc = uh + (size_t)c * 4 * q;
   A* ac = acc + (size_t)c * K * qq;
   const int pbeg = chunk * ppc, pend = min(s.P, pbeg + ppc);
+  auto prefetch = [&](int pl, int bf) {
+    const typename M::CT* src = wdt + (size_t)pl * K * qq;
+    typename M::CT* dst = wds + (size_t)bf * K * qq;
+    for (int e = threadIdx.x; e < K * qq; e += blockDim.x) cp_async16(dst + e, src + e);
+    if (valid) {
+      const cd* Ep = E + ((size_t)pl * s.R + r) * s.n_edge;
+      cd* rbc = rb + ((size_t)bf * ncol + c) * 4 * q;
+      for (int side = 0; side < 4; ++side) cp_async16(rbc + side * q + a, Ep + (size_t)bseg[box * 4 + side] * q + a);
+    }
+    cp_async_commit();
+  };
+  if (pbeg < pend) prefetch(pbeg, 0);
   for (int pl = pbeg; pl < pend; ++pl) {
+    const int buf = (pl - pbeg) & 1;
+    // this pole's edge values and weights have landed; every thread is past
+    // the previous pole, so the other buffers can take the next pole's
+    cp_async_wait_all();
+    __syncthreads();
+    if (pl + 1 < pend) prefetch(pl + 1, buf ^ 1);
     // edge values of this leaf, sides S, E, N, W
-    const cd* Ep = E + ((size_t)pl * s.R + r) * s.n_edge;
+    const cd* rbc = rb + ((size_t)buf * ncol + c) * 4 * q;
     for (int side = 0; side < 4; ++side) {
-      const cd u = valid ? Ep[(size_t)bseg[box * 4 + side] * q + a] : make_double2(0.0, 0.0);
+      const cd u = valid ? rbc[side * q + a] : make_double2(0.0, 0.0);
       ubc[side * q + a] = Cx<M>{M::from(u.x), M::from(u.y)};
     }
     __syncthreads();
@@ -348,7 +396,7 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const t
     __syncthreads();
     // acc_k(a, b) -= Re(wd_k(a, b) (A_ib u_b)^(a, b))
     const Cx<M> uSa = uhc[a], uNa = uhc[2 * q + a];
-    const typename M::CT* W = wdt + (size_t)pl * K * qq;
+    const typename M::CT* W = wds + (size_t)buf * K * qq;
     for (int b = 0; b < q; ++b) {
       const int idx = b * q + a;
       const Cx<M> uE = uhc[q + b], uW = uhc[3 * q + b];
@@ -361,7 +409,7 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const t
       const R brn = M::norm(br), bin = M::norm(bi);
       for (int kk = 0; kk < K; ++kk) {
         R wr, wi;
-        M::ldc(W + kk * qq + idx, wr, wi);
+        M::lds(W + kk * qq + idx, wr, wi);
         A t = ac[kk * qq + idx];
         M::msub(t, wr, brn);
         M::mac(t, wi, bin);
@@ -472,13 +520,13 @@ eo_status raise_smem(Kern k, size_t bytes, size_t& cap) {
 size_t fd_up_smem(int q, int K) {
   const int qq = q * q, ncol = fd_ncol(q);
   return sizeof(double) * ((size_t)4 * qq + 10 * q + even_up((size_t)ncol * K * qq)) +
-         sizeof(cd) * ((size_t)ncol * qq + (size_t)2 * ncol * 4 * q);
+         sizeof(cd) * ((size_t)ncol * qq + (size_t)2 * ncol * 4 * q + (size_t)2 * K * qq);
 }
 
 size_t fd_down_smem(int q, int K) {
   const int qq = q * q, ncol = fd_ncol(q);
   return sizeof(double) * ((size_t)4 * qq + 10 * q + even_up((size_t)ncol * K * qq) + even_up((size_t)ncol * qq)) +
-         sizeof(cd) * ((size_t)2 * ncol * 4 * q);
+         sizeof(cd) * ((size_t)2 * ncol * 4 * q + (size_t)2 * K * qq + (size_t)2 * ncol * 4 * q);
 }
 
 template <class M>

@@ -19,6 +19,12 @@ typedef double2 cd;   // complex FP64, interleaved (re, im)
       return fail(EO_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// Launch shape chosen by the autotuner (0: the default heuristic).
+struct Tuned {
+  int nc = 0;   // columns per block
+  int nt = 0;   // threads per block
+};
+
 // One tree level as the kernels see it.
 struct LevelDev {
   int nbox = 0, nbx = 0, nby = 0, nbd = 0, nseg = 0, n3 = 0, dir = -1;
@@ -38,6 +44,7 @@ struct LevelDev {
   const void* aZU = nullptr;    // operators the apply reads (FP64 above, or FP32 copies)
   const void* aS = nullptr;
   int fp32 = 0;                 // this level's blocks: 0 FP64, 1 FP32, 2 FP32 pairs
+  Tuned up, down;               // autotuned launch shapes of the merge kernels
 };
 
 struct Handle {
@@ -101,6 +108,8 @@ struct Handle {
   double* fd_gsum = nullptr;    // workspace [K][K][q*q] pole-summed particular part
   double* fd_ghat = nullptr;    // workspace [rhs][K][n_int] sources in the eigenbasis
   int64_t op_bytes = 0, ws_bytes = 0;
+  Tuned root_tuned;             // autotuned launch shape of the root wall solve
+  int tuned_R = 0;              // n_rhs the launch shapes were tuned for (0: not tuned)
   // recorded step pair (CUDA graph) for repeated applies
   cudaGraphExec_t graph_exec = nullptr;
   cudaStream_t cap_st = nullptr;

@@ -186,11 +186,15 @@ def test_graph_replay_matches_plain_steps(eo, n_steps):
     states to the same steps launched one by one, on the default stream, for
     even and odd step counts and after the state buffer changes."""
     w = W.WAVE_4X4_P12
-    g, op_g, prob, u0 = wave_case(eo, w)
+    g, _, prob, u0 = wave_case(eo, w)
     x, y = g.nodes()
     c = W.wave_c(w, x, y)
+    # fixed launch shapes on both handles (autotuned shapes may differ between
+    # handles and change the rounding)
+    op_g = eo.Operator(g, eo.WAVE_DIRICHLET, band=W.BAND[w.name], n_poles=w.n_poles, c2=c * c,
+                       autotune=False)
     op_p = eo.Operator(g, eo.WAVE_DIRICHLET, band=W.BAND[w.name], n_poles=w.n_poles, c2=c * c,
-                       use_graphs=False)
+                       use_graphs=False, autotune=False)
     a = torch.tensor(u0, device="cuda")
     b = torch.tensor(u0, device="cuda")
     op_g.apply(a, n_steps)
@@ -203,3 +207,18 @@ def test_graph_replay_matches_plain_steps(eo, n_steps):
     op_g.apply(a2, n_steps)
     torch.cuda.synchronize()
     assert torch.equal(a2, b) and torch.equal(a, keep)
+
+
+def test_autotuned_launch_shapes_give_the_same_step(eo):
+    """The autotuner only changes launch shapes (columns per block, k groups):
+    the step it produces equals the heuristic shapes' step up to rounding."""
+    g, op_t, prob, u0 = sw_case(eo, 4, 10, True)
+    _, op_h, _, _ = sw_case(eo, 4, 10, True)
+    x, y = g.nodes()
+    op_h = eo.Operator(g, eo.SW_WALLS, band=60.0, n_poles=21, f=10.0, g=1.0, H=1.0, shared_ops=True,
+                       autotune=False)
+    a = torch.tensor(u0, device="cuda")
+    b = torch.tensor(u0, device="cuda")
+    op_t.apply(a, 2)
+    op_h.apply(b, 2)
+    assert rel(a.cpu().numpy(), b.cpu().numpy()) < 1e-12
