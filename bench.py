@@ -103,8 +103,9 @@ def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False):
                        dense_leaves=dense_leaves)
 
 
-def timed_steps(torch, op, u, steps, stream, dist):
-    """K steps bracketed by barrier + synchronize, CUDA events on the launching stream."""
+def timed_steps(torch, op, u, steps, stream, dist, label="timed"):
+    """K steps bracketed by barrier + synchronize, CUDA events on the launching stream.
+    The steps sit in an NVTX range (``label``) so that a profiler can select them."""
     op.set_timing(True)
     op.timing()
     if dist:
@@ -112,8 +113,10 @@ def timed_steps(torch, op, u, steps, stream, dist):
     torch.cuda.synchronize()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
+    torch.cuda.nvtx.range_push(label)
     for _ in range(steps):
         op.apply(u, 1)
+    torch.cuda.nvtx.range_pop()
     e1.record(stream)
     torch.cuda.synchronize()
     if dist:
@@ -294,7 +297,7 @@ def run_ours(args):
         u64 = torch.tensor(U0, device=dev)
         for _ in range(args.warmup):
             op64.apply(u64, 1)
-        ms64, _ = timed_steps(torch, op64, u64, args.steps, stream, dist)
+        ms64, _ = timed_steps(torch, op64, u64, args.steps, stream, dist, label="timed_fp64")
         a = torch.tensor(U0, device=dev)
         b = torch.tensor(U0, device=dev)
         op.apply(a, 1)

@@ -69,6 +69,7 @@ typedef enum {
 
 typedef struct eo_grid_s *eo_grid_t;
 typedef struct eo_handle_s *eo_handle_t;
+typedef struct eo_batch_s *eo_batch_t;
 
 /* Options of eo_build_operator.  Zero-initialise and set what you need. */
 typedef struct {
@@ -204,6 +205,22 @@ eo_status eo_apply_resolvent(eo_handle_t h, int j, const double *u_dev, double *
  * synchronises the stream before returning. */
 eo_status eo_apply_resolvent_noalloc(eo_handle_t h, int j, const double *u_dev, double *x_dev,
                                      void *stream);
+
+/* Batches of independent instances (the paper has no counterpart).  n built handles -- any
+ * grids, kinds, pole counts and precisions, each with its own DEVICE state u_dev[i]
+ * ([n_rhs[i]][fields][n_nodes], caller-owned, 1 <= n_rhs[i] <= max_rhs) -- are advanced
+ * together: eo_batch_create tunes every handle's launch shapes, then records one step pair
+ * of every instance as parallel branches of one CUDA graph (so small instances run side by
+ * side); eo_batch_apply(n_steps) replays it n_steps/2 times on `stream` (an odd last step
+ * runs per instance).  The states and handles must stay alive and unchanged in address
+ * until eo_batch_destroy; a handle may appear once; handles in a batch must not be used
+ * concurrently elsewhere (they share their workspace with the graph).  Call
+ * eo_batch_create outside any stream capture; it synchronises the device.
+ * Errors: EO_ERR_INVALID_ARG, EO_ERR_CUDA. */
+eo_status eo_batch_create(int n, const eo_handle_t *handles, double *const *u_dev, const int *n_rhs,
+                          eo_batch_t *out);
+eo_status eo_batch_apply(eo_batch_t batch, int n_steps, void *stream);
+eo_status eo_batch_destroy(eo_batch_t batch);
 
 /* Kernel tracing.  While on, every launch made by eo_apply / eo_apply_host /
  * eo_apply_resolvent is bracketed by CUDA events recorded on the launching stream.

@@ -16,7 +16,7 @@ import numpy as np
 from . import _capi
 from ._capi import SW_WALLS, WAVE_DIRICHLET, ExpopError, Opts, check
 
-__all__ = ["Grid", "Operator", "fit", "leaf_basis", "WAVE_DIRICHLET", "SW_WALLS", "ExpopError"]
+__all__ = ["Grid", "Operator", "Batch", "fit", "leaf_basis", "WAVE_DIRICHLET", "SW_WALLS", "ExpopError"]
 
 
 def fit(n_poles: int = 0, X: float = 0.0, delta: float = 1e-10, cap: int = 20001):
@@ -171,3 +171,34 @@ class Operator:
 
     def __del__(self):
         self.close()
+
+
+class Batch:
+    """Independent instances (operators with their own device states) advanced
+    together: one step pair of every instance is recorded as parallel branches of
+    one CUDA graph and replayed (eo_batch_create / eo_batch_apply)."""
+
+    def __init__(self, ops, states):
+        if len(ops) != len(states) or not ops:
+            raise ValueError("need one state per operator")
+        n = len(ops)
+        for op, u in zip(ops, states):
+            if not (u.is_cuda and u.element_size() == 8 and u.is_contiguous()):
+                raise ValueError("states must be contiguous CUDA float64 tensors")
+            if u.shape[-2:] != (op.fields, op.grid.n_nodes):
+                raise ValueError("state shape does not match its operator")
+        self._ops, self._states = list(ops), list(states)
+        hs = (C.c_void_p * n)(*[op._h.value for op in ops])
+        us = (C.c_void_p * n)(*[u.data_ptr() for u in states])
+        rs = (C.c_int * n)(*[1 if u.dim() == 2 else u.shape[0] for u in states])
+        self._b = C.c_void_p()
+        check(_capi.lib().eo_batch_create(n, hs, us, rs, C.byref(self._b)))
+
+    def apply(self, n_steps=1, stream=None):
+        check(_capi.lib().eo_batch_apply(self._b, n_steps, _stream_ptr(stream)))
+        return self._states
+
+    def __del__(self):
+        if getattr(self, "_b", None) and _capi._lib is not None:
+            _capi._lib.eo_batch_destroy(self._b)
+            self._b = None

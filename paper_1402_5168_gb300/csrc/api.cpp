@@ -24,6 +24,9 @@ struct eo_handle_s {
   Handle h;
   double* host_stage = nullptr;   // device state used by eo_apply_host
 };
+struct eo_batch_s {
+  Batch b;
+};
 
 namespace eo {
 
@@ -326,6 +329,41 @@ eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double* coeff, c
   }
   *out = hs;
   set_error("");
+  return EO_OK;
+}
+
+eo_status eo_batch_create(int n, const eo_handle_t* handles, double* const* u_dev, const int* n_rhs,
+                          eo_batch_t* out) {
+  if (!out) return fail(EO_ERR_INVALID_ARG, "null output pointer");
+  *out = nullptr;
+  if (n < 1 || !handles || !u_dev || !n_rhs) return fail(EO_ERR_INVALID_ARG, "empty batch or null array");
+  eo_batch_s* bs = new (std::nothrow) eo_batch_s;
+  if (!bs) return fail(EO_ERR_OOM, "host allocation failed");
+  for (int i = 0; i < n; ++i) {
+    if (!handles[i] || !u_dev[i]) { delete bs; return fail(EO_ERR_INVALID_ARG, "null handle or state"); }
+    for (int j = 0; j < i; ++j)
+      if (handles[j] == handles[i]) { delete bs; return fail(EO_ERR_INVALID_ARG, "a handle appears twice"); }
+    Handle& h = handles[i]->h;
+    if (n_rhs[i] < 1 || n_rhs[i] > h.R) { delete bs; return fail(EO_ERR_INVALID_ARG, "n_rhs out of range"); }
+    if (h.timing) { delete bs; return fail(EO_ERR_INVALID_ARG, "tracing is on for a batched handle"); }
+    bs->b.h.push_back(&h);
+    bs->b.u.push_back(u_dev[i]);
+    bs->b.R.push_back(n_rhs[i]);
+  }
+  eo_status rc = batch_build(bs->b);
+  if (rc) { delete bs; return rc; }
+  *out = bs;
+  set_error("");
+  return EO_OK;
+}
+
+eo_status eo_batch_apply(eo_batch_t batch, int n_steps, void* stream) {
+  if (!batch) return fail(EO_ERR_INVALID_ARG, "null batch");
+  return batch_apply(batch->b, n_steps, (cudaStream_t)stream);
+}
+
+eo_status eo_batch_destroy(eo_batch_t batch) {
+  delete batch;
   return EO_OK;
 }
 

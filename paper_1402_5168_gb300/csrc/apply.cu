@@ -147,9 +147,13 @@ __global__ void __launch_bounds__(256) k_root_sw(Sweep s, RootArgs ra, const cd*
     Bs[e] = Cv<TA>::from(v);
   }
   __syncthreads();
-  cmv<NC, TA>((const TA*)ra.Binv + (long long)p * n * n, n, n, n, Bs, n, Cs, red);
-  for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
-    const int c = e / n, i = e - c * n;
+  // rows [r_lo, r_lo + nr) of the wall solve (blocks along z split the rows)
+  const int rows_per = (n + gridDim.z - 1) / gridDim.z;
+  const int r_lo = blockIdx.z * rows_per, nr = min(rows_per, n - r_lo);
+  if (nr <= 0) return;
+  cmv<NC, TA>((const TA*)ra.Binv + (long long)p * n * n + r_lo, n, nr, n, Bs, n, Cs, red);
+  for (int e = threadIdx.x; e < NC * nr; e += blockDim.x) {
+    const int c = e / nr, i = r_lo + (e - c * nr);
     const int r = c0 + c;
     if (r >= s.R) continue;
     E[((long long)pl * s.R + r) * s.n_edge + (long long)ra.bseg[i / ra.q] * ra.q + (i % ra.q)] = Cs[e];
@@ -601,11 +605,14 @@ struct DownMerge {
 
 template <int NC, typename TA>
 struct RootSW {
-  static eo_status run(const Sweep& s, const RootArgs& ra, const cd* hroot, cd* E, int nt, cudaStream_t st) {
-    dim3 grid((s.R + NC - 1) / NC, s.P);
+  static eo_status run(const Sweep& s, const RootArgs& ra, const cd* hroot, cd* E, int nt, int rsplit,
+                       cudaStream_t st) {
+    rsplit = std::max(1, rsplit);
+    dim3 grid((s.R + NC - 1) / NC, s.P, rsplit);
+    const int rows_per = (ra.n + rsplit - 1) / rsplit;
     const size_t smem = sizeof(cd) * ((size_t)NC * 2 * ra.n + 256 * NC) + 64;
     EO_SET_SMEM((k_root_sw<NC, TA>), smem);
-    k_root_sw<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(ra.n), smem, st>>>(s, ra, hroot, E);
+    k_root_sw<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(rows_per), smem, st>>>(s, ra, hroot, E);
     EO_CUDA_TRY(cudaGetLastError());
     return EO_OK;
   }
@@ -709,7 +716,7 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
     RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, uin, 3};
     if ((rc = h.trace_begin(st))) return rc;
     const int nc = h.root_tuned.nc ? h.root_tuned.nc : pick_nc(0, R, rl.nbd, rl.nbd);
-    if ((rc = dispatch<RootSW>(h.root_fp32, nc, s, ra, hcur, h.E, h.root_tuned.nt, st))) return rc;
+    if ((rc = dispatch<RootSW>(h.root_fp32, nc, s, ra, hcur, h.E, h.root_tuned.nt, h.root_tuned.rs, st))) return rc;
     if ((rc = h.trace_end(TR_ROOT, st))) return rc;
   }
   // down: merges
@@ -849,12 +856,13 @@ eo_status autotune(Handle& h, int R, cudaStream_t st) {
     RootArgs ra{rl.nbd, h.g.q, rl.sx * h.g.q, rl.sy * h.g.q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, h.ustate, 3};
     float best = 1e30f;
     for (int nc = 1; nc <= 8 && nc <= R; nc *= 2)
-      for (int nt : nt_list(rl.nbd)) {
-        if ((size_t)nc * (2 * rl.nbd + 256) * sizeof(cd) > 200 * 1024) continue;
-        const float t = timeit([&] { return dispatch<RootSW>(h.root_fp32, nc, s, ra, h.hA, h.E, nt, st); });
-        if (t < 0) return fail(EO_ERR_CUDA, "autotune: root launch failed");
-        if (t < best) { best = t; h.root_tuned = Tuned{nc, nt}; }
-      }
+      for (int rs = 1; rs <= 4; rs *= 2)
+        for (int nt : nt_list((rl.nbd + rs - 1) / rs)) {
+          if ((size_t)nc * (2 * rl.nbd + 256) * sizeof(cd) > 200 * 1024) continue;
+          const float t = timeit([&] { return dispatch<RootSW>(h.root_fp32, nc, s, ra, h.hA, h.E, nt, rs, st); });
+          if (t < 0) return fail(EO_ERR_CUDA, "autotune: root launch failed");
+          if (t < best) { best = t; h.root_tuned = Tuned{nc, nt, rs}; }
+        }
   }
   h.tuned_R = R;
   return EO_OK;
@@ -903,6 +911,67 @@ eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st) {
   if (cur != u)
     EO_CUDA_TRY(cudaMemcpyAsync(u, cur, sizeof(double) * (size_t)n_rhs * h.F * h.g.n_nodes,
                                 cudaMemcpyDeviceToDevice, st));
+  return EO_OK;
+}
+
+// ---------------------------------------------------------------- batches of instances
+Batch::~Batch() {
+  if (exec) cudaGraphExecDestroy(exec);
+  for (cudaStream_t s : st) cudaStreamDestroy(s);
+  if (st0) cudaStreamDestroy(st0);
+  for (cudaEvent_t e : ev) cudaEventDestroy(e);
+}
+
+// Record one step pair of every instance (u -> workspace -> u) as parallel
+// branches of one CUDA graph: a fork event on a private stream, one branch
+// stream per instance, join events back.  Launch shapes are tuned first,
+// outside the capture.
+eo_status batch_build(Batch& b) {
+  const int n = (int)b.h.size();
+  for (int i = 0; i < n; ++i) {
+    eo_status rc = autotune(*b.h[i], b.R[i], nullptr);
+    if (rc) return rc;
+  }
+  EO_CUDA_TRY(cudaStreamCreateWithFlags(&b.st0, cudaStreamNonBlocking));
+  b.st.assign(n, nullptr);
+  for (int i = 0; i < n; ++i) EO_CUDA_TRY(cudaStreamCreateWithFlags(&b.st[i], cudaStreamNonBlocking));
+  b.ev.assign(n + 1, nullptr);
+  for (int i = 0; i <= n; ++i) EO_CUDA_TRY(cudaEventCreateWithFlags(&b.ev[i], cudaEventDisableTiming));
+  EO_CUDA_TRY(cudaDeviceSynchronize());
+  EO_CUDA_TRY(cudaStreamBeginCapture(b.st0, cudaStreamCaptureModeThreadLocal));
+  eo_status rc = EO_OK;
+  cudaError_t e = cudaEventRecord(b.ev[n], b.st0);
+  for (int i = 0; i < n && !rc && e == cudaSuccess; ++i) {
+    Handle& h = *b.h[i];
+    e = cudaStreamWaitEvent(b.st[i], b.ev[n], 0);
+    if (e != cudaSuccess) break;
+    rc = run_step(h, b.u[i], h.ustate, b.R[i], 0, h.P, h.wgt, h.C, b.st[i]);
+    if (!rc) rc = run_step(h, h.ustate, b.u[i], b.R[i], 0, h.P, h.wgt, h.C, b.st[i]);
+    if (!rc) e = cudaEventRecord(b.ev[i], b.st[i]);
+    if (!rc && e == cudaSuccess) e = cudaStreamWaitEvent(b.st0, b.ev[i], 0);
+  }
+  cudaGraph_t graph = nullptr;
+  const cudaError_t ec = cudaStreamEndCapture(b.st0, &graph);
+  if (rc) { if (graph) cudaGraphDestroy(graph); return rc; }
+  if (e != cudaSuccess || ec != cudaSuccess) {
+    if (graph) cudaGraphDestroy(graph);
+    return fail(EO_ERR_CUDA, std::string("batch capture: ") + cudaGetErrorString(e != cudaSuccess ? e : ec));
+  }
+  e = cudaGraphInstantiate(&b.exec, graph, 0);
+  cudaGraphDestroy(graph);
+  if (e != cudaSuccess) return fail(EO_ERR_CUDA, std::string("batch graph instantiate: ") + cudaGetErrorString(e));
+  return EO_OK;
+}
+
+eo_status batch_apply(Batch& b, int n_steps, cudaStream_t st) {
+  if (n_steps < 0) return fail(EO_ERR_INVALID_ARG, "negative n_steps");
+  for (int i = 0; i + 1 < n_steps; i += 2) EO_CUDA_TRY(cudaGraphLaunch(b.exec, st));
+  if (n_steps % 2) {
+    for (size_t i = 0; i < b.h.size(); ++i) {
+      eo_status rc = apply(*b.h[i], b.u[i], b.R[i], 1, st);
+      if (rc) return rc;
+    }
+  }
   return EO_OK;
 }
 

@@ -456,19 +456,19 @@ __global__ void k_fd_wd(int np, int p0, int K, int qq, const cd* __restrict__ wg
 }
 
 // gsum[k][k'](a, b) = sum_p Re(wgt[p][k] coef[p][k'] dinv_p(a, b)).  A block takes
-// 32 consecutive outputs; its 8 warps stride over the poles and the warp partials
-// are added in a fixed order (deterministic).
-__global__ void __launch_bounds__(256) k_fd_gsum(int np, int p0, int K, int qq, const cd* __restrict__ wgt,
-                                                 const cd* __restrict__ coef, const cd* __restrict__ dinv,
-                                                 double* __restrict__ gsum) {
-  __shared__ double red[8][32];
+// 32 consecutive outputs; its 32 warps stride over the poles and the warp
+// partials are added in a fixed order (deterministic).
+__global__ void __launch_bounds__(1024) k_fd_gsum(int np, int p0, int K, int qq, const cd* __restrict__ wgt,
+                                                  const cd* __restrict__ coef, const cd* __restrict__ dinv,
+                                                  double* __restrict__ gsum) {
+  __shared__ double red[32][32];
   const int lane = threadIdx.x & 31, wp = threadIdx.x >> 5;
   const int t = blockIdx.x * 32 + lane;
   const bool ok = t < K * K * qq;
   const int kk = ok ? t / (K * qq) : 0, k2 = ok ? (t / qq) % K : 0, idx = ok ? t % qq : 0;
   double sum = 0.0;
   if (ok)
-    for (int pl = wp; pl < np; pl += 8) {
+    for (int pl = wp; pl < np; pl += 32) {
       const int p = p0 + pl;
       const cd w = wgt[p * K + kk], cf = coef[p * K + k2], d = dinv[(size_t)p * qq + idx];
       const double wr = w.x * cf.x - w.y * cf.y, wi = w.x * cf.y + w.y * cf.x;
@@ -478,7 +478,7 @@ __global__ void __launch_bounds__(256) k_fd_gsum(int np, int p0, int K, int qq, 
   __syncthreads();
   if (wp == 0 && ok) {
     double v = 0.0;
-    for (int w = 0; w < 8; ++w) v += red[w][lane];
+    for (int w = 0; w < 32; ++w) v += red[w][lane];
     gsum[t] = v;
   }
 }
@@ -555,7 +555,7 @@ eo_status down_leaf_t(Handle& h, const Sweep& s, const FdArgs& f, int& nchunk, c
                                                                                  h.fd_dinv, wd);
   EO_CUDA_TRY(cudaGetLastError());
   const int ng = s.K * s.K * qq;
-  k_fd_gsum<<<(ng + 31) / 32, 256, 0, st>>>(s.P, s.p0, s.K, qq, s.wgt, s.coef, h.fd_dinv, h.fd_gsum);
+  k_fd_gsum<<<(ng + 31) / 32, 1024, 0, st>>>(s.P, s.p0, s.K, qq, s.wgt, s.coef, h.fd_dinv, h.fd_gsum);
   EO_CUDA_TRY(cudaGetLastError());
   const int ncols = f.nleaf * s.R;
   const int ngroups = (ncols + f.ncol - 1) / f.ncol;

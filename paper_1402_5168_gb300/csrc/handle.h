@@ -23,6 +23,7 @@ typedef double2 cd;   // complex FP64, interleaved (re, im)
 struct Tuned {
   int nc = 0;   // columns per block
   int nt = 0;   // threads per block
+  int rs = 1;   // row blocks per block product (root wall solve)
 };
 
 // One tree level as the kernels see it.
@@ -146,6 +147,20 @@ eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st);
 eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStream_t st);
 eo_status apply_adjoint(Handle& h, double* y, int n_rhs, int n_steps, cudaStream_t st);
 eo_status apply_resolvent_noalloc(Handle& h, int j, const double* u, double* x, cudaStream_t st);
+// independent instances advanced together through one CUDA graph (apply.cu)
+struct Batch {
+  std::vector<Handle*> h;
+  std::vector<double*> u;
+  std::vector<int> R;
+  std::vector<cudaStream_t> st;   // one branch stream per instance
+  cudaStream_t st0 = nullptr;     // capture (fork/join) stream
+  std::vector<cudaEvent_t> ev;    // per-instance join events, then the fork event
+  cudaGraphExec_t exec = nullptr;
+  ~Batch();
+};
+eo_status batch_build(Batch& b);
+eo_status batch_apply(Batch& b, int n_steps, cudaStream_t st);
+
 // fast-diagonalisation leaves (fd.cu)
 eo_status fd_setup(Handle& h, const double* dAii0, const double* dAib, const double* dFbi, cudaStream_t st);
 struct Sweep;

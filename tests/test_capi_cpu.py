@@ -86,3 +86,12 @@ def test_wide_band_fit_meets_contract(capi):
     band, mod, tail = rational.check_contract(alpha, b, X, 1e-10)
     assert band <= 1e-10 and mod <= 1.0 + 1e-12 and tail < 1.0
     assert np.array_equal(alpha[::-1], np.conj(alpha)) and np.array_equal(b[::-1], np.conj(b))
+
+
+def test_batch_create_rejects_empty_and_null(capi):
+    L = capi.lib()
+    out = C.c_void_p()
+    assert L.eo_batch_create(0, None, None, None, C.byref(out)) == 1
+    assert L.eo_batch_create(1, None, None, None, C.byref(out)) == 1
+    assert L.eo_batch_apply(None, 1, None) == 1
+    assert L.eo_batch_destroy(None) == 0
