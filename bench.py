@@ -195,6 +195,18 @@ def class_work(op, w, R, prec, fd):
     return work
 
 
+# DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one step's launches of a
+# kernel class, from the ncu --set full capture of the shallow-water workload with 301 poles
+# (151 distinct), FP32-pair precision, summarised in
+# profiles/step_kernels_sw_16x16_p16_N301_df32.md.  Traffic grows with the number of distinct
+# poles (one block set per pole, read once), so a full step scales it by P / 151.
+NCU_TRAFFIC_151 = {
+    ("sw_walls_16x16_p16_tau20T", "df32", "up_merge"): 1.2009e9 + 12.85e6,
+    ("sw_walls_16x16_p16_tau20T", "df32", "down_merge"): 0.9587e9 + 10.57e6,
+    ("sw_walls_16x16_p16_tau20T", "df32", "root"): 1.9419e9 + 3.43e6,
+}
+
+
 def alu_peak(prec):
     # FP32-pair products cost 48 FP32 instructions per complex multiply-add (4
     # split products of 12): pipe bound in FP64-equivalent flops FP32_peak / 2 / 48 * 8
@@ -236,7 +248,11 @@ def roofline(op, w, R, tim, prec, pk, pk_kind, fd):
     else:
         rf = {"bound": "hbm", "achieved": d["gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": d["hbm_frac"],
               "peak_source": pk_kind}
-    rf.update({"kernel": kname, "class": top, "traffic": None,
+    P = (op.alpha.size + 1) // 2
+    tr = NCU_TRAFFIC_151.get((w.name, prec, top)) if R == 1 and not (top.endswith("leaf")) else None
+    rf.update({"kernel": kname, "class": top, "traffic": None if tr is None else tr * P / 151,
+               "traffic_note": None if tr is None else
+               "ncu DRAM bytes of this class's launches in one step of the 301-pole case, scaled by P/151",
                "algorithmic_flops": work[top][0], "algorithmic_bytes": work[top][1],
                "avg_launch_ms": d["ms_per_step"] / d["launches_per_step"],
                "launches": tim[top][0], "per_class": per})

@@ -249,6 +249,7 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
     if ((rc = h.alloc((void**)&h.fd_wd, sizeof(cd) * P * h.K * ni, false))) return rc;
     if ((rc = h.alloc((void**)&h.fd_gsum, sizeof(double) * h.K * h.K * ni, false))) return rc;
     if ((rc = h.alloc((void**)&h.fd_ghat, sizeof(double) * R * h.K * g.n_int, false))) return rc;
+    EO_CUDA_TRY(cudaMemsetAsync(h.fd_ghat, 0, sizeof(double) * R * h.K * g.n_int, st));
   }
   if (h.kind == EO_SW_WALLS) {
     if ((rc = h.alloc((void**)&h.afull, sizeof(double) * R * h.K * g.n_nodes, false))) return rc;

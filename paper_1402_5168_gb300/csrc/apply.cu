@@ -732,7 +732,7 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   int nchunk = 1;
   if ((rc = h.trace_begin(st))) return rc;
   if (h.fd) {
-    if ((rc = fd_down_leaf(h, s, nleaf, nchunk, st))) return rc;
+    if ((rc = fd_down_leaf(h, s, nleaf, h.fd_ncol_down, nchunk, st))) return rc;
   } else {
     const int nc = pick_nc(h.shared, R, ni + nb, ni, nleaf);
     const int ncg = (nleaf * R + nc - 1) / nc;
@@ -850,6 +850,19 @@ eo_status autotune(Handle& h, int R, cudaStream_t st) {
         if (t < 0) return fail(EO_ERR_CUDA, "autotune: merge launch failed");
         if (t < best) { best = t; ld.down = Tuned{nc, nt}; }
       }
+  }
+  if (h.fd) {
+    const int nleaf = h.g.nlx * h.g.nly;
+    float bu = 1e30f, bd = 1e30f;
+    for (int nc : fd_ncol_candidates(h)) {
+      float t = timeit([&] { return fd_up_kernel(h, s, nleaf, h.hA, nc, st); });
+      if (t < 0) return fail(EO_ERR_CUDA, "autotune: leaf launch failed");
+      if (t < bu) { bu = t; h.fd_ncol_up = nc; }
+      int nchunk = 0;
+      t = timeit([&] { return fd_down_leaf(h, s, nleaf, nc, nchunk, st); });
+      if (t < 0) return fail(EO_ERR_CUDA, "autotune: leaf launch failed");
+      if (t < bd) { bd = t; h.fd_ncol_down = nc; }
+    }
   }
   if (h.kind == EO_SW_WALLS) {
     const Level& rl = h.plan.lv[L];

@@ -498,11 +498,11 @@ __global__ void k_fd_dc(int P, int K, int qq, const cd* __restrict__ coef, const
 
 namespace {
 
-int fd_ncol(int q) { return std::max(1, 128 / q); }
+int fd_ncol(int q, int tuned) { return tuned > 0 ? tuned : std::max(1, 128 / q); }
 
-FdArgs fd_args(const Handle& h, int nleaf) {
+FdArgs fd_args(const Handle& h, int nleaf, int ncol) {
   FdArgs f;
-  f.q = h.g.q; f.K = h.K; f.ncol = fd_ncol(h.g.q); f.nleaf = nleaf;
+  f.q = h.g.q; f.K = h.K; f.ncol = fd_ncol(h.g.q, ncol); f.nleaf = nleaf;
   f.c = h.fd_c; f.gsum = h.fd_gsum; f.ghat = h.fd_ghat;
   return f;
 }
@@ -517,14 +517,14 @@ eo_status raise_smem(Kern k, size_t bytes, size_t& cap) {
   return EO_OK;
 }
 
-size_t fd_up_smem(int q, int K) {
-  const int qq = q * q, ncol = fd_ncol(q);
+size_t fd_up_smem(int q, int K, int ncol) {
+  const int qq = q * q;
   return sizeof(double) * ((size_t)4 * qq + 10 * q + even_up((size_t)ncol * K * qq)) +
          sizeof(cd) * ((size_t)ncol * qq + (size_t)2 * ncol * 4 * q + (size_t)2 * K * qq);
 }
 
-size_t fd_down_smem(int q, int K) {
-  const int qq = q * q, ncol = fd_ncol(q);
+size_t fd_down_smem(int q, int K, int ncol) {
+  const int qq = q * q;
   return sizeof(double) * ((size_t)4 * qq + 10 * q + even_up((size_t)ncol * K * qq) + even_up((size_t)ncol * qq)) +
          sizeof(cd) * ((size_t)2 * ncol * 4 * q + (size_t)2 * K * qq + (size_t)2 * ncol * 4 * q);
 }
@@ -537,7 +537,7 @@ eo_status up_leaf_t(Handle& h, const Sweep& s, const FdArgs& f, cd* h0, cudaStre
   int nchunk = std::max(1, std::min(s.P, (608 + ngroups - 1) / ngroups));
   const int ppc = (s.P + nchunk - 1) / nchunk;
   nchunk = (s.P + ppc - 1) / ppc;
-  const size_t smem = fd_up_smem(q, s.K);
+  const size_t smem = fd_up_smem(q, s.K, f.ncol);
   static size_t cap = 48 * 1024;
   eo_status rc = raise_smem(k_fd_up_leaf<M>, smem, cap);
   if (rc) return rc;
@@ -563,7 +563,7 @@ eo_status down_leaf_t(Handle& h, const Sweep& s, const FdArgs& f, int& nchunk, c
   nchunk = std::min(nchunk, h.nchunk);
   const int ppc = (s.P + nchunk - 1) / nchunk;
   nchunk = (s.P + ppc - 1) / ppc;
-  const size_t smem = fd_down_smem(q, s.K);
+  const size_t smem = fd_down_smem(q, s.K, f.ncol);
   static size_t cap = 48 * 1024;
   eo_status rc = raise_smem(k_fd_down_leaf<M>, smem, cap);
   if (rc) return rc;
@@ -574,17 +574,35 @@ eo_status down_leaf_t(Handle& h, const Sweep& s, const FdArgs& f, int& nchunk, c
 
 }  // namespace
 
-eo_status fd_up_leaf(Handle& h, const Sweep& s, int nleaf, cd* h0, cudaStream_t st) {
-  const int qq = h.g.q * h.g.q;
-  FdArgs f = fd_args(h, nleaf);
-  k_fd_src<<<dim3(nleaf, s.R), 256, sizeof(double) * 4 * qq, st>>>(s, f, h.fd_ghat);
-  EO_CUDA_TRY(cudaGetLastError());
+eo_status fd_up_kernel(Handle& h, const Sweep& s, int nleaf, cd* h0, int ncol, cudaStream_t st) {
+  FdArgs f = fd_args(h, nleaf, ncol);
   return h.fd_pair ? up_leaf_t<Pair>(h, s, f, h0, st) : up_leaf_t<F64>(h, s, f, h0, st);
 }
 
-eo_status fd_down_leaf(Handle& h, const Sweep& s, int nleaf, int& nchunk, cudaStream_t st) {
-  FdArgs f = fd_args(h, nleaf);
+eo_status fd_up_leaf(Handle& h, const Sweep& s, int nleaf, cd* h0, cudaStream_t st) {
+  const int qq = h.g.q * h.g.q;
+  FdArgs f = fd_args(h, nleaf, h.fd_ncol_up);
+  k_fd_src<<<dim3(nleaf, s.R), 256, sizeof(double) * 4 * qq, st>>>(s, f, h.fd_ghat);
+  EO_CUDA_TRY(cudaGetLastError());
+  return fd_up_kernel(h, s, nleaf, h0, h.fd_ncol_up, st);
+}
+
+eo_status fd_down_leaf(Handle& h, const Sweep& s, int nleaf, int ncol, int& nchunk, cudaStream_t st) {
+  FdArgs f = fd_args(h, nleaf, ncol);
   return h.fd_pair ? down_leaf_t<Pair>(h, s, f, nchunk, st) : down_leaf_t<F64>(h, s, f, nchunk, st);
+}
+
+// columns per block the leaf kernels can take at this q (block <= 256 threads,
+// shared memory <= 200 KB)
+std::vector<int> fd_ncol_candidates(const Handle& h) {
+  std::vector<int> v;
+  const int q = h.g.q;
+  for (int nc : {2, 3, 4, 6, 9, 12, 16}) {
+    if (nc * q > 256) continue;
+    if (fd_up_smem(q, h.K, nc) > 200 * 1024 || fd_down_smem(q, h.K, nc) > 200 * 1024) continue;
+    v.push_back(nc);
+  }
+  return v;
 }
 
 // Build-time setup from the leaf-0 real matrices the dense build assembled

@@ -102,6 +102,7 @@ struct Handle {
   // fast-diagonalisation leaves (shared constant-coefficient operators)
   int fd = 0;
   int fd_pair = 0;              // leaf arithmetic: 0 FP64, 1 FP32 pairs (tables dc, wd then hold float4)
+  int fd_ncol_up = 0, fd_ncol_down = 0;   // autotuned columns per block (0: default)
   double* fd_c = nullptr;       // leaf eigenbases and 1-D vectors (layout in fd.cu)
   cd* fd_dinv = nullptr;        // [P][q*q] 1 / (lx_a + ly_b - kappa_p^2), index b*q + a
   cd* fd_dc = nullptr;          // [P][K][q*q] coef[p][k] * dinv_p (FP64 or FP32-pair complex)
@@ -165,6 +166,8 @@ eo_status batch_apply(Batch& b, int n_steps, cudaStream_t st);
 eo_status fd_setup(Handle& h, const double* dAii0, const double* dAib, const double* dFbi, cudaStream_t st);
 struct Sweep;
 eo_status fd_up_leaf(Handle& h, const Sweep& s, int nleaf, cd* h0, cudaStream_t st);
-eo_status fd_down_leaf(Handle& h, const Sweep& s, int nleaf, int& nchunk, cudaStream_t st);
+eo_status fd_up_kernel(Handle& h, const Sweep& s, int nleaf, cd* h0, int ncol, cudaStream_t st);
+eo_status fd_down_leaf(Handle& h, const Sweep& s, int nleaf, int ncol, int& nchunk, cudaStream_t st);
+std::vector<int> fd_ncol_candidates(const Handle& h);
 
 }  // namespace eo

@@ -52,3 +52,39 @@ def test_reference_arm_runs_on_the_small_workload():
     assert r.returncode == 0, r.stderr
     line = json.loads(r.stdout.strip().splitlines()[-1])
     assert line["impl"] == "reference" and line["value"] > 0 and line["cpu_baseline"]["kind"] == "oracle"
+
+
+def test_plan_levels_match_the_library_plan():
+    """bench.py's level sizes (for the algorithmic flops and bytes of the
+    rooflines) against the library's own tree plan, seen through the operator
+    memory it reports: per pole, ZU and S blocks of every merge level."""
+    sys.path.insert(0, ROOT)
+    import bench
+    lv = bench.plan_levels(16, 16, 14)
+    assert [l["nbox"] for l in lv] == [128, 64, 32, 16, 8, 4, 2, 1]
+    assert [l["n3"] for l in lv] == [14, 28, 28, 56, 56, 112, 112, 224]
+    assert [l["nbd"] for l in lv] == [84, 112, 168, 224, 336, 448, 672, 896]
+    # rectangular grid: merges along x until one column remains, then along y
+    lv = bench.plan_levels(4, 1, 6)
+    assert [l["nbox"] for l in lv] == [2, 1]
+    assert [l["n3"] for l in lv] == [6, 6]
+    assert lv[-1]["nbd"] == 2 * (4 + 1) * 6
+
+
+def test_class_work_counts_for_the_shallow_water_workload():
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+
+    class Op:
+        alpha = __import__("numpy").zeros(5757)
+    w = W.SW_16X16_P16
+    work = bench.class_work(Op(), w, 1, "df32", fd=True)
+    P, q = 2879, 14
+    # fast-diagonal leaves: (4K + 32) q^2 flops per (pole, leaf, rhs), K = 3
+    assert work["up_leaf"][0] == (4 * 3 + 32) * q * q * P * 256
+    # root wall solve: one complex multiply-add per entry of the 896 x 896 block
+    assert work["root"][0] == 8.0 * P * 896 * 896
+    assert work["root"][1] == P * 896 * 896 * 16 + P * 2 * 896 * 16
+    # top up merge: ZU has n3 + nbd rows and n3 columns
+    assert work["up_merge"][0] > 8.0 * P * (224 + 896) * 224

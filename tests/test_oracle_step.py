@@ -193,3 +193,35 @@ def test_wave_adjoint_equals_transpose_of_dense_step(poles21):
     lhs = np.sum(y * st2.step(u))
     rhs = np.sum(adjoint_step(st2, y) * u)
     assert abs(lhs - rhs) <= 1e-9 * abs(lhs)
+
+
+def _resolvent_matrix(prob, alpha):
+    """Dense matrix of the oracle's shallow-water resolvent on [U, V, h] (small grids)."""
+    import scipy.sparse.linalg as spla
+    n = prob.grid.n_nodes
+    lu = spla.splu(prob.system(alpha))
+    M = np.zeros((3 * n, 3 * n), dtype=complex)
+    for j in range(3 * n):
+        e = np.zeros(3 * n)
+        e[j] = 1.0
+        st = e.reshape(3, n)
+        M[:, j] = prob.post(alpha, lu.solve(prob.rhs(alpha, st)), st).ravel()
+    return M
+
+
+@pytest.mark.parametrize("f,consistent", [(0.0, True), (10.0, False)])
+def test_sw_resolvent_identity_holds_only_without_rotation(f, consistent):
+    """A documented property of the paper's elimination on this discretisation.
+    Without rotation the per-pole solves are resolvents of one discrete operator:
+    R(a) - R(b) = (a - b) R(a) R(b).  With rotation the elimination drops
+    Curl(G h), which the recovered edge gradient does not make zero, so the
+    identity fails at O(1)."""
+    g = sem.Grid(1, 1, 6)
+    prob = Problem(g, "sw", 1.0, f=f, g=1.0, H=1.0)
+    a, b = 0.7 + 3.0j, 1.3 - 5.0j
+    Ra, Rb = _resolvent_matrix(prob, a), _resolvent_matrix(prob, b)
+    defect = np.linalg.norm(Ra - Rb - (a - b) * Ra @ Rb) / np.linalg.norm(Ra - Rb)
+    if consistent:
+        assert defect < 1e-12
+    else:
+        assert defect > 1e-2
