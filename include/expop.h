@@ -206,6 +206,29 @@ eo_status eo_apply_resolvent(eo_handle_t h, int j, const double *u_dev, double *
 eo_status eo_apply_resolvent_noalloc(eo_handle_t h, int j, const double *u_dev, double *x_dev,
                                      void *stream);
 
+/* Other functions of tau L on the SAME poles (dense output and phi-functions; the
+ * solves are shared, only the pole-sum weights change).  Host-only fit of residues b
+ * (2M+1 complex, interleaved, the eo_get_poles order, b_{-m} = conj(b_m)) such that
+ * sum_m b_m / (z - alpha_m) approximates, on the handle's band z = i x, |x| <= X:
+ *   kind EO_FN_EXP (0):  exp(c z), 0 < c <= 1   (exp(c tau L): output inside the step)
+ *   kind EO_FN_PHI1 (1): phi1(z) = (exp(z) - 1) / z.
+ * Narrow fits solve for every residue by least squares on the band; wide fits take
+ * the central residues from the trapezoidal rule of the function's Cauchy integral
+ * along the pole line and fit the outer pairs.  err (may be NULL) receives
+ * max |f(ix) - R(ix)| on the band.  Errors: EO_ERR_INVALID_ARG, EO_ERR_FIT. */
+#define EO_FN_EXP 0
+#define EO_FN_PHI1 1
+eo_status eo_fit_function(eo_handle_t h, int kind, double c, double *b, double *err);
+
+/* out_dev[k] = f_k(tau L) u for n_out residue sets b_sets[k] (each 2M+1 complex
+ * interleaved, as from eo_fit_function or eo_get_poles) on the handle's poles: one
+ * upward sweep and merge pass for all, then the leaf interiors, pole sums and
+ * post-map once per set.  u_dev: DEVICE [fields][n_nodes] (one state);
+ * out_dev: DEVICE [n_out][fields][n_nodes], not overlapping u_dev.  Synchronises the
+ * stream before returning.  Errors: EO_ERR_INVALID_ARG, EO_ERR_CUDA. */
+eo_status eo_apply_functions(eo_handle_t h, int n_out, const double *b_sets, const double *u_dev,
+                             double *out_dev, void *stream);
+
 /* Batches of independent instances (the paper has no counterpart).  n built handles -- any
  * grids, kinds, pole counts and precisions, each with its own DEVICE state u_dev[i]
  * ([n_rhs[i]][fields][n_nodes], caller-owned, 1 <= n_rhs[i] <= max_rhs) -- are advanced

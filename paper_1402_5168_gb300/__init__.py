@@ -152,6 +152,28 @@ class Operator:
                                              _stream_ptr(stream)))
         return x
 
+    def fit_function(self, kind: str = "exp", c: float = 1.0):
+        """Residues (numpy complex, eo_get_poles order) of exp(c z) ("exp") or
+        phi1(z) ("phi1") on this operator's poles, and the band error."""
+        n = self.alpha.size
+        b = np.zeros(2 * n)
+        err = C.c_double()
+        check(_capi.lib().eo_fit_function(self._h, {"exp": 0, "phi1": 1}[kind], c,
+                                          b.ctypes.data_as(C.POINTER(C.c_double)), C.byref(err)))
+        return b[0::2] + 1j * b[1::2], err.value
+
+    def apply_functions(self, b_sets, u, out, stream=None):
+        """out[k] <- f_k(tau L) u for residue sets b_sets[k] on these poles (one
+        shared sweep); u: CUDA float64 [fields, n_nodes]; out: [n_out, fields, n_nodes]."""
+        bs = np.ascontiguousarray(np.stack([np.stack([np.real(b), np.imag(b)], axis=1).ravel()
+                                            for b in b_sets]))
+        if out.shape[0] != len(b_sets) or not out.is_contiguous() or not u.is_contiguous():
+            raise ValueError("out must be contiguous [n_out, fields, n_nodes]")
+        check(_capi.lib().eo_apply_functions(self._h, len(b_sets), bs.ctypes.data_as(C.POINTER(C.c_double)),
+                                             C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()),
+                                             _stream_ptr(stream)))
+        return out
+
     def set_timing(self, on: bool):
         check(_capi.lib().eo_set_timing(self._h, int(on)))
 

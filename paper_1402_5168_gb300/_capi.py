@@ -15,7 +15,8 @@ WAVE_DIRICHLET, SW_WALLS = 0, 1
 # every symbol include/expop.h declares
 SYMBOLS = ("eo_fit", "eo_grid_create", "eo_grid_info", "eo_grid_nodes", "eo_grid_destroy", "eo_build_operator",
            "eo_get_poles", "eo_memory", "eo_apply", "eo_apply_adjoint", "eo_apply_host", "eo_apply_resolvent", "eo_apply_resolvent_noalloc", "eo_set_timing", "eo_get_timing", "eo_destroy",
-           "eo_last_error", "eo_leaf_basis", "eo_batch_create", "eo_batch_apply", "eo_batch_destroy")
+           "eo_last_error", "eo_leaf_basis", "eo_batch_create", "eo_batch_apply", "eo_batch_destroy",
+           "eo_fit_function", "eo_apply_functions")
 
 
 class Opts(C.Structure):
@@ -60,6 +61,8 @@ def lib() -> C.CDLL:
         "eo_batch_create": [C.c_int, C.POINTER(vp), C.POINTER(vp), C.POINTER(C.c_int), C.POINTER(vp)],
         "eo_batch_apply": [vp, C.c_int, vp],
         "eo_batch_destroy": [vp],
+        "eo_fit_function": [vp, C.c_int, C.c_double, dp, dp],
+        "eo_apply_functions": [vp, C.c_int, dp, vp, vp, vp],
     }
     for name, args in sig.items():
         f = getattr(L, name)

@@ -545,13 +545,10 @@ int pick_nc_t(int shared, int R, int k, int rows, int nbox = 1 << 30) {
 
 #define EO_SET_SMEM_T(kern, bytes)                                                            \
   do {                                                                                        \
-    /* raise the dynamic shared-memory cap once per kernel (outside any capture) */          \
-    static size_t cap_ = 48 * 1024;                                                           \
-    if ((bytes) > cap_) {                                                                     \
-      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 8192)); \
-      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));     \
-      cap_ = 200 * 1024 + 8192;                                                               \
-    }                                                                                         \
+    /* raise the dynamic shared-memory cap once per kernel and device */                     \
+    static size_t cap_[64] = {};                                                              \
+    eo_status rs_ = ensure_smem((const void*)(kern), (bytes), cap_, 200 * 1024 + 8192);       \
+    if (rs_) return rs_;                                                                      \
   } while (0)
 
 template <int NC, typename TA>

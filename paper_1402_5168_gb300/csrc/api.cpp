@@ -72,6 +72,38 @@ eo_status upload(Handle& h, T** dst, const std::vector<T>& v, cudaStream_t st) {
   return EO_OK;
 }
 
+}  // namespace
+
+// Pole-sum weights [P][K] (device layout) and post-map constants for the pole
+// weights cw (c_0 = b_0, c_j = 2 b_j of the conjugate-pole form, Section 3.3):
+//   wave: V = Re sum c V_p, U = Re sum (c tau / alpha) V_p - C0 f_u, C0 = Re sum c / alpha;
+//   shallow water: h = Re sum c h_p and the two velocity weights c (-alpha / D),
+//   c (-tau f / D), D = alpha^2 + (tau f)^2, whose real sums C0, C1 scale the
+//   input velocities in the post-map.
+void eo::pole_weights(const Handle& h, const std::vector<cx>& cw, std::vector<cd>& wgt, double C[4]) {
+  wgt.clear();
+  C[0] = C[1] = C[2] = C[3] = 0.0;
+  const double tau = h.tau;
+  for (int j = 0; j < h.P; ++j) {
+    const cx a = h.alpha[j], c = cw[j];
+    if (h.kind == EO_WAVE_DIRICHLET) {
+      const cx w0 = c, w1 = c * tau / a;
+      wgt.push_back(make_double2(w0.real(), w0.imag()));
+      wgt.push_back(make_double2(w1.real(), w1.imag()));
+      C[0] += (c / a).real();
+    } else {
+      const double tf = tau * h.opts.sw_f;
+      const cx D = a * a + tf * tf;
+      const cx w0 = c, w1 = c * (-a / D), w2 = c * (-tf / D);
+      for (cx v : {w0, w1, w2}) wgt.push_back(make_double2(v.real(), v.imag()));
+      C[0] += w1.real();
+      C[1] += w2.real();
+    }
+  }
+}
+
+namespace {
+
 eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   const Grid& g = h.g;
   const int p = g.p, q = g.q, ni = q * q, nb = 4 * q;
@@ -112,27 +144,20 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
     // elliptic unknown V: (A - (alpha/tau)^2) V = (alpha/tau^2) f_v + (1/tau) A f_u,
     // U = (tau V - f_u) / alpha; sums: V = Re sum c V_p, U = Re sum (c tau/alpha) V_p - C0 f_u
     for (int j = 0; j < h.P; ++j) {
-      const cx a = h.alpha[j], c = h.cw[j];
-      const cx c0 = a / (tau * tau), c1 = 1.0 / tau, w0 = c, w1 = c * tau / a;
+      const cx a = h.alpha[j];
+      const cx c0 = a / (tau * tau), c1 = 1.0 / tau;
       coef.push_back(make_double2(c0.real(), c0.imag()));
       coef.push_back(make_double2(c1.real(), c1.imag()));
-      wgt.push_back(make_double2(w0.real(), w0.imag()));
-      wgt.push_back(make_double2(w1.real(), w1.imag()));
-      C[0] += (c / a).real();
     }
   } else {
     h.K = 3; h.F = 3;
     const double f = o.sw_f, gg = o.sw_g, H = o.sw_H, tf = tau * f;
     if (!(gg > 0) || !(H > 0)) return fail(EO_ERR_INVALID_ARG, "sw_g and sw_H must be positive");
     for (int j = 0; j < h.P; ++j) {
-      const cx a = h.alpha[j], c = h.cw[j];
+      const cx a = h.alpha[j];
       const cx D = a * a + tf * tf;
       const cx c0 = D / (tau * tau * gg * H * a), c1 = -1.0 / (tau * gg), c2 = -f / (gg * a);
-      const cx w0 = c, w1 = c * (-a / D), w2 = c * (-tf / D);
       for (cx v : {c0, c1, c2}) coef.push_back(make_double2(v.real(), v.imag()));
-      for (cx v : {w0, w1, w2}) wgt.push_back(make_double2(v.real(), v.imag()));
-      C[0] += w1.real();
-      C[1] += w2.real();
       // wall right-hand sides per side S, E, N, W: coefficients of (F1, F2)
       const cx xw0 = -a / (tau * gg), xw1 = -f / gg;       // x-walls: -(a F1 + tau f F2)/(tau g)
       const cx yw0 = f / gg, yw1 = -a / (tau * gg);         // y-walls: (tau f F1 - a F2)/(tau g)
@@ -143,6 +168,7 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
       for (int sd = 0; sd < 4; ++sd) nu.push_back(make_double2(sg[sd] * a.real(), sg[sd] * a.imag()));
     }
   }
+  pole_weights(h, h.cw, wgt, C);
   std::memcpy(h.C, C, sizeof(C));
   // scaled differentiation matrices
   for (int i = 0; i < p * p; ++i) {
@@ -331,6 +357,49 @@ eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double* coeff, c
   *out = hs;
   set_error("");
   return EO_OK;
+}
+
+eo_status eo_fit_function(eo_handle_t hd, int kind, double c, double* b, double* err) {
+  if (!hd || !b) return fail(EO_ERR_INVALID_ARG, "null argument");
+  std::vector<cx> bv;
+  double e = 0;
+  eo_status rc = fit_function(hd->h.fit, kind, c, bv, e);
+  if (rc) return rc;
+  for (size_t i = 0; i < bv.size(); ++i) { b[2 * i] = bv[i].real(); b[2 * i + 1] = bv[i].imag(); }
+  if (err) *err = e;
+  set_error("");
+  return EO_OK;
+}
+
+eo_status eo_apply_functions(eo_handle_t hd, int n_out, const double* b_sets, const double* u_dev, double* out_dev,
+                             void* stream) {
+  if (!hd || !b_sets || !u_dev || !out_dev) return fail(EO_ERR_INVALID_ARG, "null argument");
+  if (n_out < 1) return fail(EO_ERR_INVALID_ARG, "n_out must be >= 1");
+  Handle& h = hd->h;
+  const int N = h.fit.N(), M = (N - 1) / 2;
+  std::vector<cd> wall;
+  std::vector<double> Call(4 * (size_t)n_out);
+  for (int k = 0; k < n_out; ++k) {
+    const double* bk = b_sets + (size_t)2 * N * k;
+    std::vector<cx> cw(h.P);
+    for (int j = 0; j < h.P; ++j) {
+      const int i = M + j;
+      if (!std::isfinite(bk[2 * i]) || !std::isfinite(bk[2 * i + 1])) return fail(EO_ERR_INVALID_ARG, "non-finite residue");
+      cw[j] = (j == 0 ? 1.0 : 2.0) * cx(bk[2 * i], bk[2 * i + 1]);
+    }
+    std::vector<cd> w;
+    pole_weights(h, cw, w, &Call[4 * (size_t)k]);
+    wall.insert(wall.end(), w.begin(), w.end());
+  }
+  cudaStream_t st = (cudaStream_t)stream;
+  cd* dw = nullptr;
+  EO_CUDA_TRY(cudaMallocAsync(&dw, sizeof(cd) * wall.size(), st));
+  EO_CUDA_TRY(cudaMemcpyAsync(dw, wall.data(), sizeof(cd) * wall.size(), cudaMemcpyHostToDevice, st));
+  eo_status rc = apply_functions(h, n_out, dw, Call.data(), u_dev, out_dev, st);
+  cudaFreeAsync(dw, st);
+  EO_CUDA_TRY(cudaStreamSynchronize(st));
+  if (!rc) set_error("");
+  return rc;
 }
 
 eo_status eo_batch_create(int n, const eo_handle_t* handles, double* const* u_dev, const int* n_rhs,

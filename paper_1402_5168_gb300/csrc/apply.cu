@@ -557,13 +557,10 @@ eo_status dispatch(int prec, int nc, Args&&... args) {
 
 #define EO_SET_SMEM(kern, bytes)                                                            \
   do {                                                                                        \
-    /* raise the dynamic shared-memory cap once per kernel (outside any capture) */          \
-    static size_t cap_ = 48 * 1024;                                                           \
-    if ((bytes) > cap_) {                                                                     \
-      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, 200 * 1024 + 8192)); \
-      EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));     \
-      cap_ = 200 * 1024 + 8192;                                                               \
-    }                                                                                         \
+    /* raise the dynamic shared-memory cap once per kernel and device */                     \
+    static size_t cap_[64] = {};                                                              \
+    eo_status rs_ = ensure_smem((const void*)(kern), (bytes), cap_, 200 * 1024 + 8192);       \
+    if (rs_) return rs_;                                                                      \
   } while (0)
 
 template <int NC, typename TA>
@@ -654,18 +651,25 @@ Sweep base_sweep(const Handle& h, int R, int p0, int np, const cd* wgt) {
   return s;
 }
 
-// One application of sum_p c_p (tau L - alpha_p)^{-1} restricted to poles
-// [p0, p0 + np) with accumulation weights wgt (device [P][K]) and post constants C.
-eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, int np, const cd* wgt,
-                   const double* C, cudaStream_t st) {
+LeafGeo leaf_geo(const Handle& h) {
+  const Grid& g = h.g;
+  const int q = g.q;
+  return LeafGeo{g.nlx, g.nly, g.p, q, g.n_int, g.n_hseg, h.dDx, h.dDx + g.p * g.p, h.dDx + 2 * g.p * g.p,
+                 h.dDx + 2 * g.p * g.p + q * q};
+}
+
+// First part of a step: pre-map, upward sweep, root, downward merges.  Leaves
+// every pole's interface and boundary values in h.E and returns the sweep
+// description (sources of the leaf solves) in s.
+eo_status sweep_to_edges(Handle& h, const double* uin, int R, int p0, int np, const cd* wgt, Sweep& s,
+                         cudaStream_t st) {
   const Grid& g = h.g;
   const int q = g.q, ni = q * q, nb = 4 * q;
   const int nleaf = g.nlx * g.nly;
   const int L = h.plan.L();
   eo_status rc;
-  Sweep s = base_sweep(h, R, p0, np, wgt);
-  LeafGeo geo{g.nlx, g.nly, g.p, q, g.n_int, g.n_hseg, h.dDx, h.dDx + g.p * g.p, h.dDx + 2 * g.p * g.p,
-              h.dDx + 2 * g.p * g.p + q * q};
+  s = base_sweep(h, R, p0, np, wgt);
+  const LeafGeo geo = leaf_geo(h);
   if (h.kind == EO_WAVE_DIRICHLET) {
     // s = (alpha / tau^2) v + (1 / tau) A u: sources v (field 1) and A u (pre-map)
     if ((rc = h.trace_begin(st))) return rc;
@@ -728,6 +732,19 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
     if ((rc = dispatch<DownMerge>(h.lv[l].fp32, nc, s, m, h.E, tu.nt, st))) return rc;
     if ((rc = h.trace_end(TR_DOWN_MERGE, st))) return rc;
   }
+  return EO_OK;
+}
+
+// Second part: leaf interiors with the weighted pole sum (weights s.wgt), edge
+// sums and the post-map with constants C, into uout.
+eo_status finish_step(Handle& h, const Sweep& s, const double* uin, double* uout, const double* C,
+                      cudaStream_t st) {
+  const Grid& g = h.g;
+  const int q = g.q, ni = q * q, nb = 4 * q;
+  const int nleaf = g.nlx * g.nly;
+  const int R = s.R, np = s.P;
+  const LeafGeo geo = leaf_geo(h);
+  eo_status rc;
   // down: leaves with the pole sum
   int nchunk = 1;
   if ((rc = h.trace_begin(st))) return rc;
@@ -762,6 +779,16 @@ eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, in
   }
   if ((rc = h.trace_end(TR_POST, st))) return rc;
   return EO_OK;
+}
+
+// One application of sum_p c_p (tau L - alpha_p)^{-1} restricted to poles
+// [p0, p0 + np) with accumulation weights wgt (device [P][K]) and post constants C.
+eo_status run_step(Handle& h, const double* uin, double* uout, int R, int p0, int np, const cd* wgt,
+                   const double* C, cudaStream_t st) {
+  Sweep s;
+  eo_status rc = sweep_to_edges(h, uin, R, p0, np, wgt, s, st);
+  if (rc) return rc;
+  return finish_step(h, s, uin, uout, C, st);
 }
 
 }  // namespace
@@ -924,6 +951,23 @@ eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st) {
   if (cur != u)
     EO_CUDA_TRY(cudaMemcpyAsync(u, cur, sizeof(double) * (size_t)n_rhs * h.F * h.g.n_nodes,
                                 cudaMemcpyDeviceToDevice, st));
+  return EO_OK;
+}
+
+// out[k] = f_k(tau L) u for n_out pole-weight sets that share the poles (dense
+// output, phi-functions): one pre-map, upward sweep, root and downward merge pass,
+// then leaf interiors, pole sums and post-map once per set.
+eo_status apply_functions(Handle& h, int n_out, const cd* wgts, const double* Cs, const double* u, double* out,
+                          cudaStream_t st) {
+  eo_status rc = autotune(h, 1, st);
+  if (rc) return rc;
+  Sweep s;
+  if ((rc = sweep_to_edges(h, u, 1, 0, h.P, wgts, s, st))) return rc;
+  const size_t nst = (size_t)h.F * h.g.n_nodes;
+  for (int k = 0; k < n_out; ++k) {
+    s.wgt = wgts + (size_t)k * h.P * h.K;
+    if ((rc = finish_step(h, s, u, out + k * nst, Cs + 4 * k, st))) return rc;
+  }
   return EO_OK;
 }
 

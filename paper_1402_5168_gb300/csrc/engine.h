@@ -2,6 +2,7 @@
 #pragma once
 
 #include <cuda_runtime.h>
+#include <complex>
 #include <cstdint>
 #include <string>
 #include <vector>
@@ -62,8 +63,13 @@ void make_plan(const Grid& g, Plan& plan);
 struct Fit {
   std::vector<double> are, aim, bre, bim;   // 2M+1 poles / residues, m = -M..M
   double X = 0, sigma = 0, s = 0;
+  int E = 0;                                // wide fits: outer pairs fitted by least squares (0: all)
   int N() const { return (int)are.size(); }
 };
+
+// Residues on the poles of f for exp(c z) (kind 0) or phi1(z) (kind 1), and the
+// band error max |f(ix) - R(ix)| on [-X, X].
+eo_status fit_function(const Fit& f, int kind, double c, std::vector<std::complex<double>>& b, double& err);
 
 // Widest band X for a given odd pole count; returns EO_ERR_FIT if none.
 eo_status fit_for_poles(int n_poles, double delta, Fit& out);

@@ -507,16 +507,6 @@ FdArgs fd_args(const Handle& h, int nleaf, int ncol) {
   return f;
 }
 
-template <typename Kern>
-eo_status raise_smem(Kern k, size_t bytes, size_t& cap) {
-  if (bytes > cap) {
-    if (bytes > 48 * 1024)
-      EO_CUDA_TRY(cudaFuncSetAttribute(k, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes));
-    cap = bytes;
-  }
-  return EO_OK;
-}
-
 size_t fd_up_smem(int q, int K, int ncol) {
   const int qq = q * q;
   return sizeof(double) * ((size_t)4 * qq + 10 * q + even_up((size_t)ncol * K * qq)) +
@@ -538,8 +528,8 @@ eo_status up_leaf_t(Handle& h, const Sweep& s, const FdArgs& f, cd* h0, cudaStre
   const int ppc = (s.P + nchunk - 1) / nchunk;
   nchunk = (s.P + ppc - 1) / ppc;
   const size_t smem = fd_up_smem(q, s.K, f.ncol);
-  static size_t cap = 48 * 1024;
-  eo_status rc = raise_smem(k_fd_up_leaf<M>, smem, cap);
+  static size_t cap[64] = {};
+  eo_status rc = ensure_smem((const void*)k_fd_up_leaf<M>, smem, cap, 0);
   if (rc) return rc;
   k_fd_up_leaf<M><<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, (const typename M::CT*)h.fd_dc, ppc, h0);
   EO_CUDA_TRY(cudaGetLastError());
@@ -564,8 +554,8 @@ eo_status down_leaf_t(Handle& h, const Sweep& s, const FdArgs& f, int& nchunk, c
   const int ppc = (s.P + nchunk - 1) / nchunk;
   nchunk = (s.P + ppc - 1) / ppc;
   const size_t smem = fd_down_smem(q, s.K, f.ncol);
-  static size_t cap = 48 * 1024;
-  eo_status rc = raise_smem(k_fd_down_leaf<M>, smem, cap);
+  static size_t cap[64] = {};
+  eo_status rc = ensure_smem((const void*)k_fd_down_leaf<M>, smem, cap, 0);
   if (rc) return rc;
   k_fd_down_leaf<M><<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, wd, h.lv[0].bseg, ppc, h.E, h.part);
   EO_CUDA_TRY(cudaGetLastError());

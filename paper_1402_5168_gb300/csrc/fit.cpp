@@ -193,7 +193,8 @@ static bool accept(double X, double delta, const std::vector<cplx>& al,
 }
 
 static void store(const std::vector<cplx>& al, const std::vector<cplx>& b, double r,
-                  double X, double sigma, double s, Fit& out) {
+                  double X, double sigma, double s, Fit& out, int E = 0) {
+  out.E = E;
   const int N = (int)al.size();
   out.are.resize(N); out.aim.resize(N); out.bre.resize(N); out.bim.resize(N);
   const double scale = 1.0 / std::max(1.0, r);
@@ -366,7 +367,7 @@ eo_status fit_wide(double X, double delta, Fit& out) {
   for (const auto& c : cand) {
     double r = 0;
     if (wide_candidate(X, delta, c[0], c[1], (int)c[2], c[3], al, b, &r)) {
-      store(al, b, r, X, c[1] * c[0], c[0], out);
+      store(al, b, r, X, c[1] * c[0], c[0], out, (int)c[2]);
       return EO_OK;
     }
   }
@@ -385,7 +386,7 @@ static eo_status fit_wide_poles(int N, double delta, Fit& out) {
     if (X < 8.0) continue;
     double r = 0;
     if (wide_candidate(X, delta, c[0], c[1], (int)c[2], c[3], al, b, &r) && (int)al.size() == N) {
-      store(al, b, r, X, c[1] * c[0], c[0], out);
+      store(al, b, r, X, c[1] * c[0], c[0], out, (int)c[2]);
       return EO_OK;
     }
   }
@@ -409,6 +410,105 @@ eo_status fit_for_band(double X, double delta, int nmax, Fit& out) {
       }
   }
   return fail(EO_ERR_FIT, "band*tau too wide for the supported pole counts");
+}
+
+// ---------------------------------------------------------------- other functions, same poles
+// Values on the imaginary axis of the functions the same poles can carry
+// (dense output and phi-functions, Section 1.2 remarks on reusing the solves):
+//   kind 0: exp(c z), 0 < c <= 1;   kind 1: phi1(z) = (exp(z) - 1) / z.
+static cplx fn_value(int kind, double c, double th) {
+  if (kind == 0) return std::exp(cplx(0.0, c * th));
+  if (std::abs(th) < 1e-6) return cplx(1.0 - th * th / 6.0, th / 2.0 - th * th * th / 24.0);
+  return (std::exp(cplx(0.0, th)) - 1.0) / cplx(0.0, th);
+}
+
+// Residues b of sum_m b_m / (z - alpha_m) on the poles of `f` for the function
+// `kind` (parameter c).  Poles of a narrow fit: every residue by least squares on
+// [0, X].  Poles of a wide fit: the central residues from the trapezoidal rule of
+// the Cauchy integral of the function along the pole line (spacing s),
+//   exp(c z):  b_m = -(s / 2 pi) exp(c alpha_m),
+//   phi1(z):   b_m = -(s / 2 pi) (exp(alpha_m) - 1) / alpha_m  (the integral over c in [0, 1]),
+// and the E outermost pairs by least squares, as for exp(z) itself.
+// err: max |f(i x) - R(i x)| on [0, X] (both signs by conjugate symmetry).
+eo_status fit_function(const Fit& f, int kind, double c, std::vector<cplx>& b, double& err) {
+  if (kind != 0 && kind != 1) return fail(EO_ERR_INVALID_ARG, "unknown function kind");
+  if (kind == 0 && !(c > 0 && c <= 1)) return fail(EO_ERR_INVALID_ARG, "c must be in (0, 1]");
+  const int N = f.N(), M = (N - 1) / 2;
+  const double X = f.X, s = f.s;
+  std::vector<cplx> al(N);
+  for (int i = 0; i < N; ++i) al[i] = cplx(f.are[i], f.aim[i]);
+  b.assign(N, cplx(0, 0));
+  int E = f.E > 0 ? f.E : M;   // least-squares pairs beyond the centre
+  if (f.E > 0) {
+    for (int m = 0; m <= M; ++m) {
+      const cplx a = al[m + M];
+      b[m + M] = kind == 0 ? -(s / (2 * M_PI)) * std::exp(c * a) : -(s / (2 * M_PI)) * (std::exp(a) - 1.0) / a;
+      b[M - m] = std::conj(b[m + M]);
+    }
+    b[M] = b[M].real();
+  }
+  // least squares for b_0 (narrow fits) and the E outer pairs
+  const bool with_centre = f.E == 0;
+  const int ns = (int)std::ceil(X * (with_centre ? 20.0 : 8.0)) + 41;
+  const int rows = 2 * ns, cols = 2 * E + (with_centre ? 1 : 0);
+  std::vector<double> A((size_t)rows * cols), t(rows), x;
+  par_for(ns, [&](int64_t i0, int64_t i1) {
+    for (int64_t i = i0; i < i1; ++i) {
+      const double th = X * i / (ns - 1);
+      const cplx z(0.0, th);
+      cplx rc(0, 0);
+      if (!with_centre)
+        for (int m = -(M - E); m <= M - E; ++m) rc += b[m + M] / (z - al[m + M]);
+      const cplx tg = fn_value(kind, c, th) - rc;
+      t[i] = tg.real();
+      t[ns + i] = tg.imag();
+      int col = 0;
+      if (with_centre) {
+        const cplx v = 1.0 / (z - al[M]);
+        A[(size_t)col * rows + i] = v.real();
+        A[(size_t)col * rows + ns + i] = v.imag();
+        ++col;
+      }
+      for (int k = 0; k < E; ++k, col += 2) {
+        const int mm = M - E + 1 + k;
+        const cplx pp = 1.0 / (z - al[mm + M]), nn = 1.0 / (z - al[-mm + M]);
+        const cplx c1 = pp + nn, c2 = cplx(0, 1) * (pp - nn);
+        A[(size_t)col * rows + i] = c1.real();
+        A[(size_t)col * rows + ns + i] = c1.imag();
+        A[(size_t)(col + 1) * rows + i] = c2.real();
+        A[(size_t)(col + 1) * rows + ns + i] = c2.imag();
+      }
+    }
+  });
+  std::vector<double> sc(cols);
+  for (int j = 0; j < cols; ++j) {
+    double s2 = 0;
+    for (int i = 0; i < rows; ++i) s2 += A[(size_t)j * rows + i] * A[(size_t)j * rows + i];
+    sc[j] = std::sqrt(s2);
+    if (sc[j] == 0) return fail(EO_ERR_FIT, "degenerate least-squares column");
+    for (int i = 0; i < rows; ++i) A[(size_t)j * rows + i] /= sc[j];
+  }
+  if (!lsq(A, t, rows, cols, x)) return fail(EO_ERR_FIT, "least squares failed");
+  int col = 0;
+  if (with_centre) { b[M] = x[0] / sc[0]; col = 1; }
+  for (int k = 0; k < E; ++k, col += 2) {
+    const int mm = M - E + 1 + k;
+    b[mm + M] = cplx(x[col] / sc[col], x[col + 1] / sc[col + 1]);
+    b[-mm + M] = std::conj(b[mm + M]);
+  }
+  const int64_t nb = (int64_t)std::ceil(X / 0.02) + 1;
+  std::vector<double> part(64, 0.0);
+  std::atomic<int> slot(0);
+  par_for(nb, [&](int64_t i0, int64_t i1) {
+    double mx = 0;
+    for (int64_t i = i0; i < i1; ++i) {
+      const double th = X * i / (nb - 1);
+      mx = std::max(mx, std::abs(fn_value(kind, c, th) - Reval(th, al, b)));
+    }
+    part[slot++] = mx;
+  });
+  err = *std::max_element(part.begin(), part.end());
+  return EO_OK;
 }
 
 }  // namespace eo

@@ -19,6 +19,22 @@ typedef double2 cd;   // complex FP64, interleaved (re, im)
       return fail(EO_ERR_CUDA, std::string(#expr) + ": " + cudaGetErrorString(e_)); \
   } while (0)
 
+// Raise a kernel's dynamic shared-memory cap (and prefer the full carveout) on the
+// current device when `bytes` exceeds the 48 KB default.  The attribute is per
+// device, so the record `cap` keeps one entry per device ordinal (< 64; larger
+// ordinals set it on every call).
+inline eo_status ensure_smem(const void* kern, size_t bytes, size_t* cap, size_t set_to) {
+  if (bytes <= 48 * 1024) return EO_OK;
+  int dev = 0;
+  EO_CUDA_TRY(cudaGetDevice(&dev));
+  if (dev < 64 && bytes <= cap[dev]) return EO_OK;
+  const size_t v = set_to > bytes ? set_to : bytes;
+  EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)v));
+  EO_CUDA_TRY(cudaFuncSetAttribute(kern, cudaFuncAttributePreferredSharedMemoryCarveout, 100));
+  if (dev < 64) cap[dev] = v;
+  return EO_OK;
+}
+
 // Launch shape chosen by the autotuner (0: the default heuristic).
 struct Tuned {
   int nc = 0;   // columns per block
@@ -148,6 +164,10 @@ eo_status apply(Handle& h, double* u, int n_rhs, int n_steps, cudaStream_t st);
 eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStream_t st);
 eo_status apply_adjoint(Handle& h, double* y, int n_rhs, int n_steps, cudaStream_t st);
 eo_status apply_resolvent_noalloc(Handle& h, int j, const double* u, double* x, cudaStream_t st);
+eo_status apply_functions(Handle& h, int n_out, const cd* wgts, const double* Cs, const double* u, double* out,
+                          cudaStream_t st);
+void pole_weights(const Handle& h, const std::vector<std::complex<double>>& cw, std::vector<cd>& wgt, double C[4]);
+
 // independent instances advanced together through one CUDA graph (apply.cu)
 struct Batch {
   std::vector<Handle*> h;
