@@ -122,6 +122,7 @@ struct F64 {
   __device__ static void mac(A& a, R x, R y) { a = fma(x, y, a); }
   __device__ static void msub(A& a, R x, R y) { a = fma(-x, y, a); }
   __device__ static R norm(A a) { return a; }
+  __device__ static void acc_add(A& a, const A& b) { a += b; }
   __device__ static A acc_from(double v) { return v; }
   __device__ static double acc_to(A a) { return a; }
   __device__ static void ldc(const CT* p, R& re, R& im) { const CT v = __ldg(p); re = v.x; im = v.y; }
@@ -160,6 +161,14 @@ struct Pair {
   __device__ static A acc_from(double v) {
     const float h = __double2float_rn(v);
     return PairAcc{h, __double2float_rn(v - (double)h)};
+  }
+  // a += b for two accumulators: two-sum of the leading parts, corrections added
+  __device__ static void acc_add(A& a, const A& b) {
+    const float t = __fadd_rn(a.s, b.s);
+    const float bp = __fsub_rn(t, a.s);
+    const float err = __fadd_rn(__fsub_rn(a.s, __fsub_rn(t, bp)), __fsub_rn(b.s, bp));
+    a.s = t;
+    a.c = __fadd_rn(a.c, __fadd_rn(b.c, err));
   }
   __device__ static double acc_to(A a) { return (double)a.s + (double)a.c; }
   __device__ static void ldc(const CT* p, R& re, R& im) {
@@ -247,9 +256,33 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typ
     if (pl + 1 < pend) prefetch(pl + 1, buf ^ 1);
     const typename M::CT* DC = dcs + (size_t)buf * K * qq;
     Cx<M>* tb = ts + (size_t)(buf * ncol + c) * 4 * q;
-    // z^(a, b) = sum_k dc_k(a, b) g^_k(a, b); row contractions with rS^, rN^
-    A sr = M::zero(), si = M::zero(), nr = M::zero(), ni_ = M::zero();
-    for (int b = 0; b < q; ++b) {
+    // z^(a, b) = sum_k dc_k(a, b) g^_k(a, b); row contractions with rS^, rN^.
+    // Two columns b, b + 1 per iteration with separate partial sums (more
+    // independent dependency chains per thread).
+    A sr[2], si[2], nr[2], ni_[2];
+#pragma unroll
+    for (int h2 = 0; h2 < 2; ++h2) sr[h2] = si[h2] = nr[h2] = ni_[h2] = M::zero();
+    int b = 0;
+    for (; b + 1 < q; b += 2) {
+      const int i0 = b * q + a, i1 = i0 + q;
+      A zr0 = M::zero(), zi0 = M::zero(), zr1 = M::zero(), zi1 = M::zero();
+      for (int kk = 0; kk < K; ++kk) {
+        R dr0, di0, dr1, di1;
+        M::lds(DC + kk * qq + i0, dr0, di0);
+        M::lds(DC + kk * qq + i1, dr1, di1);
+        const R g0 = g[kk * qq + i0], g1 = g[kk * qq + i1];
+        M::mac(zr0, dr0, g0); M::mac(zi0, di0, g0);
+        M::mac(zr1, dr1, g1); M::mac(zi1, di1, g1);
+      }
+      const R zre0 = M::norm(zr0), zim0 = M::norm(zi0), zre1 = M::norm(zr1), zim1 = M::norm(zi1);
+      M::mac(sr[0], zre0, rS[b]); M::mac(si[0], zim0, rS[b]);
+      M::mac(nr[0], zre0, rN[b]); M::mac(ni_[0], zim0, rN[b]);
+      M::mac(sr[1], zre1, rS[b + 1]); M::mac(si[1], zim1, rS[b + 1]);
+      M::mac(nr[1], zre1, rN[b + 1]); M::mac(ni_[1], zim1, rN[b + 1]);
+      zc[i0] = Cx<M>{zre0, zim0};
+      zc[i1] = Cx<M>{zre1, zim1};
+    }
+    if (b < q) {
       const int idx = b * q + a;
       A zr = M::zero(), zi = M::zero();
       for (int kk = 0; kk < K; ++kk) {
@@ -260,23 +293,37 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typ
         M::mac(zi, di, gv);
       }
       const R zre = M::norm(zr), zim = M::norm(zi);
-      M::mac(sr, zre, rS[b]); M::mac(si, zim, rS[b]);
-      M::mac(nr, zre, rN[b]); M::mac(ni_, zim, rN[b]);
+      M::mac(sr[0], zre, rS[b]); M::mac(si[0], zim, rS[b]);
+      M::mac(nr[0], zre, rN[b]); M::mac(ni_[0], zim, rN[b]);
       zc[idx] = Cx<M>{zre, zim};
     }
-    tb[a] = Cx<M>{M::norm(sr), M::norm(si)};
-    tb[2 * q + a] = Cx<M>{M::norm(nr), M::norm(ni_)};
+    M::acc_add(sr[0], sr[1]); M::acc_add(si[0], si[1]);
+    M::acc_add(nr[0], nr[1]); M::acc_add(ni_[0], ni_[1]);
+    tb[a] = Cx<M>{M::norm(sr[0]), M::norm(si[0])};
+    tb[2 * q + a] = Cx<M>{M::norm(nr[0]), M::norm(ni_[0])};
     __syncthreads();
     // column contractions with rE^, rW^ (thread a takes column b = a)
     {
-      A er = M::zero(), ei = M::zero(), wr = M::zero(), wi = M::zero();
-      for (int m = 0; m < q; ++m) {
-        const Cx<M> z = zc[a * q + m];
-        M::mac(er, z.re, rE[m]); M::mac(ei, z.im, rE[m]);
-        M::mac(wr, z.re, rW[m]); M::mac(wi, z.im, rW[m]);
+      A er[2], ei[2], wr[2], wi[2];
+#pragma unroll
+      for (int h2 = 0; h2 < 2; ++h2) er[h2] = ei[h2] = wr[h2] = wi[h2] = M::zero();
+      int m = 0;
+      for (; m + 1 < q; m += 2) {
+        const Cx<M> z0 = zc[a * q + m], z1 = zc[a * q + m + 1];
+        M::mac(er[0], z0.re, rE[m]); M::mac(ei[0], z0.im, rE[m]);
+        M::mac(wr[0], z0.re, rW[m]); M::mac(wi[0], z0.im, rW[m]);
+        M::mac(er[1], z1.re, rE[m + 1]); M::mac(ei[1], z1.im, rE[m + 1]);
+        M::mac(wr[1], z1.re, rW[m + 1]); M::mac(wi[1], z1.im, rW[m + 1]);
       }
-      tb[q + a] = Cx<M>{M::norm(er), M::norm(ei)};
-      tb[3 * q + a] = Cx<M>{M::norm(wr), M::norm(wi)};
+      if (m < q) {
+        const Cx<M> z = zc[a * q + m];
+        M::mac(er[0], z.re, rE[m]); M::mac(ei[0], z.im, rE[m]);
+        M::mac(wr[0], z.re, rW[m]); M::mac(wi[0], z.im, rW[m]);
+      }
+      M::acc_add(er[0], er[1]); M::acc_add(ei[0], ei[1]);
+      M::acc_add(wr[0], wr[1]); M::acc_add(wi[0], wi[1]);
+      tb[q + a] = Cx<M>{M::norm(er[0]), M::norm(ei[0])};
+      tb[3 * q + a] = Cx<M>{M::norm(wr[0]), M::norm(wi[0])};
     }
     __syncthreads();
     // back to nodal edge values: h_S, h_N through V_x; h_E, h_W through V_y
@@ -397,8 +444,8 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const t
     // acc_k(a, b) -= Re(wd_k(a, b) (A_ib u_b)^(a, b))
     const Cx<M> uSa = uhc[a], uNa = uhc[2 * q + a];
     const typename M::CT* W = wds + (size_t)buf * K * qq;
-    for (int b = 0; b < q; ++b) {
-      const int idx = b * q + a;
+    // (A_ib u_b)^(a, b) for one column b, then the weighted update of acc
+    auto bnd = [&](int b, R& brn, R& bin) {
       const Cx<M> uE = uhc[q + b], uW = uhc[3 * q + b];
       const R cs = cS[b], cn = cN[b];
       A br = M::zero(), bi = M::zero();
@@ -406,7 +453,30 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const t
       M::mac(br, cEa, uE.re); M::mac(bi, cEa, uE.im);
       M::mac(br, uSa.re, cs); M::mac(bi, uSa.im, cs);
       M::mac(br, uNa.re, cn); M::mac(bi, uNa.im, cn);
-      const R brn = M::norm(br), bin = M::norm(bi);
+      brn = M::norm(br);
+      bin = M::norm(bi);
+    };
+    int b = 0;
+    for (; b + 1 < q; b += 2) {
+      const int i0 = b * q + a, i1 = i0 + q;
+      R br0, bi0, br1, bi1;
+      bnd(b, br0, bi0);
+      bnd(b + 1, br1, bi1);
+      for (int kk = 0; kk < K; ++kk) {
+        R wr0, wi0, wr1, wi1;
+        M::lds(W + kk * qq + i0, wr0, wi0);
+        M::lds(W + kk * qq + i1, wr1, wi1);
+        A t0 = ac[kk * qq + i0], t1 = ac[kk * qq + i1];
+        M::msub(t0, wr0, br0); M::mac(t0, wi0, bi0);
+        M::msub(t1, wr1, br1); M::mac(t1, wi1, bi1);
+        ac[kk * qq + i0] = t0;
+        ac[kk * qq + i1] = t1;
+      }
+    }
+    if (b < q) {
+      const int idx = b * q + a;
+      R brn, bin;
+      bnd(b, brn, bin);
       for (int kk = 0; kk < K; ++kk) {
         R wr, wi;
         M::lds(W + kk * qq + idx, wr, wi);
