@@ -350,14 +350,19 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typ
 }
 
 // ---------------------------------------------------------------- down: leaf interiors + pole sum
-template <class M>
+// QR > 0: q == QR and K == 3 fixed at compile time; each thread keeps its row of
+// the pole-sum accumulators in registers (no shared-memory read-modify-write,
+// smaller shared footprint, more resident blocks).  QR == 0: any q, accumulators
+// in shared memory.
+template <class M, int QR>
 __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const typename M::CT* __restrict__ wdt,
                                                       const int* __restrict__ bseg, int ppc,
                                                       const cd* __restrict__ E, double* __restrict__ part) {
   typedef typename M::R R;
   typedef typename M::A A;
   extern __shared__ double fsm[];
-  const int q = f.q, qq = q * q, K = s.K, ncol = f.ncol;
+  constexpr bool REG = QR > 0;
+  const int q = REG ? QR : f.q, qq = q * q, K = REG ? 3 : s.K, ncol = f.ncol;
   const FdLayout Lo{q, qq};
   const int c = threadIdx.x / q, a = threadIdx.x - c * q;
   const int ncols = f.nleaf * s.R;
@@ -367,25 +372,40 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const t
   int box = 0, r = 0;
   if (valid) col_box(col, s.R, box, r);
   R* cst = (R*)fsm;
-  A* acc = (A*)(cst + Lo.size());                                  // [ncol][K][qq]
-  R* T = (R*)(acc + even_up((size_t)ncol * K * qq));               // [ncol][qq]
+  A* acc = (A*)(cst + Lo.size());                                  // [ncol][K][qq] (shared variant)
+  R* T = REG ? (R*)(cst + Lo.size()) : (R*)(acc + even_up((size_t)ncol * K * qq));   // [ncol][qq]
+  A accr[REG ? 3 : 1][REG ? QR : 1];                               // register variant
   Cx<M>* ub = (Cx<M>*)(T + even_up((size_t)ncol * qq));            // [ncol][4][q]
   Cx<M>* uh = ub + (size_t)ncol * 4 * q;                           // [ncol][4][q]
   typename M::CT* wds = (typename M::CT*)(uh + (size_t)ncol * 4 * q);   // [2][K][qq] pole tables
   cd* rb = (cd*)(wds + (size_t)2 * K * qq);                        // [2][ncol][4][q] raw edge values
   load_consts<M>(f.c, cst, Lo.size());
   // chunk 0 starts from the pole-summed particular part, sum_k' gsum[k][k'] g^_k'
-  for (int e = threadIdx.x; e < ncol * K * qq; e += blockDim.x) {
-    const int cc = e / (K * qq), rem = e - cc * K * qq, kk = rem / qq, idx = rem - kk * qq;
-    const int colc = blockIdx.x * ncol + cc;
-    double v = 0.0;
-    if (chunk == 0 && colc < ncols) {
-      int bx, rr;
-      col_box(colc, s.R, bx, rr);
-      for (int k2 = 0; k2 < K; ++k2)
-        v = fma(f.gsum[(kk * K + k2) * qq + idx], f.ghat[((long long)(rr * K + k2) * f.nleaf + bx) * qq + idx], v);
+  if constexpr (REG) {
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+      for (int bq = 0; bq < QR; ++bq) {
+        double v = 0.0;
+        const int idx = bq * QR + a;
+        if (chunk == 0 && valid)
+          for (int k2 = 0; k2 < 3; ++k2)
+            v = fma(f.gsum[(kk * 3 + k2) * qq + idx], f.ghat[((long long)(r * 3 + k2) * f.nleaf + box) * qq + idx], v);
+        accr[kk][bq] = M::acc_from(v);
+      }
+  } else {
+    for (int e = threadIdx.x; e < ncol * K * qq; e += blockDim.x) {
+      const int cc = e / (K * qq), rem = e - cc * K * qq, kk = rem / qq, idx = rem - kk * qq;
+      const int colc = blockIdx.x * ncol + cc;
+      double v = 0.0;
+      if (chunk == 0 && colc < ncols) {
+        int bx, rr;
+        col_box(colc, s.R, bx, rr);
+        for (int k2 = 0; k2 < K; ++k2)
+          v = fma(f.gsum[(kk * K + k2) * qq + idx], f.ghat[((long long)(rr * K + k2) * f.nleaf + bx) * qq + idx], v);
+      }
+      acc[e] = M::acc_from(v);
     }
-    acc[e] = M::acc_from(v);
   }
   const R* Vxi = cst + Lo.Vxi();
   const R* Vyi = cst + Lo.Vyi();
@@ -456,6 +476,22 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const t
       brn = M::norm(br);
       bin = M::norm(bi);
     };
+    if constexpr (REG) {
+#pragma unroll
+      for (int bq = 0; bq < QR; ++bq) {
+        const int idx = bq * QR + a;
+        R brn, bin;
+        bnd(bq, brn, bin);
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          R wr, wi;
+          M::lds(W + kk * qq + idx, wr, wi);
+          M::msub(accr[kk][bq], wr, brn);
+          M::mac(accr[kk][bq], wi, bin);
+        }
+      }
+      continue;
+    }
     int b = 0;
     for (; b + 1 < q; b += 2) {
       const int i0 = b * q + a, i1 = i0 + q;
@@ -493,11 +529,28 @@ __global__ void __launch_bounds__(256) k_fd_down_leaf(Sweep s, FdArgs f, const t
   R* Tc = T + (size_t)c * qq;
   for (int kk = 0; kk < K; ++kk) {
     __syncthreads();
-    const A* ak = ac + kk * qq;
-    for (int j = 0; j < q; ++j) {
-      A t = M::zero();
-      for (int b = 0; b < q; ++b) M::mac(t, M::norm(ak[b * q + a]), Vy[j * q + b]);
-      Tc[j * q + a] = M::norm(t);
+    if constexpr (REG) {
+      R an[QR];
+#pragma unroll
+      for (int bq = 0; bq < QR; ++bq) {
+        A v = accr[0][bq];
+        if (kk == 1) v = accr[1][bq];
+        if (kk == 2) v = accr[2][bq];
+        an[bq] = M::norm(v);
+      }
+      for (int j = 0; j < q; ++j) {
+        A t = M::zero();
+#pragma unroll
+        for (int bq = 0; bq < QR; ++bq) M::mac(t, an[bq], Vy[j * q + bq]);
+        Tc[j * q + a] = M::norm(t);
+      }
+    } else {
+      const A* ak = ac + kk * qq;
+      for (int j = 0; j < q; ++j) {
+        A t = M::zero();
+        for (int b = 0; b < q; ++b) M::mac(t, M::norm(ak[b * q + a]), Vy[j * q + b]);
+        Tc[j * q + a] = M::norm(t);
+      }
     }
     __syncthreads();
     if (valid) {
@@ -583,9 +636,14 @@ size_t fd_up_smem(int q, int K, int ncol) {
          sizeof(cd) * ((size_t)ncol * qq + (size_t)2 * ncol * 4 * q + (size_t)2 * K * qq);
 }
 
+// leaf q with a register-accumulator instantiation of the down kernel (K = 3)
+constexpr int kFdRegQ = 14;
+bool fd_down_reg(int q, int K) { return q == kFdRegQ && K == 3; }
+
 size_t fd_down_smem(int q, int K, int ncol) {
   const int qq = q * q;
-  return sizeof(double) * ((size_t)4 * qq + 10 * q + even_up((size_t)ncol * K * qq) + even_up((size_t)ncol * qq)) +
+  const size_t accd = fd_down_reg(q, K) ? 0 : even_up((size_t)ncol * K * qq);
+  return sizeof(double) * ((size_t)4 * qq + 10 * q + accd + even_up((size_t)ncol * qq)) +
          sizeof(cd) * ((size_t)2 * ncol * 4 * q + (size_t)2 * K * qq + (size_t)2 * ncol * 4 * q);
 }
 
@@ -624,10 +682,18 @@ eo_status down_leaf_t(Handle& h, const Sweep& s, const FdArgs& f, int& nchunk, c
   const int ppc = (s.P + nchunk - 1) / nchunk;
   nchunk = (s.P + ppc - 1) / ppc;
   const size_t smem = fd_down_smem(q, s.K, f.ncol);
-  static size_t cap[64] = {};
-  eo_status rc = ensure_smem((const void*)k_fd_down_leaf<M>, smem, cap, 0);
-  if (rc) return rc;
-  k_fd_down_leaf<M><<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, wd, h.lv[0].bseg, ppc, h.E, h.part);
+  if (fd_down_reg(q, s.K)) {
+    static size_t cap[64] = {};
+    eo_status rc = ensure_smem((const void*)k_fd_down_leaf<M, kFdRegQ>, smem, cap, 0);
+    if (rc) return rc;
+    k_fd_down_leaf<M, kFdRegQ><<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, wd, h.lv[0].bseg, ppc, h.E,
+                                                                              h.part);
+  } else {
+    static size_t cap[64] = {};
+    eo_status rc = ensure_smem((const void*)k_fd_down_leaf<M, 0>, smem, cap, 0);
+    if (rc) return rc;
+    k_fd_down_leaf<M, 0><<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, wd, h.lv[0].bseg, ppc, h.E, h.part);
+  }
   EO_CUDA_TRY(cudaGetLastError());
   return EO_OK;
 }
