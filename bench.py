@@ -16,6 +16,7 @@ import json
 import os
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -27,7 +28,7 @@ import workloads as W  # noqa: E402
 
 METRIC = "exp(tau L) applies/sec at stated rel. L2 error, mixed/batched vs FP64 on 1 GB300"
 UNIT = "applies/s"
-# FP64 fused multiply-add throughput measured on a GB300 of this machine (8 independent
+# FP64 fused multiply-add throughput measured on a GB300 (8 independent
 # FMA chains per thread, 1216 blocks x 256 threads, ~1995 MHz): 1.207 TFLOP/s
 FP64_PEAK_TFLOPS = 1.207
 # FP32 FMA throughput measured the same way: 75.4 TFLOP/s
@@ -52,7 +53,7 @@ class Clocks:
 
     def __init__(self, index):
         self.p = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"expop_clocks_{os.getpid()}.csv")
         try:
             os.makedirs(os.path.dirname(self.path), exist_ok=True)
             self.f = open(self.path, "w")
@@ -244,7 +245,8 @@ def roofline(op, w, R, tim, prec, pk, pk_kind, fd):
               "frac": d["alu_frac"],
               "peak_source": {"fp32": "FP32 FMA microbenchmark", "fp64": "FP64 FMA microbenchmark",
                               "df32": "FP32 FMA microbenchmark, 48 FP32 instructions per FP32-pair complex "
-                                      "multiply-add"}[d["precision"]] + " on this pool's GB300 (DESIGN.md)"}
+                                      "multiply-add"}[d["precision"]] +
+                             " measured on a GB300 (8 independent FMA chains per thread, 1216 x 256 threads)"}
     else:
         rf = {"bound": "hbm", "achieved": d["gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": d["hbm_frac"],
               "peak_source": pk_kind}

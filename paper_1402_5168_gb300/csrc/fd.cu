@@ -199,13 +199,16 @@ __device__ __forceinline__ void load_consts(const double* c, typename M::R* cst,
 // ---------------------------------------------------------------- up: leaf fluxes
 // Block: ncol columns (leaf, rhs) x q threads; thread (c, a) owns eigen row a of
 // column c.  Blocks along y take consecutive chunks of ppc poles.
-template <class M>
+// QR > 0: q == QR and K == 3 fixed at compile time; each thread keeps its row of
+// the transformed sources g^ in registers (no shared copy).  QR == 0: any q.
+template <class M, int QR>
 __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typename M::CT* __restrict__ dct,
                                                     int ppc, cd* __restrict__ h0) {
   typedef typename M::R R;
   typedef typename M::A A;
   extern __shared__ double fsm[];
-  const int q = f.q, qq = q * q, K = s.K, ncol = f.ncol;
+  constexpr bool REG = QR > 0;
+  const int q = REG ? QR : f.q, qq = q * q, K = REG ? 3 : s.K, ncol = f.ncol;
   const FdLayout Lo{q, qq};
   const int c = threadIdx.x / q, a = threadIdx.x - c * q;
   const int ncols = f.nleaf * s.R;
@@ -215,20 +218,29 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typ
   if (valid) col_box(col, s.R, box, r);
   R* cst = (R*)fsm;
   R* gs = cst + Lo.size();
-  Cx<M>* zs = (Cx<M>*)(gs + even_up((size_t)ncol * K * qq));
+  Cx<M>* zs = (Cx<M>*)(gs + (REG ? 0 : even_up((size_t)ncol * K * qq)));
   Cx<M>* ts = zs + (size_t)ncol * qq;   // [2][ncol][4][q]
   typename M::CT* dcs = (typename M::CT*)(ts + (size_t)2 * ncol * 4 * q);   // [2][K][qq] pole tables
+  R gr[REG ? 3 : 1][REG ? QR : 1];
   load_consts<M>(f.c, cst, Lo.size());
-  for (int e = threadIdx.x; e < ncol * K * qq; e += blockDim.x) {
-    const int cc = e / (K * qq), rem = e - cc * K * qq, kk = rem / qq, idx = rem - kk * qq;
-    const int colc = blockIdx.x * ncol + cc;
-    double v = 0.0;
-    if (colc < ncols) {
-      int bx, rr;
-      col_box(colc, s.R, bx, rr);
-      v = f.ghat[((long long)(rr * K + kk) * f.nleaf + bx) * qq + idx];
+  if constexpr (REG) {
+#pragma unroll
+    for (int kk = 0; kk < 3; ++kk)
+#pragma unroll
+      for (int bq = 0; bq < QR; ++bq)
+        gr[kk][bq] = M::from(valid ? f.ghat[((long long)(r * 3 + kk) * f.nleaf + box) * qq + bq * QR + a] : 0.0);
+  } else {
+    for (int e = threadIdx.x; e < ncol * K * qq; e += blockDim.x) {
+      const int cc = e / (K * qq), rem = e - cc * K * qq, kk = rem / qq, idx = rem - kk * qq;
+      const int colc = blockIdx.x * ncol + cc;
+      double v = 0.0;
+      if (colc < ncols) {
+        int bx, rr;
+        col_box(colc, s.R, bx, rr);
+        v = f.ghat[((long long)(rr * K + kk) * f.nleaf + bx) * qq + idx];
+      }
+      gs[e] = M::from(v);
     }
-    gs[e] = M::from(v);
   }
   __syncthreads();
   const R* Vx = cst + Lo.Vx();
@@ -237,7 +249,7 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typ
   const R* rN = cst + Lo.rN();
   const R* rE = cst + Lo.rE();
   const R* rW = cst + Lo.rW();
-  const R* g = gs + (size_t)c * K * qq;
+  const R* g = gs + (size_t)c * K * qq;   // shared variant only
   Cx<M>* zc = zs + (size_t)c * qq;
   const int pbeg = blockIdx.y * ppc, pend = min(s.P, pbeg + ppc);
   auto prefetch = [&](int pl, int bf) {
@@ -263,6 +275,25 @@ __global__ void __launch_bounds__(256) k_fd_up_leaf(Sweep s, FdArgs f, const typ
 #pragma unroll
     for (int h2 = 0; h2 < 2; ++h2) sr[h2] = si[h2] = nr[h2] = ni_[h2] = M::zero();
     int b = 0;
+    if constexpr (REG) {
+#pragma unroll
+      for (int bq = 0; bq < QR; ++bq) {
+        const int idx = bq * QR + a, h2 = bq & 1;
+        A zr = M::zero(), zi = M::zero();
+#pragma unroll
+        for (int kk = 0; kk < 3; ++kk) {
+          R dr, di;
+          M::lds(DC + kk * qq + idx, dr, di);
+          M::mac(zr, dr, gr[kk][bq]);
+          M::mac(zi, di, gr[kk][bq]);
+        }
+        const R zre = M::norm(zr), zim = M::norm(zi);
+        M::mac(sr[h2], zre, rS[bq]); M::mac(si[h2], zim, rS[bq]);
+        M::mac(nr[h2], zre, rN[bq]); M::mac(ni_[h2], zim, rN[bq]);
+        zc[idx] = Cx<M>{zre, zim};
+      }
+      b = q;
+    }
     for (; b + 1 < q; b += 2) {
       const int i0 = b * q + a, i1 = i0 + q;
       A zr0 = M::zero(), zi0 = M::zero(), zr1 = M::zero(), zi1 = M::zero();
@@ -630,15 +661,17 @@ FdArgs fd_args(const Handle& h, int nleaf, int ncol) {
   return f;
 }
 
+// leaf q with register instantiations of the leaf kernels (K = 3)
+constexpr int kFdRegQ = 14;
+bool fd_down_reg(int q, int K) { return q == kFdRegQ && K == 3; }
+
 size_t fd_up_smem(int q, int K, int ncol) {
   const int qq = q * q;
-  return sizeof(double) * ((size_t)4 * qq + 10 * q + even_up((size_t)ncol * K * qq)) +
+  const size_t gsd = fd_down_reg(q, K) ? 0 : even_up((size_t)ncol * K * qq);
+  return sizeof(double) * ((size_t)4 * qq + 10 * q + gsd) +
          sizeof(cd) * ((size_t)ncol * qq + (size_t)2 * ncol * 4 * q + (size_t)2 * K * qq);
 }
 
-// leaf q with a register-accumulator instantiation of the down kernel (K = 3)
-constexpr int kFdRegQ = 14;
-bool fd_down_reg(int q, int K) { return q == kFdRegQ && K == 3; }
 
 size_t fd_down_smem(int q, int K, int ncol) {
   const int qq = q * q;
@@ -656,10 +689,18 @@ eo_status up_leaf_t(Handle& h, const Sweep& s, const FdArgs& f, cd* h0, cudaStre
   const int ppc = (s.P + nchunk - 1) / nchunk;
   nchunk = (s.P + ppc - 1) / ppc;
   const size_t smem = fd_up_smem(q, s.K, f.ncol);
-  static size_t cap[64] = {};
-  eo_status rc = ensure_smem((const void*)k_fd_up_leaf<M>, smem, cap, 0);
-  if (rc) return rc;
-  k_fd_up_leaf<M><<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, (const typename M::CT*)h.fd_dc, ppc, h0);
+  const typename M::CT* dct = (const typename M::CT*)h.fd_dc;
+  if (fd_down_reg(q, s.K)) {
+    static size_t cap[64] = {};
+    eo_status rc = ensure_smem((const void*)k_fd_up_leaf<M, kFdRegQ>, smem, cap, 0);
+    if (rc) return rc;
+    k_fd_up_leaf<M, kFdRegQ><<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, dct, ppc, h0);
+  } else {
+    static size_t cap[64] = {};
+    eo_status rc = ensure_smem((const void*)k_fd_up_leaf<M, 0>, smem, cap, 0);
+    if (rc) return rc;
+    k_fd_up_leaf<M, 0><<<dim3(ngroups, nchunk), f.ncol * q, smem, st>>>(s, f, dct, ppc, h0);
+  }
   EO_CUDA_TRY(cudaGetLastError());
   return EO_OK;
 }
