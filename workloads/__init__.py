@@ -80,6 +80,32 @@ WAVE_32X32_P16 = Workload(
 
 WORKLOADS = {w.name: w for w in (WAVE_4X4_P12, SW_16X16_P16, WAVE_32X32_P16)}
 
+# Uneven batch (after configuration 3, scaled to fit the batch's operators in a
+# few tens of GB): independent instances, alternately wave (variable c, per-box
+# operators, 8x8 leaves) and shallow water (walls, shared operators, 8x8 or 16x16
+# leaves), p in {8, 12, 16}, 2M+1 in [41, 201] (wave <= 101), 1-8 right-hand sides.
+UNEVEN_BATCH = "uneven_batch_16"
+
+
+def uneven_instances(n: int = 16, seed: int = 3000) -> list:
+    """Seeded instance list of the uneven batch: Workload objects with sizes,
+    pole counts and right-hand-side counts drawn per instance."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        p = int(rng.choice([8, 12, 16]))
+        rhs = int(rng.integers(1, 9))
+        if i % 2 == 0:
+            npol = int(rng.integers(20, 51)) * 2 + 1
+            out.append(dataclasses.replace(WAVE_32X32_P16, name=f"wave_8x8_p{p}_N{npol}_r{rhs}", nlx=8, nly=8, p=p,
+                                           n_poles=npol, n_rhs=rhs, seed=seed + i))
+        else:
+            nl = int(rng.choice([8, 16]))
+            npol = int(rng.integers(20, 101)) * 2 + 1
+            out.append(dataclasses.replace(SW_16X16_P16, name=f"sw_{nl}x{nl}_p{p}_N{npol}_r{rhs}", nlx=nl, nly=nl,
+                                           p=p, n_poles=npol, tau=0.0, n_rhs=rhs, seed=seed + i))
+    return out
+
 # Band Lambda (largest resolved |eigenvalue|) per workload.  4x4/p12 wave: the
 # content of the Gaussian bump above |lambda| = 320 of the discrete operator is
 # below 1e-10 (dense eigendecomposition of that 4000-unknown operator); the
