@@ -210,39 +210,77 @@ static eo_status fit_wide_poles(int N, double delta, Fit& out);
 static const double kS[] = {0.8, 0.9, 1.0, 1.1, 1.2, 1.3, 1.4, 1.5, 1.6};
 static const double kRatio[] = {3.75, 4.0, 4.5, 5.0};
 
+// Finer candidate grids, tried when the default grids give no admissible fit.
+static const double kSFine[] = {0.7, 0.75, 0.8, 0.85, 0.9, 0.95, 1.0, 1.05, 1.1, 1.15, 1.2, 1.25, 1.3,
+                                1.35, 1.4, 1.45, 1.5, 1.55, 1.6, 1.7, 1.8};
+static const double kRatioFine[] = {3.5, 3.75, 4.0, 4.25, 4.5, 4.75, 5.0, 5.5};
+
+static eo_status fit_for_poles_grid(int N, double delta, Fit& out, const double* ss, int ns_, const double* rs,
+                                    int nr);
+
 eo_status fit_for_poles(int N, double delta, Fit& out) {
   if (N < 3 || N % 2 == 0) return fail(EO_ERR_INVALID_ARG, "n_poles must be odd and >= 3");
   // beyond ~100 poles the dense search is slow and the wide construction is as good
   if (N > 101) return fit_wide_poles(N, delta, out);
+  if (fit_for_poles_grid(N, delta, out, kS, (int)(sizeof(kS) / sizeof(kS[0])), kRatio,
+                         (int)(sizeof(kRatio) / sizeof(kRatio[0]))) == EO_OK)
+    return EO_OK;
+  if (fit_for_poles_grid(N, delta, out, kSFine, (int)(sizeof(kSFine) / sizeof(kSFine[0])), kRatioFine,
+                         (int)(sizeof(kRatioFine) / sizeof(kRatioFine[0]))) == EO_OK)
+    return EO_OK;
+  return fit_wide_poles(N, delta, out);
+}
+
+static void par_for(int64_t n, const std::function<void(int64_t, int64_t)>& fn);
+
+// Widest accepted band over the candidate line spacings ss and sigma/s ratios rs
+// (candidates searched in parallel host threads, then the widest kept; ties go to
+// the first candidate in grid order, so the result does not depend on threads).
+static eo_status fit_for_poles_grid(int N, double delta, Fit& out, const double* ss, int ns_, const double* rs,
+                                    int nr) {
   const int M = (N - 1) / 2;
-  double bestX = 0;
-  std::vector<cplx> al, b;
-  for (double s : kS)
-    for (double ratio : kRatio) {
-      const double sigma = ratio * s;
-      // coarse scan downward from the pole span, then refine upward
-      double X = s * M;
-      double found = 0, r = 0;
-      for (; X > bestX && X > 0.5; X -= std::max(0.5, 0.05 * X)) {
-        if (residues(N, sigma, s, X, al, b) && accept(X, delta, al, b, &r)) { found = X; break; }
-      }
-      if (found == 0) continue;
-      double step = std::max(0.5, 0.05 * found) / 2;
-      for (int it = 0; it < 4; ++it, step /= 2) {
-        const double Xt = found + step;
-        double rt;
-        if (residues(N, sigma, s, Xt, al, b) && accept(Xt, delta, al, b, &rt)) found = Xt;
-      }
-      if (found > bestX) {
-        residues(N, sigma, s, found, al, b);
-        accept(found, delta, al, b, &r);
-        store(al, b, r, found, sigma, s, out);
-        bestX = found;
-      }
+  const int nc = ns_ * nr;
+  std::vector<double> foundX(nc, 0.0);
+  auto search = [&](int ci) {
+    const double s = ss[ci / nr], sigma = rs[ci % nr] * s;
+    std::vector<cplx> al, b;
+    double X = s * M, found = 0, r = 0;
+    for (; X > 0.5; X -= std::max(0.5, 0.05 * X))
+      if (residues(N, sigma, s, X, al, b) && accept(X, delta, al, b, &r)) { found = X; break; }
+    if (found == 0) return;
+    double step = std::max(0.5, 0.05 * found) / 2;
+    for (int it = 0; it < 4; ++it, step /= 2) {
+      const double Xt = found + step;
+      double rt;
+      if (residues(N, sigma, s, Xt, al, b) && accept(Xt, delta, al, b, &rt)) found = Xt;
     }
-  if (bestX == 0) return fit_wide_poles(N, delta, out);
+    foundX[ci] = found;
+  };
+  {
+    std::vector<std::thread> th;
+    std::atomic<int> next(0);
+    const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+    for (unsigned t = 0; t < nt; ++t)
+      th.emplace_back([&] {
+        for (int ci = next++; ci < nc; ci = next++) search(ci);
+      });
+    for (auto& x : th) x.join();
+  }
+  int best = -1;
+  for (int ci = 0; ci < nc; ++ci)
+    if (foundX[ci] > 0 && (best < 0 || foundX[ci] > foundX[best])) best = ci;
+  if (best < 0) return EO_ERR_FIT;
+  {
+    const double s = ss[best / nr], sigma = rs[best % nr] * s, X = foundX[best];
+    std::vector<cplx> al, b;
+    double r = 0;
+    residues(N, sigma, s, X, al, b);
+    accept(X, delta, al, b, &r);
+    store(al, b, r, X, sigma, s, out);
+  }
   return EO_OK;
 }
+
 
 // ---------------------------------------------------------------- wide bands
 // For a band X far wider than the pole spacing the dense search above is too

@@ -53,7 +53,7 @@ def test_bad_arguments_are_rejected(capi):
     assert L.eo_destroy(None) == 0
 
 
-@pytest.mark.parametrize("n_poles,min_X", [(21, 3.0), (61, 12.0)])
+@pytest.mark.parametrize("n_poles,min_X", [(21, 3.0), (57, 10.0), (61, 12.0)])
 def test_library_fit_meets_contract(capi, n_poles, min_X):
     # the host fitter's output checked by the oracle's brute-force evaluation of
     # eqs. RM_prop1 / RM_prop2 (independent code)
