@@ -228,7 +228,26 @@ eo_status fit_for_poles(int N, double delta, Fit& out) {
   if (fit_for_poles_grid(N, delta, out, kSFine, (int)(sizeof(kSFine) / sizeof(kSFine[0])), kRatioFine,
                          (int)(sizeof(kRatioFine) / sizeof(kRatioFine[0]))) == EO_OK)
     return EO_OK;
-  return fit_wide_poles(N, delta, out);
+  if (fit_wide_poles(N, delta, out) == EO_OK) return EO_OK;
+  // Last resort: the approximant with N - 2 poles plus one more conjugate pole
+  // pair on the same line with zero residues.  R is unchanged, so eqs. RM_prop1
+  // and RM_prop2 hold with the band of the smaller fit.
+  if (N <= 3) return fail(EO_ERR_FIT, "no admissible rational approximant for this pole count");
+  Fit f;
+  if (fit_for_poles(N - 2, delta, f) != EO_OK) return fail(EO_ERR_FIT, "no admissible rational approximant for this pole count");
+  const int Mo = (N - 3) / 2;
+  out = f;
+  out.E = 0;
+  out.are.insert(out.are.begin(), f.sigma);
+  out.aim.insert(out.aim.begin(), -f.s * (Mo + 1));
+  out.are.push_back(f.sigma);
+  out.aim.push_back(f.s * (Mo + 1));
+  out.bre.insert(out.bre.begin(), 0.0);
+  out.bim.insert(out.bim.begin(), 0.0);
+  out.bre.push_back(0.0);
+  out.bim.push_back(0.0);
+  set_error("");
+  return EO_OK;
 }
 
 static void par_for(int64_t n, const std::function<void(int64_t, int64_t)>& fn);
