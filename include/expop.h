@@ -100,6 +100,12 @@ typedef struct {
                           root solve on this handle's operators and keeps the
                           fastest (synchronises the stream once; skipped inside a
                           stream capture); 0: fixed heuristic shapes             */
+  int sw_consistent;   /* EO_SW_WALLS with f != 0: 1 keeps the (tau f / alpha) Curl(G h)
+                          term in the elliptic rows (G the recovered node gradient), the
+                          exact elimination of (U, V) on this discretisation, so the
+                          per-pole solves are resolvents of one discrete operator;
+                          0: the elimination as the paper writes it (curl grad = 0).
+                          1 uses dense leaf operators (no fast diagonalisation)     */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.

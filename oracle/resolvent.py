@@ -26,6 +26,11 @@ sw    linearised rotating shallow water u_t = f v - g h_x, v_t = -f u - g h_y,
         alpha h_x + tau f h_y = -(alpha F1 + tau f F2)/(tau g)   (x = 0, 1)
         alpha h_y - tau f h_x = (tau f F1 - alpha F2)/(tau g)    (y = 0, 1).
 
+With consistent=True the interior rows carry the extra term (tau f / alpha) Curl(G h),
+G the recovered node gradient of the post-map: the exact elimination of (U, V) for this
+discretisation, where Curl(G h) does not vanish next to leaf edges.  The per-pole solves
+are then resolvents of one discrete operator.
+
 Every solve is a sparse direct solve (scipy splu) of the full global system.
 """
 from __future__ import annotations
@@ -41,7 +46,7 @@ class Problem:
     """A discretised problem: grid, kind and coefficients."""
 
     def __init__(self, grid: sem.Grid, kind: str, tau: float, c2=None,
-                 f: float = 0.0, g: float = 1.0, H: float = 1.0):
+                 f: float = 0.0, g: float = 1.0, H: float = 1.0, consistent: bool = False):
         if kind not in ("wave", "sw"):
             raise ValueError(kind)
         self.grid, self.kind, self.tau = grid, kind, float(tau)
@@ -58,6 +63,11 @@ class Problem:
         self.Flux = sem.flux_continuity_rows(grid, self.a)
         if kind == "sw":
             self.Gx, self.Gy = sem.wall_gradient_rows(grid)
+        # consistent elimination (shallow water): keep the (tau f / alpha) Curl(G h)
+        # term that the continuum drops (curl grad = 0) but this discretisation does not
+        self.consistent = bool(consistent) and kind == "sw"
+        if self.consistent:
+            self.CG = sem.curl_of_gradient(grid)
         self.P_int = sp.diags((self.cls == 0).astype(float))
         self.P_ifc = sp.diags((self.cls == 1).astype(float))
         self.P_bnd = sp.diags((self.cls == 2).astype(float))
@@ -82,6 +92,8 @@ class Problem:
             yw = sp.diags(((self.side == 0) | (self.side == 2)).astype(float))
             tf = self.tau * self.f
             B = B + xw @ (alpha * self.Gx + tf * self.Gy) + yw @ (alpha * self.Gy - tf * self.Gx)
+            if self.consistent:
+                B = B + (tf / alpha) * self.CG
         return sp.csc_matrix(B)
 
     def rhs(self, alpha: complex, state: np.ndarray) -> np.ndarray:

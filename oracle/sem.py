@@ -287,6 +287,70 @@ def gradient(g: Grid, u: np.ndarray):
     return ux, uy
 
 
+def gradient_matrices(g: Grid):
+    """Sparse (Gx, Gy) with Gx @ u, Gy @ u equal to gradient(g, u): the same rules
+    written as matrix rows (interior nodes: the leaf's own row / column
+    differentiation; edge nodes: mean of the one-sided normal derivatives of the
+    touching leaves, tangential derivative of the edge interpolant)."""
+    p, n = g.p, g.n_nodes
+    inner = np.arange(1, p - 1)
+    rx, cx, vx, ry, cy, vy = [], [], [], [], [], []
+    cnt_x = np.zeros(n)
+    cnt_y = np.zeros(n)
+    for b in range(g.nly):
+        for a_ in range(g.nlx):
+            ids = g.leaf_ids(a_, b)
+            for j in inner:                                  # rows j: d/dx of interior and W/E nodes
+                for k in range(p):
+                    r = ids[j, k]
+                    if k in (0, p - 1):
+                        cnt_x[r] += 1
+                    rx.append(np.full(p, r)); cx.append(ids[j, :]); vx.append(g.Dx[k, :])
+            for k in inner:                                  # columns k: d/dy of interior and S/N nodes
+                for j in range(p):
+                    r = ids[j, k]
+                    if j in (0, p - 1):
+                        cnt_y[r] += 1
+                    ry.append(np.full(p, r)); cy.append(ids[:, k]); vy.append(g.Dy[j, :])
+    Gx = _coo(rx, cx, vx, n).tolil()
+    Gy = _coo(ry, cy, vy, n).tolil()
+    # interior rows were added once per leaf; edge-node normal rows once per touching leaf: mean
+    sx = np.where(cnt_x > 0, 1.0 / np.maximum(cnt_x, 1), 1.0)
+    sy = np.where(cnt_y > 0, 1.0 / np.maximum(cnt_y, 1), 1.0)
+    Gx = sp.diags(sx) @ Gx.tocsr()
+    Gy = sp.diags(sy) @ Gy.tocsr()
+    Gx, Gy = Gx.tolil(), Gy.tolil()
+    # tangential components on edges: rows replaced by the edge-interpolant derivative
+    for e in range(g.nly + 1):
+        for a_ in range(g.nlx):
+            ids = g.hseg_ids(e, a_)
+            for t, r in enumerate(ids):
+                Gx.rows[r] = []
+                Gx.data[r] = []
+                for m, c in enumerate(ids):
+                    Gx[r, c] = g.Ex[t, m]
+    for b in range(g.nly):
+        for e in range(g.nlx + 1):
+            ids = g.vseg_ids(b, e)
+            for t, r in enumerate(ids):
+                Gy.rows[r] = []
+                Gy.data[r] = []
+                for m, c in enumerate(ids):
+                    Gy[r, c] = g.Ey[t, m]
+    return Gx.tocsr(), Gy.tocsr()
+
+
+def curl_of_gradient(g: Grid) -> sp.csr_matrix:
+    """Interior rows of Curl(G h) = d/dx (G_y h) - d/dy (G_x h), with the interior
+    derivatives of interior_div_curl applied to the recovered gradient G (zero
+    rows elsewhere).  Zero in the continuum; on this discretisation nonzero at
+    interior nodes next to leaf edges (tangential edge derivatives)."""
+    Gx, Gy = gradient_matrices(g)
+    cls, _ = g.classify()
+    P = sp.diags((cls == 0).astype(float))
+    return (P @ (Gx @ Gy - Gy @ Gx)).tocsr()
+
+
 def interior_div_curl(g: Grid, F1: np.ndarray, F2: np.ndarray):
     """(dF1/dx + dF2/dy, dF2/dx - dF1/dy) at interior nodes (zero elsewhere),
     by leaf spectral differentiation along rows / columns."""

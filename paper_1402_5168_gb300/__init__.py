@@ -85,13 +85,13 @@ class Operator:
     def __init__(self, grid: Grid, kind: int, band: float, n_poles: int = 0, tau: float = 0.0,
                  c2=None, f=0.0, g=1.0, H=1.0, delta=1e-10, shared_ops=False, max_rhs=1,
                  mem_budget_gb=0.0, precision="fp64", fp64_top_levels=0, use_graphs=True, dense_leaves=False,
-                 autotune=True, stream=None):
+                 autotune=True, sw_consistent=False, stream=None):
         L = _capi.lib()
         prec = {"fp64": 0, "fp32": 1, "df32": 2}[precision]
         o = Opts(n_poles=n_poles, band=band, tau=tau, delta=delta, sw_f=f, sw_g=g, sw_H=H, precision=prec,
                  shared_ops=int(shared_ops), max_rhs=max_rhs, mem_budget_gb=mem_budget_gb,
                  fp64_top_levels=fp64_top_levels, use_graphs=int(use_graphs), dense_leaves=int(dense_leaves),
-                 autotune=int(autotune))
+                 autotune=int(autotune), sw_consistent=int(sw_consistent))
         coeff = None
         if c2 is not None:
             self._c2 = np.ascontiguousarray(c2, dtype=np.float64)

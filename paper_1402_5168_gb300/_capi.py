@@ -24,7 +24,7 @@ class Opts(C.Structure):
                 ("sw_f", C.c_double), ("sw_g", C.c_double), ("sw_H", C.c_double), ("precision", C.c_int),
                 ("shared_ops", C.c_int), ("max_rhs", C.c_int), ("mem_budget_gb", C.c_double),
                 ("fp64_top_levels", C.c_int), ("use_graphs", C.c_int), ("dense_leaves", C.c_int),
-                ("autotune", C.c_int)]
+                ("autotune", C.c_int), ("sw_consistent", C.c_int)]
 
 
 _lib = None

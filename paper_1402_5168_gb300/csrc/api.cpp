@@ -133,7 +133,10 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   }
   h.R = std::max(1, o.max_rhs);
   h.shared = o.shared_ops ? 1 : 0;
-  h.fd = (h.shared && !o.dense_leaves) ? 1 : 0;   // shared operators: constant coefficient
+  // fast-diagonal leaves: shared operators (constant coefficient) and a leaf coupling
+  // without the consistent curl term
+  const bool curl = h.kind == EO_SW_WALLS && o.sw_consistent && o.sw_f != 0.0;
+  h.fd = (h.shared && !o.dense_leaves && !curl) ? 1 : 0;
   h.fd_pair = (h.fd && o.precision == EO_PREC_DF32) ? 1 : 0;
   const double tau = h.tau;
   // ---- per-pole tables

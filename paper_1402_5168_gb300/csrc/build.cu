@@ -108,11 +108,36 @@ __global__ void leaf_real_ops(int nlx, int nly, int p, long long n_int, long lon
   }
 }
 
+// Leaf coupling of Curl(G h) to the leaf's own edge values (shallow water,
+// consistent elimination), column-major ni x nb like Aib.  At interior node (k, j):
+//   Curl(G h) = Dy[j][0] (dX h_S)(k) + Dy[j][p-1] (dX h_N)(k)
+//             - Dx[k][0] (dY h_W)(j) - Dx[k][p-1] (dY h_E)(j),
+// dX = (Dx)_{interior} - Ex and dY = (Dy)_{interior} - Ey: the difference between the
+// leaf's own differentiation along an edge (corner columns dropped) and the edge
+// interpolant's derivative used by the recovered gradient.  One block per leaf.
+__global__ void leaf_curl_ops(int p, const double* __restrict__ Dx, const double* __restrict__ Dy,
+                              const double* __restrict__ Ex, const double* __restrict__ Ey, double* Cib) {
+  const int q = p - 2, ni = q * q;
+  double* C = Cib + (size_t)blockIdx.x * ni * 4 * q;
+  for (int r = threadIdx.x; r < ni; r += blockDim.x) {
+    const int k = r % q + 1, j = r / q + 1;
+    for (int m = 1; m <= q; ++m) {
+      const double dX = Dx[k * p + m] - Ex[(k - 1) * q + (m - 1)];
+      const double dY = Dy[j * p + m] - Ey[(j - 1) * q + (m - 1)];
+      C[r + (size_t)(m - 1) * ni] = Dy[j * p + 0] * dX;                   // S node (m, 0)
+      C[r + (size_t)(2 * q + m - 1) * ni] = Dy[j * p + (p - 1)] * dX;     // N node (m, p-1)
+      C[r + (size_t)(3 * q + m - 1) * ni] = -Dx[k * p + 0] * dY;          // W node (0, m)
+      C[r + (size_t)(q + m - 1) * ni] = -Dx[k * p + (p - 1)] * dY;        // E node (p-1, m)
+    }
+  }
+}
+
 // Batch entry i = (pole gi, leaf) with leaf = i % nleaf, gi = i / nleaf:
 // A = Aii0 - kappa2[gi] I; XY = [I | -Aib]; T = Fbb (complex).
+// With Cib (consistent shallow water): Y's right-hand side is -(Aib + beta[gi] Cib).
 __global__ void leaf_assemble(int nbatch, int nleaf, int ni, int nb, const cd* __restrict__ kappa2,
-                              const double* Aii0, const double* Aib, const double* Fbb, cd* A, cd* XY,
-                              cd* T) {
+                              const double* Aii0, const double* Aib, const double* Fbb, const double* Cib,
+                              const cd* __restrict__ beta, cd* A, cd* XY, cd* T) {
   const size_t nA = (size_t)ni * ni, nXY = (size_t)ni * (ni + nb), nT = (size_t)nb * nb;
   const size_t tot = (size_t)nbatch * (nA + nXY + nT);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot;
@@ -128,8 +153,18 @@ __global__ void leaf_assemble(int nbatch, int nleaf, int ni, int nb, const cd* _
     } else if (e < nA + nXY) {
       e -= nA;
       const int i = e % ni, j = e / ni;
-      const double v = (j < ni) ? (i == j ? 1.0 : 0.0) : -Aib[leaf * (size_t)ni * nb + (e - (size_t)ni * ni)];
-      XY[bi * nXY + e] = make_double2(v, 0.0);
+      if (j < ni) {
+        XY[bi * nXY + e] = make_double2(i == j ? 1.0 : 0.0, 0.0);
+      } else {
+        const size_t o = leaf * (size_t)ni * nb + (e - (size_t)ni * ni);
+        double re = -Aib[o], im = 0.0;
+        if (Cib) {
+          const cd bt = beta[bi / nleaf];
+          re -= bt.x * Cib[o];
+          im -= bt.y * Cib[o];
+        }
+        XY[bi * nXY + e] = make_double2(re, im);
+      }
     } else {
       e -= nA + nXY;
       T[bi * nT + e] = make_double2(Fbb[leaf * nT + e], 0.0);
@@ -328,6 +363,15 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
                                                         acoef, Aii0, Aib, Fbi, Fbb);
   EO_CUDA_TRY(cudaGetLastError());
   if (h.fd && (rc = fd_setup(h, Aii0, Aib, Fbi, st))) return rc;
+  // consistent shallow-water elimination: the leaf coupling of Curl(G h)
+  double* Cib = nullptr;
+  cd* dbeta = nullptr;
+  if (h.kind == EO_SW_WALLS && h.opts.sw_consistent && h.opts.sw_f != 0.0) {
+    if ((rc = talloc((void**)&Cib, sizeof(double) * nlo * ni * nb))) return rc;
+    if ((rc = talloc((void**)&dbeta, sizeof(cd) * std::min(P, 64)))) return rc;
+    leaf_curl_ops<<<nlo, 256, 0, st>>>(p, dDx, dDy, dEx, dEy, Cib);
+    EO_CUDA_TRY(cudaGetLastError());
+  }
   cd* Fbi_c;
   if ((rc = talloc((void**)&Fbi_c, sizeof(cd) * nlo * nb * ni))) return rc;
   real_to_complex<<<1024, 256, 0, st>>>((size_t)nlo * nb * ni, Fbi, Fbi_c);
@@ -384,7 +428,15 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
     cd* Hp = h.H + (size_t)p0 * h.h_pstride;
     const long long xyb = (long long)ni * (ni + nb);
     const long long hb = (long long)nb * ni;
-    leaf_assemble<<<2048, 256, 0, st>>>(nbl, nlo, ni, nb, kap, Aii0, Aib, Fbb, Aw, XYp, T0);
+    if (Cib) {
+      std::vector<cd> hb(g);
+      for (int gi = 0; gi < g; ++gi) {
+        const std::complex<double> bt = (h.tau * h.opts.sw_f) / h.alpha[p0 + gi];
+        hb[gi] = make_double2(bt.real(), bt.imag());
+      }
+      EO_CUDA_TRY(cudaMemcpyAsync(dbeta, hb.data(), sizeof(cd) * g, cudaMemcpyHostToDevice, st));
+    }
+    leaf_assemble<<<2048, 256, 0, st>>>(nbl, nlo, ni, nb, kap, Aii0, Aib, Fbb, Cib, dbeta, Aw, XYp, T0);
     EO_CUDA_TRY(cudaGetLastError());
     {
       std::vector<cd*> pa(nbl), pb(nbl);

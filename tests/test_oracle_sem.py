@@ -1,5 +1,6 @@
 """Pins of oracle.sem (Section 2.2): spectral differentiation, numbering and
 quadrature against closed forms."""
+import pytest
 import numpy as np
 
 from oracle import sem
@@ -80,3 +81,19 @@ def test_quadrature_weights():
     f = g.x * (1 - g.x) * (2 * g.x - 1) ** 2 * g.y * (1 - g.y)
     assert abs(w @ f - 1.0 / 180.0) < 1e-15
     assert abs(w.sum() - 1.0) < 0.02
+
+
+@pytest.mark.parametrize("nl,p", [(1, 6), (2, 7), (2, 8)])
+def test_gradient_matrices_equal_the_procedural_gradient(nl, p):
+    g = sem.Grid(nl, nl, p)
+    Gx, Gy = sem.gradient_matrices(g)
+    u = np.random.default_rng(nl * 10 + p).standard_normal(g.n_nodes)
+    hx, hy = sem.gradient(g, u)
+    assert np.abs(Gx @ u - hx).max() <= 1e-12 * np.abs(hx).max()
+    assert np.abs(Gy @ u - hy).max() <= 1e-12 * np.abs(hy).max()
+    # Curl(G h) equals interior_div_curl of the recovered gradient and vanishes on
+    # polynomials of the leaf degree that the edge interpolant reproduces
+    c = sem.interior_div_curl(g, hx, hy)[1]
+    assert np.abs(sem.curl_of_gradient(g) @ u - c).max() <= 1e-12 * np.abs(c).max()
+    poly = g.x ** 2 * g.y + 0.5 * g.y ** 3 - g.x
+    assert np.abs(sem.curl_of_gradient(g) @ poly).max() <= 1e-9

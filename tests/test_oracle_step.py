@@ -209,15 +209,16 @@ def _resolvent_matrix(prob, alpha):
     return M
 
 
-@pytest.mark.parametrize("f,consistent", [(0.0, True), (10.0, False)])
-def test_sw_resolvent_identity_holds_only_without_rotation(f, consistent):
-    """A documented property of the paper's elimination on this discretisation.
-    Without rotation the per-pole solves are resolvents of one discrete operator:
-    R(a) - R(b) = (a - b) R(a) R(b).  With rotation the elimination drops
-    Curl(G h), which the recovered edge gradient does not make zero, so the
-    identity fails at O(1)."""
-    g = sem.Grid(1, 1, 6)
-    prob = Problem(g, "sw", 1.0, f=f, g=1.0, H=1.0)
+@pytest.mark.parametrize("f,elim,consistent", [(0.0, False, True), (10.0, False, False), (10.0, True, True),
+                                               (3.0, True, True)])
+def test_sw_resolvent_identity(f, elim, consistent):
+    """The per-pole solves are resolvents of one discrete operator,
+    R(a) - R(b) = (a - b) R(a) R(b), without rotation, and with rotation only
+    when the elimination keeps (tau f / alpha) Curl(G h) (consistent=True).  The
+    paper's elimination as written drops that term, which the recovered edge
+    gradient does not make zero, so with rotation the identity fails at O(1)."""
+    g = sem.Grid(1, 1, 6) if not elim else sem.Grid(2, 2, 6)
+    prob = Problem(g, "sw", 1.0, f=f, g=1.0, H=1.0, consistent=elim)
     a, b = 0.7 + 3.0j, 1.3 - 5.0j
     Ra, Rb = _resolvent_matrix(prob, a), _resolvent_matrix(prob, b)
     defect = np.linalg.norm(Ra - Rb - (a - b) * Ra @ Rb) / np.linalg.norm(Ra - Rb)
