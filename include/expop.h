@@ -92,14 +92,15 @@ typedef struct {
                           the first such call must not itself be inside a capture */
   int dense_leaves;    /* 0: with shared_ops (constant coefficient), leaf solves use
                           the leaf's separable eigenbasis (fast diagonalisation, see
-                          eo_leaf_basis; FP64 in every precision mode); 1: the dense
-                          leaf solution operators of Section 2.3 (always used for
-                          per-box operators and by eo_apply_adjoint)              */
+                          eo_leaf_basis), in FP32-pair arithmetic with EO_PREC_DF32
+                          and FP64 otherwise; 1: the dense leaf solution operators
+                          of Section 2.3 (always used for per-box operators and by
+                          eo_apply_adjoint)                                      */
   int autotune;        /* 1: the first eo_apply (and the first with a new n_rhs) times
-                          the candidate launch shapes of every merge level and the
-                          root solve on this handle's operators and keeps the
-                          fastest (synchronises the stream once; skipped inside a
-                          stream capture); 0: fixed heuristic shapes             */
+                          the candidate launch shapes of every merge level, the root
+                          solve and the fast-diagonal leaf kernels on this handle's
+                          operators and keeps the fastest (synchronises the stream
+                          once; skipped inside a stream capture); 0: fixed shapes  */
   int sw_consistent;   /* EO_SW_WALLS with f != 0: 1 keeps the (tau f / alpha) Curl(G h)
                           term in the elliptic rows (G the recovered node gradient), the
                           exact elimination of (U, V) on this discretisation, so the
