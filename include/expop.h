@@ -67,6 +67,14 @@ typedef enum {
                        pipe with exact product splitting and compensated sums     */
 } eo_precision;
 
+typedef enum {
+  EO_FIT_LINE = 0,  /* poles on one conjugate-closed line, residues by least squares,
+                       eqs. RM_prop1 and RM_prop2 both enforced (see eo_fit)        */
+  EO_FIT_GAUSS = 1  /* the paper's construction (Sections 3.1-3.2): shifted Gaussians
+                       replaced by the Table 1 rational, two pole lines; meets
+                       eq. RM_prop1 only (see eo_fit_gauss)                        */
+} eo_fitter;
+
 typedef struct eo_grid_s *eo_grid_t;
 typedef struct eo_handle_s *eo_handle_t;
 typedef struct eo_batch_s *eo_batch_t;
@@ -107,6 +115,10 @@ typedef struct {
                           per-pole solves are resolvents of one discrete operator;
                           0: the elimination as the paper writes it (curl grad = 0).
                           1 uses dense leaf operators (no fast diagonalisation)     */
+  int fitter;          /* eo_fitter (0: EO_FIT_LINE).  EO_FIT_GAUSS needs n_poles == 0
+                          and tau > 0                                             */
+  double gauss_h;      /* EO_FIT_GAUSS: Gaussian spacing h in x = theta / (2 pi)
+                          (0: 0.18); smaller h, more poles, smaller aliasing error  */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.
@@ -147,9 +159,28 @@ eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double *coeff,
 eo_status eo_fit(int n_poles, double X, double delta, int cap, double *alpha, double *b, int *n,
                  double *X_out);
 
-/* The approximant in use: n = 2M+1 poles alpha (2n doubles, interleaved),
- * residues b (2n doubles), the step tau and the band X = tau*Lambda it covers.
- * Pass alpha = b = NULL to query n only.  Poles are ordered m = -M..M. */
+/* Host-only: the paper's approximant (Sections 3.1-3.2) of e^z on z = i theta,
+ * |theta| <= X.  With x = theta / (2 pi), e^{2 pi i x} = sum_{m=-M..M} c_m psi_h(x + m h),
+ * psi_h(x) = (4 pi)^{-1/2} exp(-x^2 / (4 h^2)), c_m = exp(4 pi^2 h^2) exp(-2 pi i m h)
+ * (Section 3.1), and every psi_h(x + m h) = psi_1(x/h + m) is replaced by the Table 1
+ * rational psi_1(y) ~= Re sum_{j=-11..11} a_j / (i y + mu + i j) (Section 3.2; its even
+ * part, which makes the result exactly conjugate-closed).  M is the smallest that
+ * meets delta (0: 1e-10) on the band; h in (0, 0.5) (0: 0.18).  Output: two lines of
+ * 2(M+11)+1 poles each, alpha = -2 pi h (mu + i n) (right half-plane) then its mirror
+ * image 2 pi h (mu - i n), each line in order of increasing Im.  Unlike eo_fit, |R(iy)|
+ * is NOT bounded by 1: it reaches about 1.44 near |y| = 2 pi M h, so repeated steps
+ * amplify any content there unless filtered (EO_FN_FILTER).
+ *   cap: capacity of alpha and b (poles, 2*cap doubles each); n, M: pole count and M.
+ * Errors: EO_ERR_INVALID_ARG (cap too small: *n is still set), EO_ERR_FIT. */
+eo_status eo_fit_gauss(double X, double h, double delta, int cap, double *alpha, double *b, int *n,
+                       int *M);
+
+/* The approximant in use: n poles alpha (2n doubles, interleaved), residues b
+ * (2n doubles), the step tau and the band X = tau*Lambda it covers.  Pass
+ * alpha = b = NULL to query n only.  Poles come as conjugate-closed lines, each
+ * in order of increasing Im: one line m = -M..M (EO_FIT_LINE, n = 2M+1) or the
+ * two lines of eo_fit_gauss (EO_FIT_GAUSS).  Operators exist for the poles with
+ * Im >= 0 (eq. "conjugate, matrix inverses", Section 3.3). */
 eo_status eo_get_poles(eo_handle_t h, double *alpha, double *b, int *n, double *tau,
                        double *X);
 
@@ -215,19 +246,27 @@ eo_status eo_apply_resolvent_noalloc(eo_handle_t h, int j, const double *u_dev, 
 
 /* Other functions of tau L on the SAME poles (dense output and phi-functions; the
  * solves are shared, only the pole-sum weights change).  Host-only fit of residues b
- * (2M+1 complex, interleaved, the eo_get_poles order, b_{-m} = conj(b_m)) such that
+ * (n complex, interleaved, the eo_get_poles order, conjugate-symmetric) such that
  * sum_m b_m / (z - alpha_m) approximates, on the handle's band z = i x, |x| <= X:
- *   kind EO_FN_EXP (0):  exp(c z), 0 < c <= 1   (exp(c tau L): output inside the step)
- *   kind EO_FN_PHI1 (1): phi1(z) = (exp(z) - 1) / z.
- * Narrow fits solve for every residue by least squares on the band; wide fits take
- * the central residues from the trapezoidal rule of the function's Cauchy integral
- * along the pole line and fit the outer pairs.  err (may be NULL) receives
- * max |f(ix) - R(ix)| on the band.  Errors: EO_ERR_INVALID_ARG, EO_ERR_FIT. */
+ *   kind EO_FN_EXP (0):    exp(c z), 0 < c <= 1   (exp(c tau L): output inside the step)
+ *   kind EO_FN_PHI1 (1):   phi1(z) = (exp(z) - 1) / z
+ *   kind EO_FN_FILTER (2): EO_FIT_GAUSS only: the rational partition of unity
+ *                          chi(x) = sum_{|m|<=M0} psi_h(x + m h), x = z / (2 pi i),
+ *                          M0 = floor(c M), 0 < c <= 1 (the filter S of Section 3.3,
+ *                          unreduced: its poles are the handle's own).
+ * Line fits: narrow bands solve for every residue by least squares on the band; wide
+ * bands take the central residues from the trapezoidal rule of the function's Cauchy
+ * integral along the pole line and fit the outer pairs.  Gaussian-sum fits: the
+ * Gaussian coefficients of the function (exp: closed form; phi1: quadrature over c;
+ * filter: 1 for |m| <= M0) through the Table 1 rational.  err (may be NULL) receives
+ * max |f(ix) - R(ix)| on the band.  Errors: EO_ERR_INVALID_ARG, EO_ERR_FIT,
+ * EO_ERR_UNSUPPORTED (the filter on a line fit). */
 #define EO_FN_EXP 0
 #define EO_FN_PHI1 1
+#define EO_FN_FILTER 2
 eo_status eo_fit_function(eo_handle_t h, int kind, double c, double *b, double *err);
 
-/* out_dev[k] = f_k(tau L) u for n_out residue sets b_sets[k] (each 2M+1 complex
+/* out_dev[k] = f_k(tau L) u for n_out residue sets b_sets[k] (each n complex
  * interleaved, as from eo_fit_function or eo_get_poles) on the handle's poles: one
  * upward sweep and merge pass for all, then the leaf interiors, pole sums and
  * post-map once per set.  u_dev: DEVICE [fields][n_nodes] (one state);

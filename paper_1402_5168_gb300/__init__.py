@@ -16,7 +16,7 @@ import numpy as np
 from . import _capi
 from ._capi import SW_WALLS, WAVE_DIRICHLET, ExpopError, Opts, check
 
-__all__ = ["Grid", "Operator", "Batch", "fit", "leaf_basis", "WAVE_DIRICHLET", "SW_WALLS", "ExpopError"]
+__all__ = ["Grid", "Operator", "Batch", "fit", "fit_gauss", "leaf_basis", "WAVE_DIRICHLET", "SW_WALLS", "ExpopError"]
 
 
 def fit(n_poles: int = 0, X: float = 0.0, delta: float = 1e-10, cap: int = 20001):
@@ -29,6 +29,22 @@ def fit(n_poles: int = 0, X: float = 0.0, delta: float = 1e-10, cap: int = 20001
                              C.byref(Xo)))
     k = n.value
     return a[0:2 * k:2] + 1j * a[1:2 * k:2], b[0:2 * k:2] + 1j * b[1:2 * k:2], Xo.value
+
+
+def fit_gauss(X: float, h: float = 0.18, delta: float = 1e-10):
+    """The paper's Gaussian-sum approximant of e^{ix} on [-X, X] (two pole lines);
+    returns (alpha, b, M).  Host only."""
+    n, M = C.c_int(), C.c_int()
+    dp = C.POINTER(C.c_double)
+    L = _capi.lib()
+    L.eo_fit_gauss(X, h, delta, 0, None, None, C.byref(n), C.byref(M))   # size query
+    if n.value <= 0:
+        check(L.eo_fit_gauss(X, h, delta, 0, None, None, C.byref(n), C.byref(M)))
+    a = np.zeros(2 * n.value)
+    b = np.zeros(2 * n.value)
+    check(L.eo_fit_gauss(X, h, delta, n.value, a.ctypes.data_as(dp), b.ctypes.data_as(dp), C.byref(n),
+                         C.byref(M)))
+    return a[0::2] + 1j * a[1::2], b[0::2] + 1j * b[1::2], M.value
 
 
 def leaf_basis(p: int, length: float = 2.0, a: float = 1.0):
@@ -85,13 +101,15 @@ class Operator:
     def __init__(self, grid: Grid, kind: int, band: float, n_poles: int = 0, tau: float = 0.0,
                  c2=None, f=0.0, g=1.0, H=1.0, delta=1e-10, shared_ops=False, max_rhs=1,
                  mem_budget_gb=0.0, precision="fp64", fp64_top_levels=0, use_graphs=True, dense_leaves=False,
-                 autotune=True, sw_consistent=False, stream=None):
+                 autotune=True, sw_consistent=False, fitter="line", gauss_h=0.0, stream=None):
         L = _capi.lib()
         prec = {"fp64": 0, "fp32": 1, "df32": 2}[precision]
+        fit_kind = {"line": 0, "gauss": 1}[fitter]
         o = Opts(n_poles=n_poles, band=band, tau=tau, delta=delta, sw_f=f, sw_g=g, sw_H=H, precision=prec,
                  shared_ops=int(shared_ops), max_rhs=max_rhs, mem_budget_gb=mem_budget_gb,
                  fp64_top_levels=fp64_top_levels, use_graphs=int(use_graphs), dense_leaves=int(dense_leaves),
-                 autotune=int(autotune), sw_consistent=int(sw_consistent))
+                 autotune=int(autotune), sw_consistent=int(sw_consistent), fitter=fit_kind,
+                 gauss_h=gauss_h)
         coeff = None
         if c2 is not None:
             self._c2 = np.ascontiguousarray(c2, dtype=np.float64)
@@ -153,12 +171,14 @@ class Operator:
         return x
 
     def fit_function(self, kind: str = "exp", c: float = 1.0):
-        """Residues (numpy complex, eo_get_poles order) of exp(c z) ("exp") or
-        phi1(z) ("phi1") on this operator's poles, and the band error."""
+        """Residues (numpy complex, eo_get_poles order) of exp(c z) ("exp"), phi1(z)
+        ("phi1") or, for fitter="gauss", the partition-of-unity filter keeping a
+        fraction c of the Gaussians ("filter") on this operator's poles, and the
+        band error."""
         n = self.alpha.size
         b = np.zeros(2 * n)
         err = C.c_double()
-        check(_capi.lib().eo_fit_function(self._h, {"exp": 0, "phi1": 1}[kind], c,
+        check(_capi.lib().eo_fit_function(self._h, {"exp": 0, "phi1": 1, "filter": 2}[kind], c,
                                           b.ctypes.data_as(C.POINTER(C.c_double)), C.byref(err)))
         return b[0::2] + 1j * b[1::2], err.value
 
@@ -173,6 +193,20 @@ class Operator:
                                              C.c_void_p(u.data_ptr()), C.c_void_p(out.data_ptr()),
                                              _stream_ptr(stream)))
         return out
+
+    def apply_filtered(self, u, n_steps=1, keep: float = 0.9, stream=None):
+        """u <- (S(tau L) R(tau L))^n_steps u for one state [fields, n_nodes]: each step
+        applies the approximant, then the filter S (residues fit_function("filter",
+        keep)) on the same poles (Section 3.3).  Two sweeps per step."""
+        import torch
+        if not hasattr(self, "_filter") or self._filter[0] != keep:
+            self._filter = (keep, self.fit_function("filter", keep)[0])
+        out = torch.empty((1,) + tuple(u.shape), dtype=u.dtype, device=u.device)
+        for _ in range(n_steps):
+            self.apply(u, 1, stream)
+            self.apply_functions([self._filter[1]], u, out, stream)
+            u.copy_(out[0])
+        return u
 
     def set_timing(self, on: bool):
         check(_capi.lib().eo_set_timing(self._h, int(on)))

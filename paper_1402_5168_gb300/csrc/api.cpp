@@ -104,6 +104,13 @@ void eo::pole_weights(const Handle& h, const std::vector<cx>& cw, std::vector<cd
 
 namespace {
 
+// Position in the distinct pole list of pole j (eo_get_poles order), or -1.
+int distinct_of(const Handle& h, int j) {
+  for (int d = 0; d < h.P; ++d)
+    if (h.pole_index[d] == j) return d;
+  return -1;
+}
+
 eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   const Grid& g = h.g;
   const int p = g.p, q = g.q, ni = q * q, nb = 4 * q;
@@ -112,7 +119,13 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   const double delta = o.delta > 0 ? o.delta : 1e-10;
   if (!(o.band > 0)) return fail(EO_ERR_INVALID_ARG, "opts.band must be positive");
   eo_status rc;
-  if (o.n_poles > 0) {
+  if (o.fitter != EO_FIT_LINE && o.fitter != EO_FIT_GAUSS) return fail(EO_ERR_INVALID_ARG, "unknown opts.fitter");
+  if (o.fitter == EO_FIT_GAUSS) {
+    if (o.n_poles > 0) return fail(EO_ERR_INVALID_ARG, "the Gaussian-sum fitter takes tau, not n_poles");
+    if (!(o.tau > 0)) return fail(EO_ERR_INVALID_ARG, "opts.tau must be positive");
+    if ((rc = fit_gauss(o.tau * o.band, o.gauss_h > 0 ? o.gauss_h : 0.18, delta, h.fit))) return rc;
+    h.tau = o.tau;
+  } else if (o.n_poles > 0) {
     if ((rc = fit_for_poles(o.n_poles, delta, h.fit))) return rc;
     h.tau = h.fit.X / o.band;
   } else {
@@ -120,16 +133,15 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
     if ((rc = fit_for_band(o.tau * o.band, delta, 1 << 20, h.fit))) return rc;
     h.tau = o.tau;
   }
-  const int N = h.fit.N(), M = (N - 1) / 2;
-  h.P = M + 1;
+  // distinct poles of the conjugate-pole form: weight 1 on a real pole, 2 on a pair
+  distinct_poles(h.fit, h.pole_index);
+  h.P = (int)h.pole_index.size();
   h.alpha.resize(h.P);
   h.cw.resize(h.P);
-  h.pole_index.resize(h.P);
   for (int j = 0; j < h.P; ++j) {
-    const int i = M + j;
-    h.pole_index[j] = i;
+    const int i = h.pole_index[j];
     h.alpha[j] = cx(h.fit.are[i], h.fit.aim[i]);
-    h.cw[j] = (j == 0 ? 1.0 : 2.0) * cx(h.fit.bre[i], h.fit.bim[i]);
+    h.cw[j] = (h.fit.aim[i] == 0.0 ? 1.0 : 2.0) * cx(h.fit.bre[i], h.fit.bim[i]);
   }
   h.R = std::max(1, o.max_rhs);
   h.shared = o.shared_ops ? 1 : 0;
@@ -379,16 +391,16 @@ eo_status eo_apply_functions(eo_handle_t hd, int n_out, const double* b_sets, co
   if (!hd || !b_sets || !u_dev || !out_dev) return fail(EO_ERR_INVALID_ARG, "null argument");
   if (n_out < 1) return fail(EO_ERR_INVALID_ARG, "n_out must be >= 1");
   Handle& h = hd->h;
-  const int N = h.fit.N(), M = (N - 1) / 2;
+  const int N = h.fit.N();
   std::vector<cd> wall;
   std::vector<double> Call(4 * (size_t)n_out);
   for (int k = 0; k < n_out; ++k) {
     const double* bk = b_sets + (size_t)2 * N * k;
     std::vector<cx> cw(h.P);
     for (int j = 0; j < h.P; ++j) {
-      const int i = M + j;
+      const int i = h.pole_index[j];
       if (!std::isfinite(bk[2 * i]) || !std::isfinite(bk[2 * i + 1])) return fail(EO_ERR_INVALID_ARG, "non-finite residue");
-      cw[j] = (j == 0 ? 1.0 : 2.0) * cx(bk[2 * i], bk[2 * i + 1]);
+      cw[j] = (h.fit.aim[i] == 0.0 ? 1.0 : 2.0) * cx(bk[2 * i], bk[2 * i + 1]);
     }
     std::vector<cd> w;
     pole_weights(h, cw, w, &Call[4 * (size_t)k]);
@@ -458,6 +470,22 @@ eo_status eo_fit(int n_poles, double X, double delta, int cap, double* alpha, do
   return EO_OK;
 }
 
+eo_status eo_fit_gauss(double X, double h, double delta, int cap, double* alpha, double* b, int* n, int* M) {
+  if (!n) return fail(EO_ERR_INVALID_ARG, "null argument");
+  Fit f;
+  eo_status rc = fit_gauss(X, h > 0 ? h : 0.18, delta > 0 ? delta : 1e-10, f);
+  if (rc) return rc;
+  *n = f.N();
+  if (M) *M = f.gM;
+  if (cap < f.N() || !alpha || !b) return fail(EO_ERR_INVALID_ARG, "output arrays too small");
+  for (int i = 0; i < f.N(); ++i) {
+    alpha[2 * i] = f.are[i]; alpha[2 * i + 1] = f.aim[i];
+    b[2 * i] = f.bre[i]; b[2 * i + 1] = f.bim[i];
+  }
+  set_error("");
+  return EO_OK;
+}
+
 eo_status eo_get_poles(eo_handle_t hd, double* alpha, double* b, int* n, double* tau, double* X) {
   if (!hd) return fail(EO_ERR_INVALID_ARG, "null handle");
   const Fit& f = hd->h.fit;
@@ -509,10 +537,9 @@ eo_status eo_apply_host(eo_handle_t hd, double* u_host, int n_rhs, int n_steps, 
 eo_status eo_apply_resolvent(eo_handle_t hd, int j, const double* u_dev, double* x_dev, void* stream) {
   if (!hd || !u_dev || !x_dev) return fail(EO_ERR_INVALID_ARG, "null argument");
   // j is an index of eo_get_poles' order; map to the distinct pole list (Im >= 0)
-  const Handle& h = hd->h;
-  const int M = (h.fit.N() - 1) / 2;
-  if (j < M || j >= h.fit.N()) return fail(EO_ERR_INVALID_ARG, "pole index must have Im(alpha) >= 0");
-  return apply_resolvent(hd->h, j - M, u_dev, x_dev, (cudaStream_t)stream);
+  const int d = distinct_of(hd->h, j);
+  if (d < 0) return fail(EO_ERR_INVALID_ARG, "pole index must have Im(alpha) >= 0");
+  return apply_resolvent(hd->h, d, u_dev, x_dev, (cudaStream_t)stream);
 }
 
 eo_status eo_set_timing(eo_handle_t hd, int on) {
@@ -549,10 +576,9 @@ eo_status eo_get_timing(eo_handle_t hd, int* n_classes, const char** names, int6
 
 eo_status eo_apply_resolvent_noalloc(eo_handle_t hd, int j, const double* u_dev, double* x_dev, void* stream) {
   if (!hd || !u_dev || !x_dev) return fail(EO_ERR_INVALID_ARG, "null argument");
-  const Handle& h = hd->h;
-  const int M = (h.fit.N() - 1) / 2;
-  if (j < M || j >= h.fit.N()) return fail(EO_ERR_INVALID_ARG, "pole index must have Im(alpha) >= 0");
-  return apply_resolvent_noalloc(hd->h, j - M, u_dev, x_dev, (cudaStream_t)stream);
+  const int d = distinct_of(hd->h, j);
+  if (d < 0) return fail(EO_ERR_INVALID_ARG, "pole index must have Im(alpha) >= 0");
+  return apply_resolvent_noalloc(hd->h, d, u_dev, x_dev, (cudaStream_t)stream);
 }
 
 eo_status eo_destroy(eo_handle_t hd) {

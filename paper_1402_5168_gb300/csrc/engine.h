@@ -60,16 +60,33 @@ struct Plan {
 void make_plan(const Grid& g, Plan& plan);
 
 // ---------------------------------------------------------------- fitter
+// Poles and residues, as consecutive conjugate-closed vertical lines, each of
+// odd length 2K+1 in order of increasing imaginary part (index K of a line is
+// its real pole).  The line fit has one line (m = -M..M); the Gaussian-sum
+// construction of Sections 3.1-3.2 has two (the right line, then its mirror).
 struct Fit {
-  std::vector<double> are, aim, bre, bim;   // 2M+1 poles / residues, m = -M..M
+  std::vector<double> are, aim, bre, bim;
+  std::vector<int> lines;                   // line lengths (empty: one line of N)
   double X = 0, sigma = 0, s = 0;
   int E = 0;                                // wide fits: outer pairs fitted by least squares (0: all)
+  double gh = 0;                            // Gaussian-sum fit: spacing h (0: line fit)
+  int gM = 0, gL = 0;                       // Gaussian-sum fit: M Gaussians per side, L of Table 1
   int N() const { return (int)are.size(); }
 };
 
-// Residues on the poles of f for exp(c z) (kind 0) or phi1(z) (kind 1), and the
-// band error max |f(ix) - R(ix)| on [-X, X].
+// Indices (into the fit's order) of the distinct poles of the conjugate-pole form
+// (Section 3.3): per line its real pole, then the poles with Im > 0.
+void distinct_poles(const Fit& f, std::vector<int>& idx);
+
+// Residues on the poles of f for exp(c z) (kind 0), phi1(z) (kind 1) or, on a
+// Gaussian-sum fit, the rational partition of unity keeping a fraction c of the
+// Gaussians (kind 2); err = max |f(ix) - R(ix)| on [-X, X].
 eo_status fit_function(const Fit& f, int kind, double c, std::vector<std::complex<double>>& b, double& err);
+
+// The paper's approximant (Sections 3.1-3.2): e^{i theta} = e^{2 pi i x} as a
+// sum of 2M+1 shifted Gaussians psi_h, each replaced by the Table 1 rational;
+// M is the smallest meeting delta on [-X, X].  Two lines of 2(M+L)+1 poles.
+eo_status fit_gauss(double X, double h, double delta, Fit& out);
 
 // Widest band X for a given odd pole count; returns EO_ERR_FIT if none.
 eo_status fit_for_poles(int n_poles, double delta, Fit& out);

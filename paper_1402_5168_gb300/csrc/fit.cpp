@@ -469,6 +469,234 @@ eo_status fit_for_band(double X, double delta, int nmax, Fit& out) {
   return fail(EO_ERR_FIT, "band*tau too wide for the supported pole counts");
 }
 
+// ---------------------------------------------------------------- the paper's construction
+// Sections 3.1-3.2.  A function f with f^ supported in [-1/(2h), 1/(2h)] is a sum of
+// shifted Gaussians, f(x) = sum_m c_m psi_h(x + m h), psi_h(x) = (4 pi)^{-1/2}
+// e^{-x^2/(4h^2)}, c_m = h int e^{-2 pi i m h xi} f^(xi) / psi_h^(xi) dxi with
+// psi_h^(xi) = h e^{-4 pi^2 h^2 xi^2}; for e^{2 pi i t x}, c_m = e^{4 pi^2 h^2 t^2}
+// e^{-2 pi i m h t}.  Each psi_h(x + m h) = psi_1(x/h + m) is replaced by the Table 1
+// rational psi_1(y) ~= Re sum_{j=-L..L} a_j / (i y + mu + i j).  For real x,
+// Re w = (w + conj w)/2; in z = 2 pi i x (so z = i theta, e^z = e^{2 pi i x}) the two
+// halves are two vertical pole lines, n = -(M+L)..M+L:
+//   p+_n = -2 pi h (mu + i n)  (right half-plane, mu < 0),  residue  pi h sum_{m+j=n} c_m a_j,
+//   p-_n =  2 pi h (mu - i n)  (its mirror image),          residue -pi h sum_{m+j=n} c_m conj(a_j).
+// Table 1 is used through its even part (a_j + conj(a_{-j}))/2 (psi_1 is even, so the error
+// does not grow), which makes the approximant exactly conjugate-closed.
+
+// Table 1 (Section 3.2): mu and (Re a_j, Im a_j), j = -11..11.
+static const int kTabL = 11;
+static const double kTabMu = -4.315321510875024;
+static const double kTabA[2 * kTabL + 1][2] = {
+    {-1.0845749544592896e-7, 2.77075431662228e-8},  {1.858753344202957e-8, -9.105375434750162e-7},
+    {3.6743713227243024e-6, 7.073284346322969e-7},  {-2.7990058083347696e-6, 0.0000112564827639346},
+    {0.000014918577548849352, -0.0000316278486761932}, {-0.0010751767283285608, -0.00047282220513073084},
+    {0.003816465653840016, 0.017839810396560574},  {0.12124105653274578, -0.12327042473830248},
+    {-0.9774980792734348, -0.1877130220537587},    {1.3432866123333178, 3.2034715228495942},
+    {4.072408546157305, -6.123755543580666},       {-9.442699917778205, 0.0},
+    {4.072408620272648, 6.123755841848161},        {1.3432860877712938, -3.2034712658530275},
+    {-0.9774985292598916, 0.18771238018072134},    {0.1212417070363373, 0.12326987628935386},
+    {0.0038169724770333343, -0.017839242222443888}, {-0.0010756025812659208, 0.0004731874917343858},
+    {0.000014713754789095218, 0.000031358475831136815}, {-2.659323898804944e-6, -0.000011341571201752273},
+    {3.6970377676364553e-6, -6.517457477594937e-7}, {3.883933649142257e-9, 9.128496023863376e-7},
+    {-1.0816457995911385e-7, -2.954309729192276e-8}};
+
+void distinct_poles(const Fit& f, std::vector<int>& idx) {
+  idx.clear();
+  const std::vector<int> lines = f.lines.empty() ? std::vector<int>{f.N()} : f.lines;
+  int s0 = 0;
+  for (int n : lines) {
+    const int K = (n - 1) / 2;
+    for (int j = 0; j <= K; ++j) idx.push_back(s0 + K + j);
+    s0 += n;
+  }
+}
+
+static std::vector<cplx> table_even() {
+  std::vector<cplx> a(2 * kTabL + 1);
+  for (int j = -kTabL; j <= kTabL; ++j) {
+    const cplx p(kTabA[j + kTabL][0], kTabA[j + kTabL][1]), q(kTabA[kTabL - j][0], kTabA[kTabL - j][1]);
+    a[j + kTabL] = 0.5 * (p + std::conj(q));
+  }
+  a[kTabL] = a[kTabL].real();
+  return a;
+}
+
+static void gauss_poles(int M, double h, std::vector<cplx>& al) {
+  const int K = M + kTabL, n1 = 2 * K + 1;
+  al.resize(2 * (size_t)n1);
+  for (int n = -K; n <= K; ++n) {
+    const int i = K - n;                   // increasing imaginary part along each line
+    al[i] = -2.0 * M_PI * h * cplx(kTabMu, n);
+    al[n1 + i] = 2.0 * M_PI * h * cplx(kTabMu, -n);
+  }
+}
+
+// Residues on the two lines for Gaussian-sum coefficients c (m = -M..M, c_{-m} = conj c_m),
+// made exactly conjugate-symmetric along each line.
+static void gauss_residues(int M, double h, const std::vector<cplx>& c, std::vector<cplx>& b) {
+  const std::vector<cplx> a = table_even();
+  const int L = kTabL, K = M + L, n1 = 2 * K + 1;
+  b.assign(2 * (size_t)n1, cplx(0, 0));
+  for (int m = -M; m <= M; ++m)
+    for (int j = -L; j <= L; ++j) {
+      const int i = K - (m + j);
+      b[i] += M_PI * h * c[m + M] * a[j + L];
+      b[n1 + i] -= M_PI * h * c[m + M] * std::conj(a[j + L]);
+    }
+  for (int l = 0; l < 2; ++l) {
+    cplx* bl = &b[(size_t)l * n1];
+    for (int k = 1; k <= K; ++k) bl[K - k] = std::conj(bl[K + k]);
+    bl[K] = bl[K].real();
+  }
+}
+
+// c_m of e^{2 pi i t x} (eq. "coeff. for exp, gauss" with the normalisation of Section 3.1).
+static void exp_coeffs(int M, double h, double t, std::vector<cplx>& c) {
+  c.resize(2 * (size_t)M + 1);
+  const double g = std::exp(4.0 * M_PI * M_PI * h * h * t * t);
+  for (int m = 0; m <= M; ++m) {
+    c[M + m] = g * std::exp(cplx(0.0, -2.0 * M_PI * m * h * t));
+    c[M - m] = std::conj(c[M + m]);
+  }
+  c[M] = c[M].real();
+}
+
+// Gauss-Legendre nodes and weights on [0, 1] (Newton on the three-term recurrence).
+static void gauss_legendre01(int n, std::vector<double>& x, std::vector<double>& w) {
+  x.resize(n); w.resize(n);
+  for (int i = 0; i < n; ++i) {
+    double z = std::cos(M_PI * (i + 0.75) / (n + 0.5)), dp = 1.0;
+    for (int it = 0; it < 100; ++it) {
+      double p0 = 1.0, p1 = z;
+      for (int k = 2; k <= n; ++k) {
+        const double p2 = ((2.0 * k - 1.0) * z * p1 - (k - 1.0) * p0) / k;
+        p0 = p1; p1 = p2;
+      }
+      dp = n * (z * p1 - p0) / (z * z - 1.0);
+      const double dz = p1 / dp;
+      z -= dz;
+      if (std::abs(dz) < 1e-16) break;
+    }
+    x[i] = 0.5 * (1.0 - z);
+    w[i] = 1.0 / ((1.0 - z * z) * dp * dp);   // 2/((1-z^2) P'^2), halved for [0, 1]
+  }
+}
+
+// c_m of phi1(2 pi i x) = int_0^1 e^{2 pi i s x} ds: the integral over s of the
+// exp coefficients, by composite 16-point Gauss-Legendre panels short enough for
+// the oscillation e^{-2 pi i m h s} at |m| = M.
+static void phi1_coeffs(int M, double h, std::vector<cplx>& c) {
+  std::vector<double> gx, gw;
+  gauss_legendre01(16, gx, gw);
+  const int panels = std::max(4, (int)std::ceil(2.0 * M_PI * M * h / 2.0) + 1);
+  c.assign(2 * (size_t)M + 1, cplx(0, 0));
+  par_for(M + 1, [&](int64_t m0, int64_t m1) {
+    for (int64_t m = m0; m < m1; ++m) {
+      cplx acc(0, 0);
+      for (int pnl = 0; pnl < panels; ++pnl)
+        for (int k = 0; k < 16; ++k) {
+          const double s = (pnl + gx[k]) / panels;
+          acc += (gw[k] / panels) * std::exp(4.0 * M_PI * M_PI * h * h * s * s) *
+                 std::exp(cplx(0.0, -2.0 * M_PI * m * h * s));
+        }
+      c[M + m] = acc;
+    }
+  });
+  for (int m = 1; m <= M; ++m) c[M - m] = std::conj(c[M + m]);
+  c[M] = c[M].real();
+}
+
+// max over theta in [t0, t1] (step dt) of |g(theta) - R(i theta)|.
+static double band_err(const std::vector<cplx>& al, const std::vector<cplx>& b, double t0, double t1,
+                       double dt, const std::function<cplx(double)>& g) {
+  const int64_t n = std::max<int64_t>(2, (int64_t)std::ceil((t1 - t0) / dt) + 1);
+  std::vector<double> part(64, 0.0);
+  std::atomic<int> slot(0);
+  par_for(n, [&](int64_t i0, int64_t i1) {
+    double mx = 0;
+    for (int64_t i = i0; i < i1; ++i) {
+      const double th = t0 + (t1 - t0) * i / (n - 1);
+      mx = std::max(mx, std::abs(g(th) - Reval(th, al, b)));
+    }
+    part[slot++] = mx;
+  });
+  return *std::max_element(part.begin(), part.end());
+}
+
+static void store_gauss(int M, double h, double X, const std::vector<cplx>& al, const std::vector<cplx>& b,
+                        Fit& out) {
+  const int N = (int)al.size(), n1 = N / 2;
+  out.are.resize(N); out.aim.resize(N); out.bre.resize(N); out.bim.resize(N);
+  for (int i = 0; i < N; ++i) {
+    out.are[i] = al[i].real(); out.aim[i] = al[i].imag();
+    out.bre[i] = b[i].real(); out.bim[i] = b[i].imag();
+  }
+  out.lines = {n1, n1};
+  out.X = X; out.sigma = -2.0 * M_PI * h * kTabMu; out.s = 2.0 * M_PI * h; out.E = 0;
+  out.gh = h; out.gM = M; out.gL = kTabL;
+}
+
+eo_status fit_gauss(double X, double h, double delta, Fit& out) {
+  if (!(X > 0)) return fail(EO_ERR_INVALID_ARG, "band*tau must be positive");
+  if (!(h > 0 && h < 0.5)) return fail(EO_ERR_INVALID_ARG, "Gaussian spacing h must be in (0, 0.5)");
+  const int M0 = (int)std::ceil(X / (2.0 * M_PI * h));
+  if (M0 > 400000) return fail(EO_ERR_INVALID_ARG, "band too wide for this spacing h");
+  auto ex = [](double th) { return std::exp(cplx(0.0, th)); };
+  std::vector<cplx> c, al, b;
+  // R(-i theta) = conj R(i theta) exactly, so [0, X] suffices; the error grows
+  // only near the ends of the Gaussian sum, so the edge window decides M.
+  for (int M = M0; M <= M0 + 400; ++M) {
+    exp_coeffs(M, h, 1.0, c);
+    gauss_poles(M, h, al);
+    gauss_residues(M, h, c, b);
+    if (band_err(al, b, std::max(0.0, X - 40.0), X, 0.02, ex) > delta) continue;
+    if (band_err(al, b, 0.0, X, 0.02, ex) > delta)
+      return fail(EO_ERR_FIT, "Gaussian-sum approximant misses delta inside the band (h too large)");
+    store_gauss(M, h, X, al, b, out);
+    return EO_OK;
+  }
+  return fail(EO_ERR_FIT, "no Gaussian-sum approximant meets delta");
+}
+
+// Residues of exp(c z), phi1(z) or the partition of unity (kind 2, c the fraction
+// of the Gaussians kept) on the poles of a Gaussian-sum fit.
+static eo_status fit_function_gauss(const Fit& f, int kind, double c, std::vector<cplx>& b, double& err) {
+  const int M = f.gM;
+  const double h = f.gh, X = f.X;
+  std::vector<cplx> cm, al;
+  gauss_poles(M, h, al);
+  std::function<cplx(double)> g;
+  if (kind == 0) {
+    exp_coeffs(M, h, c, cm);
+    g = [c](double th) { return std::exp(cplx(0.0, c * th)); };
+  } else if (kind == 1) {
+    phi1_coeffs(M, h, cm);
+    g = [](double th) {
+      if (std::abs(th) < 1e-6) return cplx(1.0 - th * th / 6.0, th / 2.0 - th * th * th / 24.0);
+      return (std::exp(cplx(0.0, th)) - 1.0) / cplx(0.0, th);
+    };
+  } else {
+    if (!(c > 0 && c <= 1)) return fail(EO_ERR_INVALID_ARG, "filter fraction must be in (0, 1]");
+    const int M0 = (int)std::floor(c * M);
+    cm.assign(2 * (size_t)M + 1, cplx(0, 0));
+    for (int m = -M0; m <= M0; ++m) cm[m + M] = 1.0;
+    // chi(x) = sum_{|m|<=M0} psi_h(x + m h), x = theta / (2 pi); terms beyond 40 h are < e^{-400}
+    g = [M0, h](double th) {
+      const double x = th / (2.0 * M_PI);
+      const int lo = std::max(-M0, (int)std::floor(-x / h) - 40), hi = std::min(M0, (int)std::ceil(-x / h) + 40);
+      double s = 0;
+      for (int m = lo; m <= hi; ++m) {
+        const double y = (x + m * h) / h;
+        s += std::exp(-0.25 * y * y);
+      }
+      return cplx(s / std::sqrt(4.0 * M_PI), 0.0);
+    };
+  }
+  gauss_residues(M, h, cm, b);
+  err = band_err(al, b, 0.0, X, 0.02, g);
+  return EO_OK;
+}
+
 // ---------------------------------------------------------------- other functions, same poles
 // Values on the imaginary axis of the functions the same poles can carry
 // (dense output and phi-functions, Section 1.2 remarks on reusing the solves):
@@ -488,8 +716,10 @@ static cplx fn_value(int kind, double c, double th) {
 // and the E outermost pairs by least squares, as for exp(z) itself.
 // err: max |f(i x) - R(i x)| on [0, X] (both signs by conjugate symmetry).
 eo_status fit_function(const Fit& f, int kind, double c, std::vector<cplx>& b, double& err) {
-  if (kind != 0 && kind != 1) return fail(EO_ERR_INVALID_ARG, "unknown function kind");
+  if (kind != 0 && kind != 1 && kind != 2) return fail(EO_ERR_INVALID_ARG, "unknown function kind");
   if (kind == 0 && !(c > 0 && c <= 1)) return fail(EO_ERR_INVALID_ARG, "c must be in (0, 1]");
+  if (f.gh > 0) return fit_function_gauss(f, kind, c, b, err);
+  if (kind == 2) return fail(EO_ERR_UNSUPPORTED, "the filter needs the Gaussian-sum fitter");
   const int N = f.N(), M = (N - 1) / 2;
   const double X = f.X, s = f.s;
   std::vector<cplx> al(N);

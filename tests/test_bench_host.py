@@ -77,7 +77,7 @@ def test_class_work_counts_for_the_shallow_water_workload():
     import workloads as W
 
     class Op:
-        alpha = __import__("numpy").zeros(5757)
+        alpha = 4.5 + 1j * __import__("numpy").arange(-2878, 2879)     # one line, 2879 with Im >= 0
     w = W.SW_16X16_P16
     work = bench.class_work(Op(), w, 1, "df32", fd=True)
     P, q = 2879, 14

@@ -95,3 +95,40 @@ def test_batch_create_rejects_empty_and_null(capi):
     assert L.eo_batch_create(1, None, None, None, C.byref(out)) == 1
     assert L.eo_batch_apply(None, 1, None) == 1
     assert L.eo_batch_destroy(None) == 0
+
+
+@pytest.mark.parametrize("X,h", [(2 * np.pi * 27.3, 0.18), (60.0, 0.12), (20.0, 0.2)])
+def test_library_gaussian_fit_equals_the_oracle_construction(capi, X, h):
+    # the library's Sections 3.1-3.2 construction (its own Table 1 copy, C++) against
+    # the oracle's (numpy, Table 1 from the golden file), same M
+    import paper_1402_5168_gb300 as eo
+    from oracle import gauss, rational
+    from tests.test_oracle_rational import load_table1
+    mu, a = load_table1()
+    alpha, b, M = eo.fit_gauss(X, h)
+    ao, bo, Mo = gauss.gauss_fit(X, h, mu, a)
+    assert M == Mo and alpha.size == ao.size == 2 * (2 * (M + 11) + 1)
+    assert np.abs(alpha - ao).max() <= 1e-14 * np.abs(ao).max()
+    assert np.abs(b - bo).max() <= 1e-13 * np.abs(bo).max()
+    # each line exactly conjugate-closed, and the band contract by brute force
+    n1 = alpha.size // 2
+    for line in (slice(0, n1), slice(n1, 2 * n1)):
+        al, bl = alpha[line], b[line]
+        assert np.array_equal(al[::-1], np.conj(al)) and np.array_equal(bl[::-1], np.conj(bl))
+    assert gauss.band_error(alpha, b, X) <= 1e-10
+    band, mod, _ = rational.check_contract(alpha, b, X, 1e-10)
+    assert band <= 1e-10 and mod > 1.0      # eq. RM_prop2 is not part of this construction
+
+
+def test_gaussian_fit_rejects_bad_arguments(capi):
+    L = capi.lib()
+    n, M = C.c_int(), C.c_int()
+    assert L.eo_fit_gauss(C.c_double(10.0), C.c_double(0.6), C.c_double(1e-10), 0, None, None,
+                          C.byref(n), C.byref(M)) == 1
+    assert L.eo_fit_gauss(C.c_double(-1.0), C.c_double(0.18), C.c_double(1e-10), 0, None, None,
+                          C.byref(n), C.byref(M)) == 1
+    assert L.eo_fit_gauss(C.c_double(10.0), C.c_double(0.18), C.c_double(1e-10), 0, None, None,
+                          None, None) == 1
+    # h too coarse for delta: aliasing e^{-4 pi^2 (1 - 2h)} alone exceeds it
+    assert L.eo_fit_gauss(C.c_double(10.0), C.c_double(0.4), C.c_double(1e-10), 0, None, None,
+                          C.byref(n), C.byref(M)) == 2
