@@ -88,3 +88,23 @@ def test_class_work_counts_for_the_shallow_water_workload():
     assert work["root"][1] == P * 896 * 896 * 16 + P * 2 * 896 * 16
     # top up merge: ZU has n3 + nbd rows and n3 columns
     assert work["up_merge"][0] > 8.0 * P * (224 + 896) * 224
+
+
+def test_all_core_oracle_baseline_runs_one_process_per_core():
+    # the all-core CPU baseline: spawned processes, single-threaded BLAS, one distinct
+    # pole each, throughput scaled to applies/s (small wave workload, short budget)
+    import types
+    import numpy as np
+    sys.path.insert(0, ROOT)
+    import bench
+    import workloads as W
+    from oracle import sem
+    w = W.WAVE_4X4_P12
+    op = types.SimpleNamespace(alpha=4.5 + 1j * np.arange(-3, 4), b=np.ones(7, complex), tau=0.01)
+    og = sem.Grid(w.nlx, w.nly, w.p)
+    u0 = np.zeros((2, og.n_nodes))
+    u0[1] = 1.0
+    r = bench.cpu_baseline_all_cores(w, op, u0, budget_s=0.3, max_workers=2)
+    assert r["kind"] == "oracle" and r["cores"] == min(2, os.cpu_count()) and r["value"] > 0
+    assert "4 distinct poles" in r["sample"]
+    assert os.environ["OPENBLAS_NUM_THREADS"] == "1"
