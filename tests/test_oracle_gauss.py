@@ -108,7 +108,7 @@ def test_pole_lines_and_conjugate_closure():
     assert conjugate_closed(alpha, b, tol=1e-13 * np.abs(b).max())
 
 
-def test_reproduces_the_survey_x3_construction():
+def test_h_018_covers_27_3_at_1e_10_with_690_poles():
     # h = 0.18 covers |x| <= 27.3 (|theta| <= 2 pi 27.3) at 1e-10 with M = 161:
     # 2 lines x (2 (M + 11) + 1) = 690 poles (M = 160 gives 686 poles at 3.5e-10)
     X = 2 * np.pi * 27.3
