@@ -97,7 +97,7 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fitter="line"):
+def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fitter="line", root_dense=False):
     if w.kind == "wave":
         c = W.wave_c(w, x, y)
         if fitter == "gauss":
@@ -112,7 +112,7 @@ def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fi
     # a pole-count override (profiling cases) replaces the fixed step by tau = X(poles) / band
     return eo.Operator(g, eo.SW_WALLS, band=W.BAND[w.name], tau=0.0 if poles else w.tau, n_poles=poles,
                        f=pr["f"], g=pr["g"], H=pr["H"], shared_ops=True, max_rhs=R, precision=precision,
-                       dense_leaves=dense_leaves, fitter=fitter)
+                       dense_leaves=dense_leaves, fitter=fitter, root_dense=root_dense)
 
 
 def timed_steps(torch, op, u, steps, stream, dist, label="timed"):
@@ -162,9 +162,11 @@ def plan_levels(nlx, nly, q):
     return out
 
 
-def class_work(op, w, R, prec, fd):
+def class_work(op, w, R, prec, fd, root_c4=False):
     """Algorithmic FP64-equivalent flops (8 per complex multiply-add) and bytes
-    of one step, per kernel class, with the arithmetic precision of each."""
+    of one step, per kernel class, with the arithmetic precision of each.
+    root_c4: the wall solve runs as four Fourier blocks of a quarter of the wall
+    nodes each (square walled domain), a quarter of the dense inverse's entries."""
     q = w.p - 2
     ni, nb = q * q, 4 * q
     P = int((op.alpha.imag >= 0).sum())
@@ -203,7 +205,8 @@ def class_work(op, w, R, prec, fd):
     work["down_merge"] = (df, db, prec)
     if w.kind == "sw":
         nr = lv[-1]["nbd"]
-        work["root"] = (8.0 * P * R * nr * nr, P * nr * nr * esz + P * R * 2 * nr * 16, prec)
+        ent = 4 * (nr // 4) ** 2 if root_c4 else nr * nr
+        work["root"] = (8.0 * P * R * ent, P * ent * esz + P * R * 2 * nr * 16, prec)
     return work
 
 
@@ -211,11 +214,12 @@ def class_work(op, w, R, prec, fd):
 # kernel class, from the ncu --set full capture of the shallow-water workload with 301 poles
 # (151 distinct), FP32-pair precision, summarised in
 # profiles/step_kernels_sw_16x16_p16_N301_df32.md.  Traffic grows with the number of distinct
-# poles (one block set per pole, read once), so a full step scales it by P / 151.
+# poles (one block set per pole, read once), so a full step scales it by P / 151.  The root
+# entry is that of the dense wall inverse (root_dense); the four-block root has no capture.
 NCU_TRAFFIC_151 = {
     ("sw_walls_16x16_p16_tau20T", "df32", "up_merge"): 1.2009e9 + 12.85e6,
     ("sw_walls_16x16_p16_tau20T", "df32", "down_merge"): 0.9587e9 + 10.57e6,
-    ("sw_walls_16x16_p16_tau20T", "df32", "root"): 1.9419e9 + 3.43e6,
+    ("sw_walls_16x16_p16_tau20T", "df32", "root_dense"): 1.9419e9 + 3.43e6,
 }
 
 
@@ -225,12 +229,12 @@ def alu_peak(prec):
     return {"fp32": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS, "df32": FP32_PEAK_TFLOPS / 2 / 48 * 8}[prec]
 
 
-def roofline(op, w, R, tim, prec, pk, pk_kind, fd):
+def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False):
     """Per kernel class: algorithmic work of one step over that class's device
     time per step (CUDA events around its launches), against the ALU peak of
     its arithmetic and the measured HBM copy bandwidth; the class with the
     largest time share is reported as the roofline of the step."""
-    work = class_work(op, w, R, prec, fd)
+    work = class_work(op, w, R, prec, fd, root_c4)
     per = {}
     for cls, (flops, nbytes, pr) in work.items():
         n, ms = tim.get(cls, (0, 0.0))
@@ -262,7 +266,8 @@ def roofline(op, w, R, tim, prec, pk, pk_kind, fd):
         rf = {"bound": "hbm", "achieved": d["gbs"], "peak": pk["hbm_gbs"], "unit": "GB/s", "frac": d["hbm_frac"],
               "peak_source": pk_kind}
     P = int((op.alpha.imag >= 0).sum())
-    tr = NCU_TRAFFIC_151.get((w.name, prec, top)) if R == 1 and not (top.endswith("leaf")) else None
+    key = "root_dense" if top == "root" and not root_c4 else top
+    tr = NCU_TRAFFIC_151.get((w.name, prec, key)) if R == 1 and not (top.endswith("leaf")) else None
     rf.update({"kernel": kname, "class": top, "traffic": None if tr is None else tr * P / 151,
                "traffic_note": None if tr is None else
                "ncu DRAM bytes of this class's launches in one step of the 301-pole case, scaled by P/151",
@@ -294,7 +299,11 @@ def run_ours(args):
     g = eo.Grid(w.nlx, w.nly, w.p)
     x, y = g.nodes()
     t0 = time.time()
-    op = build_operator(eo, w, g, x, y, R, args.precision, args.poles, args.dense_leaves, args.fitter)
+    op = build_operator(eo, w, g, x, y, R, args.precision, args.poles, args.dense_leaves, args.fitter,
+                        args.root_dense)
+    # the library splits the wall solve of a square walled domain of square leaves into
+    # four Fourier blocks unless told not to
+    root_c4 = w.kind == "sw" and w.nlx == w.nly and not args.root_dense
     torch.cuda.synchronize()
     build_s = time.time() - t0
     U0 = np.stack([np.stack(W.initial_fields(w, x, y, r)) for r in range(R)])
@@ -322,7 +331,8 @@ def run_ours(args):
     # the mixed path's error after the same number of steps from the same input
     fp64 = None
     if reduced and args.compare_fp64:
-        op64 = build_operator(eo, w, g, x, y, R, "fp64", args.poles, args.dense_leaves, args.fitter)
+        op64 = build_operator(eo, w, g, x, y, R, "fp64", args.poles, args.dense_leaves, args.fitter,
+                              args.root_dense)
         u64 = torch.tensor(U0, device=dev)
         for _ in range(args.warmup):
             op64.apply(u64, 1)
@@ -355,6 +365,8 @@ def run_ours(args):
         "config": {"workload": w.name, "kind": w.kind, "leaves": f"{w.nlx}x{w.nly}", "p": w.p,
                    "fitter": {"line": "least-squares pole line", "gauss": "Gaussian sums + Table 1 "
                               "(two pole lines)"}[args.fitter],
+                   "root": ("four Fourier blocks of the quarter-turn-symmetric wall system" if root_c4
+                            else "dense wall inverse") if w.kind == "sw" else "none (Dirichlet)",
                    "precision": {"fp32": "FP32 operator blocks and products; FP64 vectors, pole sum, maps",
                                  "df32": "FP32-pair (hi, lo) operator blocks, exact split products and "
                                          "compensated sums on the FP32 pipe; FP64 vectors, pole sum, maps",
@@ -370,7 +382,8 @@ def run_ours(args):
                 "h2d_bytes_per_step": int(U0.nbytes), "d2h_bytes_per_step": int(U0.nbytes)},
         "gpu_launches": int(launches),
         "kernel_share": shares,
-        "roofline": roofline(op, w, R, tim, args.precision, pk, pk_kind, fd=(w.kind == "sw" and not args.dense_leaves)),
+        "roofline": roofline(op, w, R, tim, args.precision, pk, pk_kind, fd=(w.kind == "sw" and not args.dense_leaves),
+                             root_c4=root_c4),
         "clocks": clocks,
     }
     if args.cpu_baseline:
@@ -630,6 +643,8 @@ def main():
     ap.add_argument("--dense-leaves", action="store_true",
                     help="dense leaf solution operators instead of the separable leaf eigenbasis")
     ap.add_argument("--precision", default="df32", choices=["df32", "fp32", "fp64"])
+    ap.add_argument("--root-dense", action="store_true",
+                    help="keep the dense wall inverse instead of the four Fourier blocks of a square domain")
     ap.add_argument("--fitter", default="line", choices=["line", "gauss"],
                     help="line: our least-squares approximant; gauss: the paper's Gaussian-sum construction")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")

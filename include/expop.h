@@ -119,6 +119,12 @@ typedef struct {
                           and tau > 0                                             */
   double gauss_h;      /* EO_FIT_GAUSS: Gaussian spacing h in x = theta / (2 pi)
                           (0: 0.18); smaller h, more poles, smaller aliasing error  */
+  int root_dense;      /* EO_SW_WALLS on a square domain of square leaves: the wall
+                          system commutes with the quarter turn of the domain, so it
+                          splits into four Fourier blocks of a quarter of the wall
+                          nodes each (4x fewer root bytes and flops; the build checks
+                          the symmetry to 1e-9 and fails with EO_ERR_UNSUPPORTED if it
+                          does not hold).  1: keep the dense wall inverse instead   */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.

@@ -448,14 +448,36 @@ __global__ void __launch_bounds__(256) k_adj_root_sw(Sweep s, RootArgs ra, const
   const int n = ra.n;
   TA* Xs = (TA*)smem;
   cd* Out = after(Xs, (size_t)NC * n);
+  const int nq = ra.nq;
   for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
     const int c = e / n, i = e - c * n;
     cd v = make_double2(0.0, 0.0);
     if (c0 + c < s.R) v = E[((long long)pl * s.R + c0 + c) * s.n_edge + (long long)ra.bseg[i / ra.q] * ra.q + (i % ra.q)];
-    Xs[e] = Cv<TA>::from(v);
+    if (nq) Out[e] = v;
+    else Xs[e] = Cv<TA>::from(v);
   }
   __syncthreads();
-  cmvT<NC, TA>((const TA*)ra.Binv + (long long)p * n * n, n, n, n, Xs, n, Out);
+  if (nq) {
+    // (B^{-1})^T = D P^T H^T diag(Chat_m^{-T}) G^T P (the forward kernel's factors
+    // transposed): zhat_m[s] = sum_k i^{mk} x[idx_k(s)], then the transposed blocks
+    for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
+      const int c = e / n, rem = e - c * n, m = rem / nq, sr = rem - m * nq;
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int k = 0; k < 4; ++k) {
+        const cd v = times_ipow(Out[c * n + ra.c4idx[k * nq + sr]], m * k);
+        re += v.x;
+        im += v.y;
+      }
+      Xs[e] = Cv<TA>::from(make_double2(re, im));
+    }
+    __syncthreads();
+    const TA* A = (const TA*)ra.Binv + (long long)p * 4 * nq * nq;
+    for (int m = 0; m < 4; ++m)
+      cmvT<NC, TA>(A + (long long)m * nq * nq, nq, nq, nq, Xs + m * nq, n, Out + (size_t)m * NC * nq);
+  } else {
+    cmvT<NC, TA>((const TA*)ra.Binv + (long long)p * n * n, n, n, n, Xs, n, Out);
+  }
   for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
     const int c = e / n, j = e - c * n;
     const int r = c0 + c;
@@ -465,7 +487,21 @@ __global__ void __launch_bounds__(256) k_adj_root_sw(Sweep s, RootArgs ra, const
     else if (j < ra.sxq + ra.syq) side = 1;
     else if (j < 2 * ra.sxq + ra.syq) side = 2;
     else side = 3;
-    const cd qv = Out[e];
+    cd qv;
+    if (nq) {
+      // out[idx_k(s)] = c4_sign(k) (1/4) sum_m (-i)^{mk} zhat'_m[s]
+      const int ks = ra.c4inv[j], k = ks / nq, sr = ks - k * nq;
+      double re = 0.0, im = 0.0;
+#pragma unroll
+      for (int m = 0; m < 4; ++m) {
+        const cd v = times_ipow(Out[((size_t)m * NC + c) * nq + sr], -(m * k));
+        re += v.x;
+        im += v.y;
+      }
+      qv = make_double2(0.25 * c4_sign(k) * re, 0.25 * c4_sign(k) * im);
+    } else {
+      qv = Out[e];
+    }
     const cd nu = ra.nu[p * 4 + side];
     const cd hv = cmul(nu, qv);
     const long long o = ((long long)pl * s.R + r) * n + j;
@@ -691,7 +727,8 @@ eo_status adjoint_step(Handle& h, const double* yin, double* yout, int R, cudaSt
   if (sw) {
     // wall solve transposed: h_bar at the root and the wall rhs's dependence on F
     const Level& rl = h.plan.lv[L];
-    RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, yin, 3};
+    RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, yin, 3,
+                h.c4, h.c4idx, h.c4inv};
     if ((rc = h.trace_begin(st))) return rc;
     if ((rc = dispatch_t<AdjRootSW>(h.root_fp32, pick_nc_t(0, R, rl.nbd, rl.nbd), s, ra, h.E, hpar, h.qbar, st)))
       return rc;

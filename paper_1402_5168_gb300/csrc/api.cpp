@@ -104,6 +104,46 @@ void eo::pole_weights(const Handle& h, const std::vector<cx>& cw, std::vector<cd
 
 namespace {
 
+// Counterclockwise order of the root's wall nodes when the walled domain maps onto
+// itself under a quarter turn about its centre (square domain, square leaves): side S
+// in ascending x, then each side the quarter turn of the previous one.  idx[k * nq + s]
+// is the wall index (S, E, N, W blocks of nq) of node s of side k.  False when any
+// rotated node is missing or lands on another side.
+bool root_c4_map(const Grid& g, const Level& rl, std::vector<int>& idx) {
+  const int q = g.q, n = rl.nbd;
+  if (rl.sx != rl.sy || n % 4 || std::abs(g.hx - g.hy) > 1e-14 * std::max(g.hx, g.hy)) return false;
+  const int nq = n / 4;
+  std::vector<double> X, Y;
+  g.coords(X, Y);
+  const double cx = 0.5 * (g.x0 + g.x1), cy = 0.5 * (g.y0 + g.y1);
+  const double tol = 1e-10 * std::max(g.x1 - g.x0, g.y1 - g.y0);
+  std::vector<double> bx(n), by(n);
+  for (int i = 0; i < n; ++i) {
+    const int64_t node = g.n_int + (int64_t)rl.bseg[i / q] * q + (i % q);
+    bx[i] = X[node];
+    by[i] = Y[node];
+  }
+  auto turn = [&](int j) {   // wall index of the quarter turn of node j, or -1
+    const double rx = cx - (by[j] - cy), ry = cy + (bx[j] - cx);
+    for (int i = 0; i < n; ++i)
+      if (std::abs(bx[i] - rx) <= tol && std::abs(by[i] - ry) <= tol) return i;
+    return -1;
+  };
+  idx.assign(4 * (size_t)nq, -1);
+  for (int s = 0; s < nq; ++s) idx[s] = s;
+  for (int k = 1; k < 4; ++k)
+    for (int s = 0; s < nq; ++s) {
+      const int i = turn(idx[(k - 1) * nq + s]);
+      if (i < 0 || i / nq != k) return false;
+      idx[k * nq + s] = i;
+    }
+  for (int s = 0; s < nq; ++s)
+    if (turn(idx[3 * nq + s]) != idx[s]) return false;
+  for (int s = 1; s < nq; ++s)
+    if (!(bx[idx[s]] > bx[idx[s - 1]])) return false;
+  return true;
+}
+
 // Position in the distinct pole list of pole j (eo_get_poles order), or -1.
 int distinct_of(const Handle& h, int j) {
   for (int d = 0; d < h.P; ++d)
@@ -217,9 +257,12 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
       ops += P * ld.s_pstride;
     }
   }
+  std::vector<int> c4idx;
   if (h.kind == EO_SW_WALLS) {
     h.nroot = plan.lv[L].nbd;
-    ops += P * (int64_t)h.nroot * h.nroot;
+    if (!o.root_dense && L >= 1 && root_c4_map(g, plan.lv[L], c4idx)) h.c4 = h.nroot / 4;
+    h.binv_pstride = h.c4 ? 4LL * h.c4 * h.c4 : (int64_t)h.nroot * h.nroot;
+    ops += P * h.binv_pstride;
   }
   const double op_gb = (double)ops * (o.precision == EO_PREC_FP32 ? sizeof(float2) : sizeof(cd)) / 1e9;
   if (o.mem_budget_gb > 0 && op_gb > o.mem_budget_gb)
@@ -236,8 +279,14 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
     if ((rc = h.alloc((void**)&ld.ZU, sizeof(cd) * P * ld.zu_pstride, true))) return rc;
     if (ld.s_pstride && (rc = h.alloc((void**)&ld.S, sizeof(cd) * P * ld.s_pstride, true))) return rc;
   }
-  if (h.kind == EO_SW_WALLS && (rc = h.alloc((void**)&h.Binv, sizeof(cd) * P * h.nroot * h.nroot, true)))
+  if (h.kind == EO_SW_WALLS && (rc = h.alloc((void**)&h.Binv, sizeof(cd) * P * h.binv_pstride, true)))
     return rc;
+  if (h.c4) {
+    std::vector<int> inv(h.nroot, -1);
+    for (int e = 0; e < 4 * h.c4; ++e) inv[c4idx[e]] = e;
+    if ((rc = upload(h, &h.c4idx, c4idx, st))) return rc;
+    if ((rc = upload(h, &h.c4inv, inv, st))) return rc;
+  }
   // ---- index maps
   for (int l = 0; l <= L; ++l) {
     const Level& lv = plan.lv[l];

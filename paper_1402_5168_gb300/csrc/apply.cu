@@ -160,6 +160,75 @@ __global__ void __launch_bounds__(256) k_root_sw(Sweep s, RootArgs ra, const cd*
   }
 }
 
+// Root wall solve on a square walled domain: h_b = B^{-1} v with B = D P^T C P, D the
+// per-side row signs c4_sign, P the counterclockwise reordering (c4idx) and C block
+// circulant over the four sides.  So h_b = P^T G diag(Chat_m^{-1}) H P D v with
+// H: rhat_m = (1/4) sum_k (-i)^{mk} r_k and G: y_k = sum_m i^{mk} yhat_m, and Binv
+// holds the four inverse Fourier blocks of each pole (nq x nq, nq = n / 4).
+template <int NC, typename TA>
+__global__ void __launch_bounds__(256) k_root_sw_c4(Sweep s, RootArgs ra, const cd* __restrict__ hroot,
+                                                    cd* __restrict__ E) {
+  extern __shared__ cd smem[];
+  const int pl = blockIdx.y, p = s.p0 + pl;
+  const int c0 = blockIdx.x * NC;
+  const int n = ra.n, nq = ra.nq;
+  TA* Bs = (TA*)smem;
+  cd* Cs = after(Bs, (size_t)NC * n);
+  cd* red = Cs + NC * n;
+  // wall right-hand side v in wall order (into Cs, free until the products)
+  for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
+    const int c = e / n, i = e - c * n;
+    cd v = make_double2(0.0, 0.0);
+    const int r = c0 + c;
+    if (r < s.R) {
+      const int side = i / nq;
+      const long long node = s.n_int + (long long)ra.bseg[i / ra.q] * ra.q + (i % ra.q);
+      const double F1 = ra.state[(long long)r * ra.F * s.n_nodes + node];
+      const double F2 = ra.state[((long long)r * ra.F + 1) * s.n_nodes + node];
+      const cd b0 = ra.bcoef[(p * 4 + side) * 2], b1 = ra.bcoef[(p * 4 + side) * 2 + 1];
+      const cd nu = ra.nu[p * 4 + side];
+      const cd hr = hroot[((long long)pl * s.R + r) * n + i];
+      const cd nh = cmul(nu, hr);
+      v = make_double2(b0.x * F1 + b1.x * F2 - nh.x, b0.y * F1 + b1.y * F2 - nh.y);
+    }
+    Cs[e] = v;
+  }
+  __syncthreads();
+  // rhat_m[s] = (1/4) sum_k (-i)^{mk} c4_sign(k) v[idx_k(s)]: Bs[c][m * nq + s]
+  for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
+    const int c = e / n, rem = e - c * n, m = rem / nq, sr = rem - m * nq;
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int k = 0; k < 4; ++k) {
+      const cd v = times_ipow(Cs[c * n + ra.c4idx[k * nq + sr]], -(m * k));
+      re += c4_sign(k) * v.x;
+      im += c4_sign(k) * v.y;
+    }
+    Bs[e] = Cv<TA>::from(make_double2(0.25 * re, 0.25 * im));
+  }
+  __syncthreads();
+  // yhat_m = Chat_m^{-1} rhat_m: Cs[m][c][s]
+  const TA* A = (const TA*)ra.Binv + (long long)p * 4 * nq * nq;
+  for (int m = 0; m < 4; ++m)
+    cmv<NC, TA>(A + (long long)m * nq * nq, nq, nq, nq, Bs + m * nq, n, Cs + (size_t)m * NC * nq, red);
+  // y_k[s] = sum_m i^{mk} yhat_m[s], stored at wall index idx_k(s)
+  for (int e = threadIdx.x; e < NC * n; e += blockDim.x) {
+    const int c = e / n, rem = e - c * n, k = rem / nq, sr = rem - k * nq;
+    const int r = c0 + c;
+    if (r >= s.R) continue;
+    double re = 0.0, im = 0.0;
+#pragma unroll
+    for (int m = 0; m < 4; ++m) {
+      const cd v = times_ipow(Cs[((size_t)m * NC + c) * nq + sr], m * k);
+      re += v.x;
+      im += v.y;
+    }
+    const int i = ra.c4idx[k * nq + sr];
+    E[((long long)pl * s.R + r) * s.n_edge + (long long)ra.bseg[i / ra.q] * ra.q + (i % ra.q)] =
+        make_double2(re, im);
+  }
+}
+
 // ---------------------------------------------------------------- down: merges
 template <int NC, typename TA>
 __global__ void __launch_bounds__(256) k_down_merge(Sweep s, MergeArgs m, cd* __restrict__ E) {
@@ -604,10 +673,17 @@ template <int NC, typename TA>
 struct RootSW {
   static eo_status run(const Sweep& s, const RootArgs& ra, const cd* hroot, cd* E, int nt, int rsplit,
                        cudaStream_t st) {
+    const size_t smem = sizeof(cd) * ((size_t)NC * 2 * ra.n + 256 * NC) + 64;
+    if (ra.nq) {
+      dim3 grid((s.R + NC - 1) / NC, s.P, 1);
+      EO_SET_SMEM((k_root_sw_c4<NC, TA>), smem);
+      k_root_sw_c4<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(ra.nq), smem, st>>>(s, ra, hroot, E);
+      EO_CUDA_TRY(cudaGetLastError());
+      return EO_OK;
+    }
     rsplit = std::max(1, rsplit);
     dim3 grid((s.R + NC - 1) / NC, s.P, rsplit);
     const int rows_per = (ra.n + rsplit - 1) / rsplit;
-    const size_t smem = sizeof(cd) * ((size_t)NC * 2 * ra.n + 256 * NC) + 64;
     EO_SET_SMEM((k_root_sw<NC, TA>), smem);
     k_root_sw<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(rows_per), smem, st>>>(s, ra, hroot, E);
     EO_CUDA_TRY(cudaGetLastError());
@@ -717,7 +793,8 @@ eo_status sweep_to_edges(Handle& h, const double* uin, int R, int p0, int np, co
     EO_CUDA_TRY(cudaGetLastError());
   } else {
     const Level& rl = h.plan.lv[L];
-    RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, uin, 3};
+    RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, uin, 3,
+                h.c4, h.c4idx, h.c4inv};
     if ((rc = h.trace_begin(st))) return rc;
     const int nc = h.root_tuned.nc ? h.root_tuned.nc : pick_nc(0, R, rl.nbd, rl.nbd);
     if ((rc = dispatch<RootSW>(h.root_fp32, nc, s, ra, hcur, h.E, h.root_tuned.nt, h.root_tuned.rs, st))) return rc;
@@ -893,11 +970,12 @@ eo_status autotune(Handle& h, int R, cudaStream_t st) {
   }
   if (h.kind == EO_SW_WALLS) {
     const Level& rl = h.plan.lv[L];
-    RootArgs ra{rl.nbd, h.g.q, rl.sx * h.g.q, rl.sy * h.g.q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, h.ustate, 3};
+    RootArgs ra{rl.nbd, h.g.q, rl.sx * h.g.q, rl.sy * h.g.q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, h.ustate, 3,
+                h.c4, h.c4idx, h.c4inv};
     float best = 1e30f;
     for (int nc = 1; nc <= 8 && nc <= R; nc *= 2)
-      for (int rs = 1; rs <= 4; rs *= 2)
-        for (int nt : nt_list((rl.nbd + rs - 1) / rs)) {
+      for (int rs = 1; rs <= (h.c4 ? 1 : 4); rs *= 2)
+        for (int nt : nt_list(h.c4 ? h.c4 : (rl.nbd + rs - 1) / rs)) {
           if ((size_t)nc * (2 * rl.nbd + 256) * sizeof(cd) > 200 * 1024) continue;
           const float t = timeit([&] { return dispatch<RootSW>(h.root_fp32, nc, s, ra, h.hA, h.E, nt, rs, st); });
           if (t < 0) return fail(EO_ERR_CUDA, "autotune: root launch failed");

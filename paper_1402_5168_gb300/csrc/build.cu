@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstring>
 #include <string>
 
 #include "handle.h"
@@ -272,6 +273,58 @@ __global__ void root_system(int nbatch, int n, int q, int sxq, int syq, const cd
   }
 }
 
+// Fourier blocks of the rotation-symmetric wall system (square walled domain).  With
+// the wall rows put in the rotation-covariant form (side k's rows times c4s(k)) and
+// both rows and columns in counterclockwise side order, C_{k,l}[s][u] =
+// c4s(k) B[idx_k(s)][idx_l(u)] is block circulant, C_{k,l} = c_{(l-k) mod 4}, and
+// C y = r splits into the four systems Chat_m yhat_m = rhat_m, Chat_m = sum_d i^{md} c_d.
+// c_d is the mean of C_{k,(k+d) mod 4} over the four k; the largest deviation of a
+// C_{k,k+d} entry from it and the largest |B| entry go to stat[0..1] (atomic max of
+// non-negative doubles through their bit patterns).  W: [nbatch][4][nq x nq],
+// column-major like B.
+__device__ __forceinline__ double c4s(int k) { return (k == 1 || k == 2) ? 1.0 : -1.0; }
+
+__global__ void root_c4_blocks(int nbatch, int n, int nq, const int* __restrict__ idx, const cd* __restrict__ B,
+                               cd* __restrict__ W, unsigned long long* stat) {
+  const size_t per = (size_t)nq * nq;
+  double dev = 0.0, bmax = 0.0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)nbatch * per;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t gi = t / per, e = t % per;
+    const int sr = (int)(e % nq), u = (int)(e / nq);
+    const cd* Bg = B + gi * (size_t)n * n;
+    cd c[4];
+    for (int d = 0; d < 4; ++d) {
+      cd v[4];
+      double mx = 0.0, my = 0.0;
+      for (int k = 0; k < 4; ++k) {
+        const cd b = Bg[idx[k * nq + sr] + (size_t)idx[((k + d) & 3) * nq + u] * n];
+        v[k] = make_double2(c4s(k) * b.x, c4s(k) * b.y);
+        mx += v[k].x;
+        my += v[k].y;
+        bmax = fmax(bmax, fmax(fabs(b.x), fabs(b.y)));
+      }
+      c[d] = make_double2(0.25 * mx, 0.25 * my);
+      for (int k = 0; k < 4; ++k) dev = fmax(dev, fmax(fabs(v[k].x - c[d].x), fabs(v[k].y - c[d].y)));
+    }
+    for (int m = 0; m < 4; ++m) {
+      double re = 0.0, im = 0.0;
+      for (int d = 0; d < 4; ++d) {
+        const cd x = c[d];
+        switch ((m * d) & 3) {            // x * i^{md}
+          case 0: re += x.x; im += x.y; break;
+          case 1: re -= x.y; im += x.x; break;
+          case 2: re -= x.x; im -= x.y; break;
+          default: re += x.y; im -= x.x; break;
+        }
+      }
+      W[(gi * 4 + m) * per + sr + (size_t)u * nq] = make_double2(re, im);
+    }
+  }
+  atomicMax(&stat[0], (unsigned long long)__double_as_longlong(dev));
+  atomicMax(&stat[1], (unsigned long long)__double_as_longlong(bmax));
+}
+
 namespace {
 
 struct Cublas {
@@ -392,10 +445,16 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
     ws_merge = std::max(ws_merge, nbo * (2 * (size_t)lv.n3 * lv.n3 + 2 * (size_t)lv.nbd * lv.n3));
     maxT = std::max(maxT, nbo * lv.nbd * lv.nbd);
   }
+  cd* c4w = nullptr;
+  unsigned long long* c4stat = nullptr;
   if (h.kind == EO_SW_WALLS) {
     maxpiv = std::max(maxpiv, (size_t)G * h.nroot);
-    maxinfo = std::max(maxinfo, (size_t)G);
+    maxinfo = std::max(maxinfo, (size_t)G * (h.c4 ? 4 : 1));
     ws_merge = std::max(ws_merge, (size_t)G * h.nroot * h.nroot);
+    if (h.c4) {
+      if ((rc = talloc((void**)&c4w, sizeof(cd) * G * 4 * h.c4 * h.c4))) return rc;
+      if ((rc = talloc((void**)&c4stat, sizeof(unsigned long long) * 2))) return rc;
+    }
   }
   cd *Aw, *T0, *Tc, *Tn, *mw = nullptr, *kap, *dal;
   int *piv, *info;
@@ -521,11 +580,29 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
       const Level& rl = plan.lv[L];
       const int n = rl.nbd;
       cd* Broot = mw;
-      cd* Bi = h.Binv + (size_t)p0 * n * n;
+      cd* Bi = h.Binv + (size_t)p0 * h.binv_pstride;
       root_system<<<2048, 256, 0, st>>>(g, n, q, rl.sx * q, rl.sy * q, dal, h.tau * h.opts.sw_f, dEx, dEy,
                                         Tprev, Broot);
       EO_CUDA_TRY(cudaGetLastError());
-      if ((rc = batched_inverse(cb, st, n, g, Broot, Bi, piv, info, hinfo, "root wall system"))) return rc;
+      if (h.c4) {
+        const int nq = h.c4;
+        EO_CUDA_TRY(cudaMemsetAsync(c4stat, 0, sizeof(unsigned long long) * 2, st));
+        root_c4_blocks<<<2048, 256, 0, st>>>(g, n, nq, h.c4idx, Broot, c4w, c4stat);
+        EO_CUDA_TRY(cudaGetLastError());
+        unsigned long long hs[2];
+        EO_CUDA_TRY(cudaMemcpyAsync(hs, c4stat, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        EO_CUDA_TRY(cudaStreamSynchronize(st));
+        double dev, bmax;
+        std::memcpy(&dev, &hs[0], sizeof(double));
+        std::memcpy(&bmax, &hs[1], sizeof(double));
+        if (!(dev <= 1e-9 * bmax))
+          return fail(EO_ERR_UNSUPPORTED, "root wall system is not symmetric under the quarter turn (deviation " +
+                                              std::to_string(dev / bmax) + "); set opts.root_dense");
+        if ((rc = batched_inverse(cb, st, nq, 4 * g, c4w, Bi, piv, info, hinfo, "root wall Fourier block")))
+          return rc;
+      } else if ((rc = batched_inverse(cb, st, n, g, Broot, Bi, piv, info, hinfo, "root wall system"))) {
+        return rc;
+      }
     }
   }
   EO_CUDA_TRY(cudaStreamSynchronize(st));
@@ -587,7 +664,7 @@ eo_status to_reduced(Handle& h, int prec, cudaStream_t st) {
     ld.fp32 = prec;
   }
   if (keep == 0) {
-    if ((rc = conv(h.Binv, P * (size_t)h.nroot * h.nroot, &h.aBinv))) return rc;
+    if ((rc = conv(h.Binv, P * (size_t)h.binv_pstride, &h.aBinv))) return rc;
     h.root_fp32 = prec;
   }
   return EO_OK;

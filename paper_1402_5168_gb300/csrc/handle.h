@@ -82,9 +82,14 @@ struct Handle {
   cd* H = nullptr;
   cd* XY = nullptr;
   int64_t h_pstride = 0, h_bstride = 0, xy_pstride = 0, xy_bstride = 0;
-  // root oblique solve (EO_SW_WALLS): Binv [pole][nroot x nroot]
+  // root oblique solve (EO_SW_WALLS): Binv [pole][nroot x nroot], or on a square
+  // domain the four Fourier blocks of the rotation-symmetric system [pole][4][c4 x c4]
   cd* Binv = nullptr;
   int nroot = 0;
+  int c4 = 0;                   // nodes per side of the symmetric root (0: dense root)
+  int* c4idx = nullptr;         // [4 * c4] wall index of side k, node s (counterclockwise)
+  int* c4inv = nullptr;         // [nroot] inverse map
+  int64_t binv_pstride = 0;     // Binv entries per pole
   int fp32 = 0;                 // leaf blocks: 0 FP64, 1 FP32, 2 FP32 pairs
   int root_fp32 = 0;            // root wall solve blocks, same code
   const void* aH = nullptr;     // operators the apply reads

@@ -228,7 +228,28 @@ struct RootArgs {
   const cd* nu;      // [P][4]
   const double* state;
   int F;
+  // rotation-symmetric root (square walled domain): nq = n / 4 nodes per side, Binv
+  // holds the four Fourier blocks [P][4][nq x nq]; c4idx[k * nq + s] is the wall
+  // index of node s of side k in counterclockwise order, c4inv its inverse.  nq = 0:
+  // Binv is the dense [P][n x n] inverse.
+  int nq = 0;
+  const int* c4idx = nullptr;
+  const int* c4inv = nullptr;
 };
+
+// sign of the wall rows of side k (S, E, N, W) relative to the rotation-covariant
+// form alpha d_n h + tau f d_t h (outward normal, counterclockwise tangent)
+__host__ __device__ __forceinline__ double c4_sign(int k) { return (k == 1 || k == 2) ? 1.0 : -1.0; }
+
+// v * i^j (j = 0..3)
+__device__ __forceinline__ cd times_ipow(cd v, int j) {
+  switch (j & 3) {
+    case 0: return v;
+    case 1: return make_double2(-v.y, v.x);
+    case 2: return make_double2(-v.x, -v.y);
+    default: return make_double2(v.y, -v.x);
+  }
+}
 
 struct LeafGeo {
   int nlx, nly, p, q;

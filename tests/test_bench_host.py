@@ -86,6 +86,10 @@ def test_class_work_counts_for_the_shallow_water_workload():
     # root wall solve: one complex multiply-add per entry of the 896 x 896 block
     assert work["root"][0] == 8.0 * P * 896 * 896
     assert work["root"][1] == P * 896 * 896 * 16 + P * 2 * 896 * 16
+    # the four Fourier blocks of the square domain: a quarter of the entries
+    w4 = bench.class_work(Op(), w, 1, "df32", fd=True, root_c4=True)
+    assert w4["root"][0] == 8.0 * P * 4 * 224 * 224
+    assert w4["root"][1] == P * 4 * 224 * 224 * 16 + P * 2 * 896 * 16
     # top up merge: ZU has n3 + nbd rows and n3 columns
     assert work["up_merge"][0] > 8.0 * P * (224 + 896) * 224
 
