@@ -97,7 +97,8 @@ class Clocks:
                 "samples": len(sm)}
 
 
-def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fitter="line", root_dense=False):
+def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fitter="line", root_dense=False,
+                   merge_dense=False):
     if w.kind == "wave":
         c = W.wave_c(w, x, y)
         if fitter == "gauss":
@@ -112,7 +113,7 @@ def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fi
     # a pole-count override (profiling cases) replaces the fixed step by tau = X(poles) / band
     return eo.Operator(g, eo.SW_WALLS, band=W.BAND[w.name], tau=0.0 if poles else w.tau, n_poles=poles,
                        f=pr["f"], g=pr["g"], H=pr["H"], shared_ops=True, max_rhs=R, precision=precision,
-                       dense_leaves=dense_leaves, fitter=fitter, root_dense=root_dense)
+                       dense_leaves=dense_leaves, fitter=fitter, root_dense=root_dense, merge_dense=merge_dense)
 
 
 def timed_steps(torch, op, u, steps, stream, dist, label="timed"):
@@ -162,11 +163,13 @@ def plan_levels(nlx, nly, q):
     return out
 
 
-def class_work(op, w, R, prec, fd, root_c4=False):
+def class_work(op, w, R, prec, fd, root_c4=False, merge_sym=False):
     """Algorithmic FP64-equivalent flops (8 per complex multiply-add) and bytes
     of one step, per kernel class, with the arithmetic precision of each.
     root_c4: the wall solve runs as four Fourier blocks of a quarter of the wall
-    nodes each (square walled domain), a quarter of the dense inverse's entries."""
+    nodes each (square walled domain), a quarter of the dense inverse's entries.
+    merge_sym: shared levels apply even/odd blocks (Z in two, U and S in four), which
+    every level of an even q has."""
     q = w.p - 2
     ni, nb = q * q, 4 * q
     P = int((op.alpha.imag >= 0).sum())
@@ -196,11 +199,15 @@ def class_work(op, w, R, prec, fd, root_c4=False):
         par = not (root and w.kind == "wave")
         zu = l["n3"] + (l["nbd"] if par else 0)
         nbo = 1 if shared else l["nbox"]
-        uf += 8.0 * P * l["nbox"] * R * zu * l["n3"]
-        ub += P * nbo * zu * l["n3"] * esz + P * l["nbox"] * R * (2 * l["n3"] + zu) * 16
+        sym = merge_sym and shared and q % 2 == 0
+        # entries of the blocks the apply reads: [-Z; U] and S, or their even/odd blocks
+        zent = (l["n3"] // 2) * (l["n3"] + (l["nbd"] // 2 if par else 0)) if sym else zu * l["n3"]
+        sent = l["n3"] * l["nbd"] // 4 if sym else l["n3"] * l["nbd"]
+        uf += 8.0 * P * l["nbox"] * R * zent
+        ub += P * nbo * zent * esz + P * l["nbox"] * R * (2 * l["n3"] + zu) * 16
         if par:
-            df += 8.0 * P * l["nbox"] * R * l["n3"] * l["nbd"]
-            db += P * nbo * l["n3"] * l["nbd"] * esz + P * l["nbox"] * R * (l["nbd"] + l["n3"]) * 16
+            df += 8.0 * P * l["nbox"] * R * sent
+            db += P * nbo * sent * esz + P * l["nbox"] * R * (l["nbd"] + l["n3"]) * 16
     work["up_merge"] = (uf, ub, prec)
     work["down_merge"] = (df, db, prec)
     if w.kind == "sw":
@@ -229,12 +236,12 @@ def alu_peak(prec):
     return {"fp32": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS, "df32": FP32_PEAK_TFLOPS / 2 / 48 * 8}[prec]
 
 
-def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False):
+def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False, merge_sym=False):
     """Per kernel class: algorithmic work of one step over that class's device
     time per step (CUDA events around its launches), against the ALU peak of
     its arithmetic and the measured HBM copy bandwidth; the class with the
     largest time share is reported as the roofline of the step."""
-    work = class_work(op, w, R, prec, fd, root_c4)
+    work = class_work(op, w, R, prec, fd, root_c4, merge_sym)
     per = {}
     for cls, (flops, nbytes, pr) in work.items():
         n, ms = tim.get(cls, (0, 0.0))
@@ -267,7 +274,9 @@ def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False):
               "peak_source": pk_kind}
     P = int((op.alpha.imag >= 0).sum())
     key = "root_dense" if top == "root" and not root_c4 else top
-    tr = NCU_TRAFFIC_151.get((w.name, prec, key)) if R == 1 and not (top.endswith("leaf")) else None
+    if merge_sym and top.endswith("merge"):
+        key = None        # the captured traffic is that of the dense merge blocks
+    tr = NCU_TRAFFIC_151.get((w.name, prec, key)) if key and R == 1 and not (top.endswith("leaf")) else None
     rf.update({"kernel": kname, "class": top, "traffic": None if tr is None else tr * P / 151,
                "traffic_note": None if tr is None else
                "ncu DRAM bytes of this class's launches in one step of the 301-pole case, scaled by P/151",
@@ -300,10 +309,12 @@ def run_ours(args):
     x, y = g.nodes()
     t0 = time.time()
     op = build_operator(eo, w, g, x, y, R, args.precision, args.poles, args.dense_leaves, args.fitter,
-                        args.root_dense)
+                        args.root_dense, args.merge_dense)
     # the library splits the wall solve of a square walled domain of square leaves into
     # four Fourier blocks unless told not to
     root_c4 = w.kind == "sw" and w.nlx == w.nly and not args.root_dense
+    # and applies the even/odd merge blocks on every level of a shared-operator grid
+    merge_sym = w.kind == "sw" and not args.merge_dense
     torch.cuda.synchronize()
     build_s = time.time() - t0
     U0 = np.stack([np.stack(W.initial_fields(w, x, y, r)) for r in range(R)])
@@ -332,7 +343,7 @@ def run_ours(args):
     fp64 = None
     if reduced and args.compare_fp64:
         op64 = build_operator(eo, w, g, x, y, R, "fp64", args.poles, args.dense_leaves, args.fitter,
-                              args.root_dense)
+                              args.root_dense, args.merge_dense)
         u64 = torch.tensor(U0, device=dev)
         for _ in range(args.warmup):
             op64.apply(u64, 1)
@@ -365,6 +376,8 @@ def run_ours(args):
         "config": {"workload": w.name, "kind": w.kind, "leaves": f"{w.nlx}x{w.nly}", "p": w.p,
                    "fitter": {"line": "least-squares pole line", "gauss": "Gaussian sums + Table 1 "
                               "(two pole lines)"}[args.fitter],
+                   "merges": ("even/odd blocks of the reflection symmetries" if merge_sym else "dense blocks")
+                   if w.kind == "sw" else "dense blocks",
                    "root": ("four Fourier blocks of the quarter-turn-symmetric wall system" if root_c4
                             else "dense wall inverse") if w.kind == "sw" else "none (Dirichlet)",
                    "precision": {"fp32": "FP32 operator blocks and products; FP64 vectors, pole sum, maps",
@@ -383,7 +396,7 @@ def run_ours(args):
         "gpu_launches": int(launches),
         "kernel_share": shares,
         "roofline": roofline(op, w, R, tim, args.precision, pk, pk_kind, fd=(w.kind == "sw" and not args.dense_leaves),
-                             root_c4=root_c4),
+                             root_c4=root_c4, merge_sym=merge_sym),
         "clocks": clocks,
     }
     if args.cpu_baseline:
@@ -645,6 +658,8 @@ def main():
     ap.add_argument("--precision", default="df32", choices=["df32", "fp32", "fp64"])
     ap.add_argument("--root-dense", action="store_true",
                     help="keep the dense wall inverse instead of the four Fourier blocks of a square domain")
+    ap.add_argument("--merge-dense", action="store_true",
+                    help="apply the dense merge blocks instead of the even/odd reflection blocks")
     ap.add_argument("--fitter", default="line", choices=["line", "gauss"],
                     help="line: our least-squares approximant; gauss: the paper's Gaussian-sum construction")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")

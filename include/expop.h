@@ -125,6 +125,13 @@ typedef struct {
                           nodes each (4x fewer root bytes and flops; the build checks
                           the symmetry to 1e-9 and fails with EO_ERR_UNSUPPORTED if it
                           does not hold).  1: keep the dense wall inverse instead   */
+  int merge_dense;     /* shared_ops without the consistent curl term: every box of a
+                          level is symmetric under the reflections across and along its
+                          merge interface, so the forward apply uses even/odd blocks
+                          of the merge operators (Z in two, U and S in four; the build
+                          checks the symmetry to 1e-9 and fails with
+                          EO_ERR_UNSUPPORTED if it does not hold; the dense blocks stay
+                          for eo_apply_adjoint).  1: dense merge blocks only        */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.

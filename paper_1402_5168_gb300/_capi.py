@@ -25,7 +25,8 @@ class Opts(C.Structure):
                 ("shared_ops", C.c_int), ("max_rhs", C.c_int), ("mem_budget_gb", C.c_double),
                 ("fp64_top_levels", C.c_int), ("use_graphs", C.c_int), ("dense_leaves", C.c_int),
                 ("autotune", C.c_int), ("sw_consistent", C.c_int), ("fitter", C.c_int),
-                ("gauss_h", C.c_double), ("root_dense", C.c_int)]
+                ("gauss_h", C.c_double), ("root_dense", C.c_int),
+                ("merge_dense", C.c_int)]
 
 
 _lib = None

@@ -144,6 +144,79 @@ bool root_c4_map(const Grid& g, const Level& rl, std::vector<int>& idx) {
   return true;
 }
 
+// Reflection maps of the first box of merge level lv (all boxes of a level share one
+// operator set, so box 0 stands for all).  Ra reflects across the interface line
+// (it swaps the children and fixes every interface node), Rb along it (interface
+// node t goes to n3 - 1 - t).  For the parent boundary: orbits {i, Ra i, Rb i, Ra Rb i}
+// with the smallest index as representative, orb[i], osg[i] = +1 on {rep, Ra rep} and -1
+// on {Rb rep, Ra Rb rep}, mem[4 r + g].  False when a reflected node is missing, an
+// orbit has fewer than four members or the interface is not symmetric.
+bool merge_sym_maps(const Grid& g, const Level& lv, bool need_par, const std::vector<double>& X,
+                    const std::vector<double>& Y, std::vector<int>& orb, std::vector<int>& osg,
+                    std::vector<int>& mem) {
+  const int q = g.q, n3 = lv.n3, nbd = lv.nbd;
+  if (n3 % 2 || (need_par && nbd % 4)) return false;
+  const double xc = g.x0 + 0.5 * lv.sx * g.hx, yc = g.y0 + 0.5 * lv.sy * g.hy;
+  const double tol = 1e-10 * std::max(g.x1 - g.x0, g.y1 - g.y0);
+  auto refl = [&](int which, double x, double y, double& rx, double& ry) {   // 0: Ra, 1: Rb
+    const bool flip_x = (lv.dir == 0) == (which == 0);
+    rx = flip_x ? 2 * xc - x : x;
+    ry = flip_x ? y : 2 * yc - y;
+  };
+  std::vector<double> ix(n3), iy(n3);
+  for (int t = 0; t < n3; ++t) {
+    const int64_t node = g.n_int + (int64_t)lv.iseg[t / q] * q + (t % q);
+    ix[t] = X[node];
+    iy[t] = Y[node];
+  }
+  for (int t = 0; t < n3; ++t) {
+    double rx, ry;
+    refl(0, ix[t], iy[t], rx, ry);
+    if (std::abs(rx - ix[t]) > tol || std::abs(ry - iy[t]) > tol) return false;
+    refl(1, ix[t], iy[t], rx, ry);
+    if (std::abs(rx - ix[n3 - 1 - t]) > tol || std::abs(ry - iy[n3 - 1 - t]) > tol) return false;
+  }
+  orb.clear(); osg.clear(); mem.clear();
+  if (!need_par) return true;
+  std::vector<double> bx(nbd), by(nbd);
+  for (int i = 0; i < nbd; ++i) {
+    const int64_t node = g.n_int + (int64_t)lv.bseg[i / q] * q + (i % q);
+    bx[i] = X[node];
+    by[i] = Y[node];
+  }
+  auto image = [&](int which, int i) {
+    double rx, ry;
+    refl(which, bx[i], by[i], rx, ry);
+    for (int j = 0; j < nbd; ++j)
+      if (std::abs(bx[j] - rx) <= tol && std::abs(by[j] - ry) <= tol) return j;
+    return -1;
+  };
+  std::vector<int> ra(nbd), rb(nbd);
+  for (int i = 0; i < nbd; ++i) {
+    ra[i] = image(0, i);
+    rb[i] = image(1, i);
+    if (ra[i] < 0 || rb[i] < 0) return false;
+  }
+  orb.assign(nbd, -1);
+  osg.assign(nbd, 0);
+  for (int i = 0; i < nbd; ++i) {
+    if (orb[i] >= 0) continue;
+    const int m4[4] = {i, ra[i], rb[i], ra[rb[i]]};
+    for (int a = 0; a < 4; ++a)
+      for (int b = a + 1; b < 4; ++b)
+        if (m4[a] == m4[b]) return false;
+    if (rb[ra[i]] != m4[3]) return false;
+    const int r = (int)mem.size() / 4;
+    for (int k = 0; k < 4; ++k) {
+      if (orb[m4[k]] >= 0) return false;
+      orb[m4[k]] = r;
+      osg[m4[k]] = k < 2 ? 1 : -1;
+      mem.push_back(m4[k]);
+    }
+  }
+  return (int)mem.size() == nbd;
+}
+
 // Position in the distinct pole list of pole j (eo_get_poles order), or -1.
 int distinct_of(const Handle& h, int j) {
   for (int d = 0; d < h.P; ++d)
@@ -241,6 +314,9 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   const int64_t P = h.P;
   int64_t ops = P * nlo * ((int64_t)nb * ni + (int64_t)ni * (ni + nb));
   h.lv.resize(L + 1);
+  std::vector<std::vector<int>> sym_orb(L + 1), sym_osg(L + 1), sym_mem(L + 1);
+  std::vector<double> gx, gy;
+  if (h.shared && !curl && !o.merge_dense) g.coords(gx, gy);
   for (int l = 1; l <= L; ++l) {
     const Level& lv = plan.lv[l];
     LevelDev& ld = h.lv[l];
@@ -255,6 +331,15 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
       ld.s_bstride = h.shared ? 0 : (int64_t)lv.n3 * lv.nbd;
       ld.s_pstride = (int64_t)nbo * lv.n3 * lv.nbd;
       ops += P * ld.s_pstride;
+    }
+    // reflection-symmetric blocks (constant coefficient: shared operators, no curl term)
+    if (!gx.empty() && merge_sym_maps(g, lv, need_par, gx, gy, sym_orb[l], sym_osg[l], sym_mem[l])) {
+      const int n3h = lv.n3 / 2, nbq = need_par ? lv.nbd / 4 : 0;
+      ld.sym = 1;
+      ld.rh = n3h + nbq;
+      ld.zs_pstride = 2LL * ld.rh * n3h;
+      ld.ss_pstride = 2LL * n3h * nbq;
+      ops += P * (ld.zs_pstride + ld.ss_pstride);
     }
   }
   std::vector<int> c4idx;
@@ -278,6 +363,15 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
     LevelDev& ld = h.lv[l];
     if ((rc = h.alloc((void**)&ld.ZU, sizeof(cd) * P * ld.zu_pstride, true))) return rc;
     if (ld.s_pstride && (rc = h.alloc((void**)&ld.S, sizeof(cd) * P * ld.s_pstride, true))) return rc;
+    if (ld.sym) {
+      if ((rc = h.alloc((void**)&ld.ZUs, sizeof(cd) * P * ld.zs_pstride, true))) return rc;
+      if (ld.ss_pstride && (rc = h.alloc((void**)&ld.Ss, sizeof(cd) * P * ld.ss_pstride, true))) return rc;
+      if (!sym_orb[l].empty()) {
+        if ((rc = upload(h, &ld.orb, sym_orb[l], st))) return rc;
+        if ((rc = upload(h, &ld.osg, sym_osg[l], st))) return rc;
+        if ((rc = upload(h, &ld.mem, sym_mem[l], st))) return rc;
+      }
+    }
   }
   if (h.kind == EO_SW_WALLS && (rc = h.alloc((void**)&h.Binv, sizeof(cd) * P * h.binv_pstride, true)))
     return rc;

@@ -114,6 +114,125 @@ __global__ void __launch_bounds__(256) k_up_merge(Sweep s, MergeArgs m, const cd
   }
 }
 
+// Up merge of a reflection-symmetric level: h3 splits into its even and odd parts
+// under the interface reversal J (e = (h3 + J h3)/2, o = (h3 - J h3)/2, first halves);
+// [-Z; U] h3 = E [-Ze e - Zo o ...]: two products with the (n3/2 + nbd/4) x n3/2 blocks,
+// then w3[s] = ye[s] + yo[s], w3[J s] = ye[s] - yo[s] and, on the parent boundary,
+// dh[i] = ye[n3/2 + orb i] + osg[i] yo[n3/2 + orb i].
+template <int NC, typename TA>
+__global__ void __launch_bounds__(256) k_up_merge_sym(Sweep s, MergeArgs m, const cd* __restrict__ hin,
+                                                      cd* __restrict__ hout) {
+  extern __shared__ cd smem[];
+  const int pl = blockIdx.y, p = s.p0 + pl;
+  const int ncols = m.nbox * s.R;
+  const int c0 = blockIdx.x * NC;
+  const int n3 = m.n3, n3h = m.n3h, rh = m.rh;
+  TA* Bs = (TA*)smem;
+  cd* Cs = after(Bs, (size_t)NC * n3);
+  cd* red = Cs + 2 * NC * rh;
+  for (int e = threadIdx.x; e < NC * n3h; e += blockDim.x) {
+    const int c = e / n3h, t = e - c * n3h;
+    cd ev = make_double2(0.0, 0.0), od = make_double2(0.0, 0.0);
+    if (c0 + c < ncols) {
+      int box, r, ca, cb;
+      col_box(c0 + c, s.R, box, r);
+      children(m, box, ca, cb);
+      const cd* hr = hin + ((long long)pl * s.R + r) * m.nbox_c * m.nbd_c;
+      const int tj = n3 - 1 - t;
+      const cd x1 = hr[(long long)ca * m.nbd_c + m.a3[t]], y1 = hr[(long long)cb * m.nbd_c + m.b3[t]];
+      const cd x2 = hr[(long long)ca * m.nbd_c + m.a3[tj]], y2 = hr[(long long)cb * m.nbd_c + m.b3[tj]];
+      const double ar = x1.x + y1.x, ai = x1.y + y1.y, br = x2.x + y2.x, bi = x2.y + y2.y;
+      ev = make_double2(0.5 * (ar + br), 0.5 * (ai + bi));
+      od = make_double2(0.5 * (ar - br), 0.5 * (ai - bi));
+    }
+    Bs[c * n3 + t] = Cv<TA>::from(ev);
+    Bs[c * n3 + n3h + t] = Cv<TA>::from(od);
+  }
+  __syncthreads();
+  const TA* A = (const TA*)m.ZUs + (long long)p * m.zsps;
+  cmv<NC, TA>(A, rh, rh, n3h, Bs, n3, Cs, red);
+  cmv<NC, TA>(A + (long long)rh * n3h, rh, rh, n3h, Bs + n3h, n3, Cs + (size_t)NC * rh, red);
+  const cd* Ce = Cs;
+  const cd* Co = Cs + (size_t)NC * rh;
+  for (int e = threadIdx.x; e < NC * m.zu_rows; e += blockDim.x) {
+    const int c = e / m.zu_rows, row = e - c * m.zu_rows;
+    if (c0 + c >= ncols) continue;
+    int box, r;
+    col_box(c0 + c, s.R, box, r);
+    if (row < n3) {
+      const int sr = row < n3h ? row : n3 - 1 - row;
+      const double sg = row < n3h ? 1.0 : -1.0;
+      const cd a = Ce[c * rh + sr], b = Co[c * rh + sr];
+      m.w3[(((long long)pl * s.R + r) * m.nbox + box) * n3 + row] = make_double2(a.x + sg * b.x, a.y + sg * b.y);
+    } else {
+      const int i = row - n3;
+      const int k = n3h + m.orb[i];
+      const double sg = (double)m.osg[i];
+      const cd a = Ce[c * rh + k], b = Co[c * rh + k];
+      int ca, cb;
+      children(m, box, ca, cb);
+      const cd* hr = hin + ((long long)pl * s.R + r) * m.nbox_c * m.nbd_c;
+      const cd x = hr[(long long)(m.par_child[i] ? cb : ca) * m.nbd_c + m.par_idx[i]];
+      hout[(((long long)pl * s.R + r) * m.nbox + box) * m.nbd + i] =
+          make_double2(x.x + a.x + sg * b.x, x.y + a.y + sg * b.y);
+    }
+  }
+}
+
+// Down merge of a reflection-symmetric level: the parent boundary values u enter S
+// only through the orbit sums a_r = sum_g u[mem[4r+g]] and b_r = sum_g osg u[mem[4r+g]];
+// u3[s] = (Se a)[s] + (So b)[s] + w3[s], u3[J s] = (Se a)[s] - (So b)[s] + w3[J s].
+template <int NC, typename TA>
+__global__ void __launch_bounds__(256) k_down_merge_sym(Sweep s, MergeArgs m, cd* __restrict__ E) {
+  extern __shared__ cd smem[];
+  const int pl = blockIdx.y, p = s.p0 + pl;
+  const int ncols = m.nbox * s.R;
+  const int c0 = blockIdx.x * NC;
+  const int n3 = m.n3, n3h = m.n3h, nbq = m.nbq;
+  const int q = s.q;
+  TA* Bs = (TA*)smem;
+  cd* Cs = after(Bs, (size_t)NC * 2 * nbq);
+  cd* red = Cs + NC * n3;
+  for (int e = threadIdx.x; e < NC * nbq; e += blockDim.x) {
+    const int c = e / nbq, r = e - c * nbq;
+    cd a = make_double2(0.0, 0.0), b = make_double2(0.0, 0.0);
+    if (c0 + c < ncols) {
+      int box, rr;
+      col_box(c0 + c, s.R, box, rr);
+      const cd* Er = E + ((long long)pl * s.R + rr) * s.n_edge;
+#pragma unroll
+      for (int g = 0; g < 4; ++g) {
+        const int i = m.mem[4 * r + g];
+        const cd v = Er[(long long)m.bseg[box * m.nseg + i / q] * q + (i % q)];
+        const double sg = g < 2 ? 1.0 : -1.0;
+        a.x += v.x; a.y += v.y;
+        b.x += sg * v.x; b.y += sg * v.y;
+      }
+    }
+    Bs[c * 2 * nbq + r] = Cv<TA>::from(a);
+    Bs[c * 2 * nbq + nbq + r] = Cv<TA>::from(b);
+  }
+  __syncthreads();
+  const TA* A = (const TA*)m.Ss + (long long)p * m.ssps;
+  cmv<NC, TA>(A, n3h, n3h, nbq, Bs, 2 * nbq, Cs, red);
+  cmv<NC, TA>(A + (long long)n3h * nbq, n3h, n3h, nbq, Bs + nbq, 2 * nbq, Cs + (size_t)NC * n3h, red);
+  const cd* Ce = Cs;
+  const cd* Co = Cs + (size_t)NC * n3h;
+  const int n3s = n3 / q;
+  for (int e = threadIdx.x; e < NC * n3; e += blockDim.x) {
+    const int c = e / n3, row = e - c * n3;
+    if (c0 + c >= ncols) continue;
+    int box, r;
+    col_box(c0 + c, s.R, box, r);
+    const int sr = row < n3h ? row : n3 - 1 - row;
+    const double sg = row < n3h ? 1.0 : -1.0;
+    const cd a = Ce[c * n3h + sr], b = Co[c * n3h + sr];
+    const cd w = m.w3[(((long long)pl * s.R + r) * m.nbox + box) * n3 + row];
+    E[((long long)pl * s.R + r) * s.n_edge + (long long)m.iseg[box * n3s + row / q] * q + (row % q)] =
+        make_double2(w.x + a.x + sg * b.x, w.y + a.y + sg * b.y);
+  }
+}
+
 // ---------------------------------------------------------------- root (walls)
 template <int NC, typename TA>
 __global__ void __launch_bounds__(256) k_root_sw(Sweep s, RootArgs ra, const cd* __restrict__ hroot,
@@ -650,6 +769,12 @@ struct UpMerge {
   static eo_status run(const Sweep& s, const MergeArgs& m, const cd* hin, cd* hout, int nt, cudaStream_t st) {
     dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
     const size_t smem = sizeof(cd) * ((size_t)NC * (m.n3 + m.zu_rows) + 256 * NC) + 64;
+    if (m.sym) {
+      EO_SET_SMEM((k_up_merge_sym<NC, TA>), smem);
+      k_up_merge_sym<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(m.rh), smem, st>>>(s, m, hin, hout);
+      EO_CUDA_TRY(cudaGetLastError());
+      return EO_OK;
+    }
     EO_SET_SMEM((k_up_merge<NC, TA>), smem);
     k_up_merge<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(m.zu_rows), smem, st>>>(s, m, hin, hout);
     EO_CUDA_TRY(cudaGetLastError());
@@ -662,6 +787,12 @@ struct DownMerge {
   static eo_status run(const Sweep& s, const MergeArgs& m, cd* E, int nt, cudaStream_t st) {
     dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
     const size_t smem = sizeof(cd) * ((size_t)NC * (m.nbd + m.n3) + 256 * NC) + 64;
+    if (m.sym && m.Ss) {
+      EO_SET_SMEM((k_down_merge_sym<NC, TA>), smem);
+      k_down_merge_sym<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(m.n3h), smem, st>>>(s, m, E);
+      EO_CUDA_TRY(cudaGetLastError());
+      return EO_OK;
+    }
     EO_SET_SMEM((k_down_merge<NC, TA>), smem);
     k_down_merge<NC, TA><<<grid, nt > 0 ? nt : (m.S ? cmv_threads(m.n3) : 256), smem, st>>>(s, m, E);
     EO_CUDA_TRY(cudaGetLastError());
@@ -715,6 +846,11 @@ MergeArgs merge_args(const Handle& h, int l) {
   m.ZU = ld.aZU; m.zps = ld.zu_pstride; m.zbs = ld.zu_bstride;
   m.S = ld.aS; m.sps = ld.s_pstride; m.sbs = ld.s_bstride;
   m.bseg = ld.bseg; m.iseg = ld.iseg; m.nseg = ld.nseg; m.w3 = ld.w3;
+  if (ld.sym) {
+    m.sym = 1; m.n3h = ld.n3 / 2; m.rh = ld.rh; m.nbq = ld.rh - ld.n3 / 2;
+    m.ZUs = ld.aZUs; m.zsps = ld.zs_pstride; m.Ss = ld.aSs; m.ssps = ld.ss_pstride;
+    m.orb = ld.orb; m.osg = ld.osg; m.mem = ld.mem;
+  }
   return m;
 }
 
@@ -941,7 +1077,7 @@ eo_status autotune(Handle& h, int R, cudaStream_t st) {
     LevelDev& ld = h.lv[l];
     float best = 1e30f;
     for (int nc : nc_list(m.nbox, m.n3, m.zu_rows))
-      for (int nt : nt_list(m.zu_rows)) {
+      for (int nt : nt_list(m.sym ? m.rh : m.zu_rows)) {
         const float t = timeit([&] { return dispatch<UpMerge>(ld.fp32, nc, s, m, h.hA, h.hB, nt, st); });
         if (t < 0) return fail(EO_ERR_CUDA, "autotune: merge launch failed");
         if (t < best) { best = t; ld.up = Tuned{nc, nt}; }
@@ -949,7 +1085,7 @@ eo_status autotune(Handle& h, int R, cudaStream_t st) {
     if (!m.S) continue;
     best = 1e30f;
     for (int nc : nc_list(m.nbox, m.nbd, m.n3))
-      for (int nt : nt_list(m.n3)) {
+      for (int nt : nt_list(m.sym && m.Ss ? m.n3h : m.n3)) {
         const float t = timeit([&] { return dispatch<DownMerge>(ld.fp32, nc, s, m, h.E, nt, st); });
         if (t < 0) return fail(EO_ERR_CUDA, "autotune: merge launch failed");
         if (t < best) { best = t; ld.down = Tuned{nc, nt}; }

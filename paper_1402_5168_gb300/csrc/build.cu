@@ -325,6 +325,82 @@ __global__ void root_c4_blocks(int nbatch, int n, int nq, const int* __restrict_
   atomicMax(&stat[1], (unsigned long long)__double_as_longlong(bmax));
 }
 
+// Even/odd blocks of a reflection-symmetric merge level (shared operators).  With Rb
+// reversing the interface (t -> n3 - 1 - t) and the parent-boundary orbits mem[4 r + g]
+// (g: 1, Ra, Rb, Ra Rb), for s, t < n3/2 and blk 0 (even, +) or 1 (odd, -):
+//   Z rows:  ZUs[blk][s][t] = mean of ZU[s][t] +- ZU[s][Jt] and ZU[Js][Jt] +- ZU[Js][t],
+//   U rows:  ZUs[blk][n3/2 + r][t] = mean over g of f_g (U[i_g][t] +- U[i_g][Jt]),
+//   S:       Ss[blk][s][r] = mean over g of f_g (S[s][i_g] +- S[Js][i_g]) / 2,
+// with f_g = -1 for the odd block on g = Rb, Ra Rb and +1 otherwise.  The largest
+// deviation of one estimate from its mean and the largest |entry| read go to stat[0..1].
+// ZU: [nbatch][zr x n3], S: [nbatch][n3 x nbd] column-major; ZUs [nbatch][2][rh x n3/2],
+// Ss [nbatch][2][n3/2 x nbd/4].
+__global__ void merge_sym_blocks(int nbatch, int n3, int nbd, int rh, int need_par, const int* __restrict__ mem,
+                                 const cd* __restrict__ ZU, const cd* __restrict__ S, cd* __restrict__ ZUs,
+                                 cd* __restrict__ Ss, unsigned long long* stat) {
+  const int n3h = n3 / 2, nbq = need_par ? nbd / 4 : 0, zr = n3 + (need_par ? nbd : 0);
+  const size_t zb = (size_t)rh * n3h, sb = (size_t)n3h * nbq;
+  const size_t zper = 2 * zb, sper = 2 * sb, per = zper + sper;
+  double dev = 0.0, amax = 0.0;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)nbatch * per;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t gi = t / per, e = t % per;
+    cd est[4];
+    int ne = 0;
+    if (e < zper) {
+      const int blk = (int)(e / zb);
+      const size_t f = e % zb;
+      const int rho = (int)(f % rh), col = (int)(f / rh), tj = n3 - 1 - col;
+      const double sg = blk ? -1.0 : 1.0;
+      const cd* Zg = ZU + gi * (size_t)zr * n3;
+      if (rho < n3h) {
+        const int sr = rho, js = n3 - 1 - rho;
+        const cd a = Zg[sr + (size_t)col * zr], b = Zg[sr + (size_t)tj * zr];
+        const cd c = Zg[js + (size_t)tj * zr], d = Zg[js + (size_t)col * zr];
+        est[0] = make_double2(a.x + sg * b.x, a.y + sg * b.y);
+        est[1] = make_double2(c.x + sg * d.x, c.y + sg * d.y);
+        ne = 2;
+        amax = fmax(amax, fmax(fmax(fabs(a.x), fabs(a.y)), fmax(fabs(c.x), fabs(c.y))));
+      } else {
+        const int r = rho - n3h;
+        for (int g = 0; g < 4; ++g) {
+          const int i = mem[4 * r + g];
+          const double fg = (blk && g >= 2) ? -1.0 : 1.0;
+          const cd a = Zg[n3 + i + (size_t)col * zr], b = Zg[n3 + i + (size_t)tj * zr];
+          est[g] = make_double2(fg * (a.x + sg * b.x), fg * (a.y + sg * b.y));
+          amax = fmax(amax, fmax(fabs(a.x), fabs(a.y)));
+        }
+        ne = 4;
+      }
+      cd mean = make_double2(0.0, 0.0);
+      for (int k = 0; k < ne; ++k) { mean.x += est[k].x / ne; mean.y += est[k].y / ne; }
+      for (int k = 0; k < ne; ++k) dev = fmax(dev, fmax(fabs(est[k].x - mean.x), fabs(est[k].y - mean.y)));
+      ZUs[gi * zper + blk * zb + rho + (size_t)col * rh] = mean;
+    } else {
+      const size_t e2 = e - zper;
+      const int blk = (int)(e2 / sb);
+      const size_t f = e2 % sb;
+      const int sr = (int)(f % n3h), r = (int)(f / n3h), js = n3 - 1 - sr;
+      const double sg = blk ? -1.0 : 1.0;
+      const cd* Sg = S + gi * (size_t)n3 * nbd;
+      cd mean = make_double2(0.0, 0.0);
+      for (int g = 0; g < 4; ++g) {
+        const int i = mem[4 * r + g];
+        const double fg = (blk && g >= 2) ? -0.5 : 0.5;
+        const cd a = Sg[sr + (size_t)i * n3], b = Sg[js + (size_t)i * n3];
+        est[g] = make_double2(fg * (a.x + sg * b.x), fg * (a.y + sg * b.y));
+        mean.x += 0.25 * est[g].x;
+        mean.y += 0.25 * est[g].y;
+        amax = fmax(amax, fmax(fabs(a.x), fabs(a.y)));
+      }
+      for (int g = 0; g < 4; ++g) dev = fmax(dev, fmax(fabs(est[g].x - mean.x), fabs(est[g].y - mean.y)));
+      Ss[gi * sper + blk * sb + sr + (size_t)r * n3h] = mean;
+    }
+  }
+  atomicMax(&stat[0], (unsigned long long)__double_as_longlong(dev));
+  atomicMax(&stat[1], (unsigned long long)__double_as_longlong(amax));
+}
+
 namespace {
 
 struct Cublas {
@@ -447,6 +523,8 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
   }
   cd* c4w = nullptr;
   unsigned long long* c4stat = nullptr;
+  unsigned long long* symstat = nullptr;
+  if ((rc = talloc((void**)&symstat, sizeof(unsigned long long) * 2))) return rc;
   if (h.kind == EO_SW_WALLS) {
     maxpiv = std::max(maxpiv, (size_t)G * h.nroot);
     maxinfo = std::max(maxinfo, (size_t)G * (h.c4 ? 4 : 1));
@@ -571,6 +649,24 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
                                                   (cuDoubleComplex*)Tw, npar, (long long)npar * npar, nbt));
         }
       }
+      if (ld.sym) {
+        EO_CUDA_TRY(cudaMemsetAsync(symstat, 0, sizeof(unsigned long long) * 2, st));
+        merge_sym_blocks<<<2048, 256, 0, st>>>(g, n3, npar, ld.rh, need_par ? 1 : 0, ld.mem, ZUp,
+                                               need_par ? ld.S + (size_t)p0 * ld.s_pstride : nullptr,
+                                               ld.ZUs + (size_t)p0 * ld.zs_pstride,
+                                               ld.Ss ? ld.Ss + (size_t)p0 * ld.ss_pstride : nullptr, symstat);
+        EO_CUDA_TRY(cudaGetLastError());
+        unsigned long long hs[2];
+        EO_CUDA_TRY(cudaMemcpyAsync(hs, symstat, sizeof(hs), cudaMemcpyDeviceToHost, st));
+        EO_CUDA_TRY(cudaStreamSynchronize(st));
+        double dev, amax;
+        std::memcpy(&dev, &hs[0], sizeof(double));
+        std::memcpy(&amax, &hs[1], sizeof(double));
+        if (!(dev <= 1e-9 * amax))
+          return fail(EO_ERR_UNSUPPORTED, "merge level " + std::to_string(l) +
+                                              " is not reflection-symmetric (deviation " +
+                                              std::to_string(dev / amax) + "); set opts.merge_dense");
+      }
       Tprev = Tw;
       nbd_prev = npar;
       nbo_prev = nbo;
@@ -612,6 +708,8 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
   for (size_t l = 1; l < h.lv.size(); ++l) {
     h.lv[l].aZU = h.lv[l].ZU;
     h.lv[l].aS = h.lv[l].S;
+    h.lv[l].aZUs = h.lv[l].ZUs;
+    h.lv[l].aSs = h.lv[l].Ss;
   }
   return EO_OK;
 }
@@ -661,6 +759,8 @@ eo_status to_reduced(Handle& h, int prec, cudaStream_t st) {
     LevelDev& ld = h.lv[l];
     if ((rc = conv(ld.ZU, P * ld.zu_pstride, &ld.aZU))) return rc;
     if ((rc = conv(ld.S, P * ld.s_pstride, &ld.aS))) return rc;
+    if ((rc = conv(ld.ZUs, P * ld.zs_pstride, &ld.aZUs))) return rc;
+    if ((rc = conv(ld.Ss, P * ld.ss_pstride, &ld.aSs))) return rc;
     ld.fp32 = prec;
   }
   if (keep == 0) {

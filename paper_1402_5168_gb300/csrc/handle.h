@@ -62,6 +62,18 @@ struct LevelDev {
   const void* aS = nullptr;
   int fp32 = 0;                 // this level's blocks: 0 FP64, 1 FP32, 2 FP32 pairs
   Tuned up, down;               // autotuned launch shapes of the merge kernels
+  // reflection-symmetric blocks of the forward apply (shared operators; the dense
+  // ZU and S stay for the transposed sweeps): ZUs [pole][2][rh x n3/2], Ss
+  // [pole][2][n3/2 x nbd/4], orbit maps of the box boundary
+  int sym = 0, rh = 0;
+  cd* ZUs = nullptr;
+  cd* Ss = nullptr;
+  int64_t zs_pstride = 0, ss_pstride = 0;
+  int* orb = nullptr;           // [nbd]
+  int* osg = nullptr;           // [nbd]
+  int* mem = nullptr;           // [nbd] = [nbd/4][4]
+  const void* aZUs = nullptr;
+  const void* aSs = nullptr;
 };
 
 struct Handle {

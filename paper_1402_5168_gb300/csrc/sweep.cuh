@@ -212,6 +212,21 @@ struct MergeArgs {
   const int* iseg;
   int nseg;
   cd* w3;
+  // reflection-symmetric level (constant coefficient, shared operators): the box
+  // is symmetric under Ra (across the interface line; swaps the children, fixes
+  // the interface) and Rb (along it; reverses the interface, t -> n3 - 1 - t).
+  // ZUs: [P][2][rh x n3h] (even, odd; rows n3h of -Z then nbq of U), Ss:
+  // [P][2][n3h x nbq]; orbit maps of the parent boundary under {1, Ra, Rb, RaRb}:
+  // orb[i] (orbit), osg[i] (+1 for i = rep or Ra rep, -1 for Rb rep, Ra Rb rep),
+  // mem[4 r + g] (members).
+  int sym = 0, n3h = 0, nbq = 0, rh = 0;
+  const void* ZUs = nullptr;
+  long long zsps = 0;
+  const void* Ss = nullptr;
+  long long ssps = 0;
+  const int* orb = nullptr;
+  const int* osg = nullptr;
+  const int* mem = nullptr;
 };
 
 __device__ __forceinline__ void children(const MergeArgs& m, int box, int& ca, int& cb) {
