@@ -242,18 +242,24 @@ eo_status eo_apply_resolvent(eo_handle_t h, int j, const double *u_dev, double *
                              void *stream);
 
 /* eo_apply_resolvent without any device allocation.  The paper has no
- * counterpart: this exists for callers that cannot allocate device memory when
- * they call (code recording a CUDA graph capture, threads that must not touch
- * the allocator, hosts that give the whole GPU to their own memory pool).
- * Scratch comes from one fixed 16 MiB array in device memory that every GPU
- * loading the library holds until exit; problems needing more
- * (2 * P * K + 2 * fields * n_nodes doubles, P distinct poles, K = 2 wave / 3
- * shallow water) are rejected with EO_ERR_INVALID_ARG.  The first call on a
- * device looks the array's device address up (cudaGetSymbolAddress) with that
- * device current; make that first call before any stream capture.  All calls
- * share the array: calls whose work can overlap on the GPU race on it, so order
- * them on one stream.  Arguments and result as eo_apply_resolvent; the call
- * synchronises the stream before returning. */
+ * counterpart.  It exists for callers that cannot allocate device memory when
+ * they call: host threads that must stay off the device allocator (cudaMalloc
+ * takes process-wide locks and may synchronise the device), and programs that
+ * hand all of the GPU's memory to their own pool, so that any other allocation
+ * fails.  The caller passes the input and output; the scratch (the pole's K
+ * weights and the real and imaginary staging of the result) comes from one
+ * fixed 16 MiB array in device memory (a file-scope __device__ array of
+ * 2 Mi doubles) that every GPU loading the library holds until the process
+ * exits.  Problems needing more than 16 + 2 * fields * n_nodes doubles of it are
+ * rejected with EO_ERR_INVALID_ARG.  The first call on a device looks the
+ * array's device address up (cudaGetSymbolAddress) with that device current;
+ * make that first call before any stream capture.  Every call shares the array
+ * and keeps the previous call's contents (each call rewrites the weights on the
+ * device before reading them): calls whose work can overlap on the GPU race on
+ * it, so order them on one stream.  Arguments and result as eo_apply_resolvent;
+ * stream-ordered and asynchronous: x_dev holds the result once `stream` has
+ * reached the end of the call's work.  No cudaMalloc, cudaFree or allocating
+ * library routine is called. */
 eo_status eo_apply_resolvent_noalloc(eo_handle_t h, int j, const double *u_dev, double *x_dev,
                                      void *stream);
 

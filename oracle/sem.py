@@ -14,10 +14,15 @@ tutorial).
 Public node numbering (an interface; the GPU library implements it on its own):
   interior: leaf l = b*nlx + a, local node (k, j), k, j = 1..q (q = p-2):
         id = l*q*q + (j-1)*q + (k-1)
-  horizontal edge segments (y = const): line e = 0..nly, leaf column a:
+  horizontal edge segments (y = const): line e = 0..nhl-1, leaf column a:
         id = n_int + (e*nlx + a)*q + (k-1)
-  vertical edge segments (x = const): line e = 0..nlx, leaf row b:
-        id = n_int + n_h + (b*(nlx+1) + e)*q + (j-1)
+  vertical edge segments (x = const): line e = 0..nvl-1, leaf row b:
+        id = n_int + n_h + (b*nvl + e)*q + (j-1)
+with nhl = nly + 1 and nvl = nlx + 1 lines on a walled square.  On a periodic
+square (the setting of the paper's examples, Section 4) the lines y = y1 and
+x = x1 are the lines y = y0 and x = x0: nhl = nly, nvl = nlx, the top edge of
+leaf row nly-1 is line 0 and the right edge of leaf column nlx-1 is line 0, and
+every edge node is an interface node (no domain boundary).
 """
 from __future__ import annotations
 
@@ -52,11 +57,15 @@ def diff_matrix(x: np.ndarray) -> np.ndarray:
 class Grid:
     """Leaf grid, node coordinates and the public node numbering."""
 
-    def __init__(self, nlx: int, nly: int, p: int, x0=0.0, x1=1.0, y0=0.0, y1=1.0):
+    def __init__(self, nlx: int, nly: int, p: int, x0=0.0, x1=1.0, y0=0.0, y1=1.0,
+                 periodic: bool = False):
         if p < 4:
             raise ValueError("p must be >= 4")
         self.nlx, self.nly, self.p, self.q = nlx, nly, p, p - 2
         self.x0, self.x1, self.y0, self.y1 = x0, x1, y0, y1
+        self.periodic = bool(periodic)
+        self.nhl = nly if self.periodic else nly + 1     # horizontal edge lines
+        self.nvl = nlx if self.periodic else nlx + 1     # vertical edge lines
         self.hx = (x1 - x0) / nlx
         self.hy = (y1 - y0) / nly
         self.xi = cheb_points(p)
@@ -69,8 +78,8 @@ class Grid:
         q = self.q
         self.n_leaf = nlx * nly
         self.n_int = self.n_leaf * q * q
-        self.n_hseg = nlx * (nly + 1)
-        self.n_vseg = (nlx + 1) * nly
+        self.n_hseg = nlx * self.nhl
+        self.n_vseg = self.nvl * nly
         self.n_h = self.n_hseg * q
         self.n_v = self.n_vseg * q
         self.n_nodes = self.n_int + self.n_h + self.n_v
@@ -87,11 +96,11 @@ class Grid:
         if kin and jin:
             return (b * self.nlx + a) * q * q + (j - 1) * q + (k - 1)
         if kin:
-            e = b if j == 0 else b + 1
+            e = b if j == 0 else (b + 1) % self.nhl
             return self.n_int + (e * self.nlx + a) * q + (k - 1)
         if jin:
-            e = a if k == 0 else a + 1
-            return self.n_int + self.n_h + (b * (self.nlx + 1) + e) * q + (j - 1)
+            e = a if k == 0 else (a + 1) % self.nvl
+            return self.n_int + self.n_h + (b * self.nvl + e) * q + (j - 1)
         return -1
 
     def _leaf_ids(self, a, b):
@@ -110,6 +119,10 @@ class Grid:
                 ids = self.leaf_ids(a, b)
                 X = self.x0 + (a + 0.5 * (self.xi[None, :] + 1)) * self.hx
                 Y = self.y0 + (b + 0.5 * (self.xi[:, None] + 1)) * self.hy
+                if self.periodic:
+                    # the seam lines x = x1, y = y1 are the lines x = x0, y = y0
+                    X = np.where(np.isclose(X, self.x1, rtol=0, atol=1e-14 * self.hx), self.x0, X)
+                    Y = np.where(np.isclose(Y, self.y1, rtol=0, atol=1e-14 * self.hy), self.y0, Y)
                 m = ids >= 0
                 x[ids[m]] = np.broadcast_to(X, ids.shape)[m]
                 y[ids[m]] = np.broadcast_to(Y, ids.shape)[m]
@@ -119,13 +132,17 @@ class Grid:
         return self.n_int + (e * self.nlx + a) * self.q + np.arange(self.q)
 
     def vseg_ids(self, b: int, e: int) -> np.ndarray:
-        return self.n_int + self.n_h + (b * (self.nlx + 1) + e) * self.q + np.arange(self.q)
+        return self.n_int + self.n_h + (b * self.nvl + e) * self.q + np.arange(self.q)
 
     def classify(self):
         """Per node: 0 interior, 1 interface, 2 domain boundary; wall side
-        (0 south, 1 east, 2 north, 3 west; -1 elsewhere)."""
+        (0 south, 1 east, 2 north, 3 west; -1 elsewhere).  A periodic grid has
+        no domain boundary: every edge node is an interface node."""
         cls = np.zeros(self.n_nodes, dtype=int)
         side = np.full(self.n_nodes, -1)
+        if self.periodic:
+            cls[self.n_int:] = 1
+            return cls, side
         for e in range(self.nly + 1):
             for a in range(self.nlx):
                 ids = self.hseg_ids(e, a)
@@ -188,22 +205,25 @@ def flux_continuity_rows(g: Grid, a: np.ndarray) -> sp.csr_matrix:
     """Rows imposing continuity of the normal flux a du/dn at interface nodes.
 
     The outward fluxes of the two leaves sharing the node, each evaluated by
-    spectral differentiation on its own leaf, sum to zero (Section 2.2).
+    spectral differentiation on its own leaf, sum to zero (Section 2.2).  On a
+    periodic grid the seams x = x0 and y = y0 are interfaces too, between the
+    last and the first leaf of each row or column.
     """
     p = g.p
     rows, cols, vals = [], [], []
+    e0 = 0 if g.periodic else 1
     for b in range(g.nly):                      # vertical interfaces x = const
-        for e in range(1, g.nlx):
-            L = g.leaf_ids(e - 1, b)
+        for e in range(e0, g.nlx):
+            L = g.leaf_ids((e - 1) % g.nlx, b)
             R = g.leaf_ids(e, b)
             for j in range(1, p - 1):
                 r = L[j, p - 1]
                 rows.append(np.full(2 * p, r))
                 cols.append(np.concatenate([L[j, :], R[j, :]]))
                 vals.append(a[r] * np.concatenate([g.Dx[p - 1, :], -g.Dx[0, :]]))
-    for e in range(1, g.nly):                   # horizontal interfaces y = const
+    for e in range(e0, g.nly):                  # horizontal interfaces y = const
         for a_ in range(g.nlx):
-            B = g.leaf_ids(a_, e - 1)
+            B = g.leaf_ids(a_, (e - 1) % g.nly)
             T = g.leaf_ids(a_, e)
             for k in range(1, p - 1):
                 r = B[p - 1, k]
@@ -218,10 +238,14 @@ def wall_gradient_rows(g: Grid):
 
     Normal component: one-sided spectral derivative on the single adjacent
     leaf.  Tangential component: derivative of the interpolant through the
-    p-2 non-corner nodes of that leaf edge.  Rows vanish off the boundary.
+    p-2 non-corner nodes of that leaf edge.  Rows vanish off the boundary
+    (everywhere on a periodic grid).
     """
     p = g.p
     rx, cx, vx, ry, cy, vy = [], [], [], [], [], []
+    if g.periodic:
+        n = g.n_nodes
+        return _coo(rx, cx, vx, n), _coo(ry, cy, vy, n)
     for b in range(g.nly):
         for a_, kk in ((0, 0), (g.nlx - 1, p - 1)):
             ids = g.leaf_ids(a_, b)
@@ -276,12 +300,12 @@ def gradient(g: Grid, u: np.ndarray):
     ux[e_] /= cnt_x[e_]
     e_ = cnt_y > 0
     uy[e_] /= cnt_y[e_]
-    for e in range(g.nly + 1):
+    for e in range(g.nhl):
         for a_ in range(g.nlx):
             ids = g.hseg_ids(e, a_)
             ux[ids] = g.Ex @ u[ids]
     for b in range(g.nly):
-        for e in range(g.nlx + 1):
+        for e in range(g.nvl):
             ids = g.vseg_ids(b, e)
             uy[ids] = g.Ey @ u[ids]
     return ux, uy
@@ -321,7 +345,7 @@ def gradient_matrices(g: Grid):
     Gy = sp.diags(sy) @ Gy.tocsr()
     Gx, Gy = Gx.tolil(), Gy.tolil()
     # tangential components on edges: rows replaced by the edge-interpolant derivative
-    for e in range(g.nly + 1):
+    for e in range(g.nhl):
         for a_ in range(g.nlx):
             ids = g.hseg_ids(e, a_)
             for t, r in enumerate(ids):
@@ -330,7 +354,7 @@ def gradient_matrices(g: Grid):
                 for m, c in enumerate(ids):
                     Gx[r, c] = g.Ex[t, m]
     for b in range(g.nly):
-        for e in range(g.nlx + 1):
+        for e in range(g.nvl):
             ids = g.vseg_ids(b, e)
             for t, r in enumerate(ids):
                 Gy.rows[r] = []

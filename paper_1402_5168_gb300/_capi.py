@@ -10,6 +10,7 @@ LIB_PATH = os.path.join(HERE, "_build", "libexpop.so")
 EO_OK = 0
 STATUS = {0: "EO_OK", 1: "EO_ERR_INVALID_ARG", 2: "EO_ERR_FIT", 3: "EO_ERR_SINGULAR", 4: "EO_ERR_OOM",
           5: "EO_ERR_BUDGET", 6: "EO_ERR_CUDA", 7: "EO_ERR_TIMEOUT", 8: "EO_ERR_UNSUPPORTED"}
+STATUS_CODES = {v: k for k, v in STATUS.items()}
 WAVE_DIRICHLET, SW_WALLS = 0, 1
 
 # every symbol include/expop.h declares

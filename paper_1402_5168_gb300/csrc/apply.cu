@@ -1246,40 +1246,62 @@ eo_status batch_apply(Batch& b, int n_steps, cudaStream_t st) {
   return EO_OK;
 }
 
+// Weights of the two runs of one resolvent: pole j alone with weight c = 1 (real
+// part) or c = -i (imaginary part); w[k] are the K accumulation weights of that
+// pole and C the post-map constants.
+static void resolvent_weights(const Handle& h, int j, std::complex<double> c, cd w[3], double C[4]) {
+  const std::complex<double> al = h.alpha[j];
+  for (int k = 0; k < 3; ++k) w[k] = make_double2(0.0, 0.0);
+  for (int k = 0; k < 4; ++k) C[k] = 0.0;
+  if (h.kind == EO_WAVE_DIRICHLET) {
+    const std::complex<double> w0 = c, w1 = c * h.tau / al;
+    w[0] = make_double2(w0.real(), w0.imag());
+    w[1] = make_double2(w1.real(), w1.imag());
+    C[0] = (c / al).real();
+  } else {
+    const double tf = h.tau * h.opts.sw_f;
+    const std::complex<double> D = al * al + tf * tf;
+    const std::complex<double> w0 = c, w1 = c * (-al / D), w2 = c * (-tf / D);
+    w[0] = make_double2(w0.real(), w0.imag());
+    w[1] = make_double2(w1.real(), w1.imag());
+    w[2] = make_double2(w2.real(), w2.imag());
+    C[0] = w1.real();
+    C[1] = w2.real();
+  }
+}
+
 // x = (tau L - alpha_j)^{-1} u: the pole-sum pipeline run for pole j alone with
 // weight 1 (real part) and weight -i (imaginary part); every post-map is linear
 // with real coefficients in (weight * solution), so the two runs give Re and Im.
+// The two scratch buffers are stream-ordered allocations, released on every exit.
 eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStream_t st) {
   if (j < 0 || j >= h.P) return fail(EO_ERR_INVALID_ARG, "pole index out of range");
-  const std::complex<double> al = h.alpha[j];
   const std::complex<double> ws[2] = {1.0, std::complex<double>(0.0, -1.0)};
   const size_t nst = (size_t)h.F * h.g.n_nodes;
-  double* tmpw;
-  double* outb;
-  EO_CUDA_TRY(cudaMallocAsync(&tmpw, sizeof(cd) * h.P * h.K, st));
-  EO_CUDA_TRY(cudaMallocAsync(&outb, sizeof(double) * nst * 2, st));
+  struct Scratch {
+    cudaStream_t st;
+    void* p[2] = {nullptr, nullptr};
+    ~Scratch() { for (void* v : p) if (v) cudaFreeAsync(v, st); }
+  } sc{st};
+  EO_CUDA_TRY(cudaMallocAsync(&sc.p[0], sizeof(cd) * h.P * h.K, st));
+  EO_CUDA_TRY(cudaMallocAsync(&sc.p[1], sizeof(double) * nst * 2, st));
+  cd* tmpw = (cd*)sc.p[0];
+  double* outb = (double*)sc.p[1];
+  // one host table per part (the copies are stream-ordered behind the kernels that
+  // read the previous table; the host tables live until the final synchronisation)
+  std::vector<cd> w(2 * (size_t)h.P * h.K, make_double2(0.0, 0.0));
   for (int part = 0; part < 2; ++part) {
-    const std::complex<double> c = ws[part];
-    std::vector<cd> w(h.P * h.K, make_double2(0.0, 0.0));
-    double C[4] = {0, 0, 0, 0};
-    if (h.kind == EO_WAVE_DIRICHLET) {
-      const std::complex<double> w0 = c, w1 = c * h.tau / al;
-      w[j * h.K + 0] = make_double2(w0.real(), w0.imag());
-      w[j * h.K + 1] = make_double2(w1.real(), w1.imag());
-      C[0] = (c / al).real();
-    } else {
-      const double tf = h.tau * h.opts.sw_f;
-      const std::complex<double> D = al * al + tf * tf;
-      const std::complex<double> w0 = c, w1 = c * (-al / D), w2 = c * (-tf / D);
-      w[j * h.K + 0] = make_double2(w0.real(), w0.imag());
-      w[j * h.K + 1] = make_double2(w1.real(), w1.imag());
-      w[j * h.K + 2] = make_double2(w2.real(), w2.imag());
-      C[0] = w1.real();
-      C[1] = w2.real();
-    }
-    EO_CUDA_TRY(cudaMemcpyAsync(tmpw, w.data(), sizeof(cd) * h.P * h.K, cudaMemcpyHostToDevice, st));
+    cd wj[3];
+    double C[4];
+    resolvent_weights(h, j, ws[part], wj, C);
+    cd* wp = w.data() + (size_t)part * h.P * h.K;
+    for (int k = 0; k < h.K; ++k) wp[(size_t)j * h.K + k] = wj[k];
+    EO_CUDA_TRY(cudaMemcpyAsync(tmpw, wp, sizeof(cd) * h.P * h.K, cudaMemcpyHostToDevice, st));
     eo_status rc = run_step(h, u, outb + part * nst, 1, j, 1, (const cd*)tmpw, C, st);
-    if (rc) return rc;
+    if (rc) {
+      cudaStreamSynchronize(st);
+      return rc;
+    }
   }
   // interleave (re, im)
   EO_CUDA_TRY(cudaMemcpy2DAsync(x, 2 * sizeof(double), outb, sizeof(double), sizeof(double), nst,
@@ -1287,28 +1309,34 @@ eo_status apply_resolvent(Handle& h, int j, const double* u, double* x, cudaStre
   EO_CUDA_TRY(cudaMemcpy2DAsync(x + 1, 2 * sizeof(double), outb + nst, sizeof(double), sizeof(double), nst,
                                 cudaMemcpyDeviceToDevice, st));
   EO_CUDA_TRY(cudaStreamSynchronize(st));
-  cudaFree(tmpw);
-  cudaFree(outb);
   return EO_OK;
 }
 
 // ---------------------------------------------------------------- resolvent without allocation
-// Some callers cannot allocate device memory at call time: code running while a
-// stream is being captured into a CUDA graph, host threads that must not
-// synchronise with the device allocator, or embedders that hand every byte of
-// the GPU to their own pool.  eo_apply_resolvent takes two small scratch
-// buffers from cudaMallocAsync on every call; this variant takes them from a
-// fixed file-scope device array instead and allocates nothing.
+// Some callers cannot allocate device memory at the moment they call: host
+// threads that must stay off the device allocator (it takes locks and can
+// synchronise the device), and embedders that hand every byte of the GPU to their
+// own memory pool, where any outside cudaMalloc fails.  eo_apply_resolvent takes
+// two scratch buffers from cudaMallocAsync on every call; this variant takes them
+// from a fixed file-scope device array instead and allocates nothing.
 //
 // The array is kNoAllocDoubles doubles (16 MiB); every GPU that loads the library
-// holds it until the process exits.  It must fit the per-pole weight table
-// (P x K complex) and the real and imaginary outputs (2 x fields x nodes
-// doubles); larger problems are rejected with EO_ERR_INVALID_ARG.  All calls
-// share the array and each keeps only what the previous call left there, so
-// calls whose work overlaps on the GPU (different streams, or different
-// handles on one device without ordering) race on it.
+// holds it until the process exits.  It holds the selected pole's K accumulation
+// weights (kNoAllocWeights doubles) and the real and imaginary outputs
+// (2 x fields x nodes doubles); larger problems are rejected with
+// EO_ERR_INVALID_ARG.  All calls share the array and each keeps what the previous
+// call left there (the weights are rewritten on the device by every call), so
+// calls whose work overlaps on the GPU (different streams, or different handles
+// on one device without ordering) race on it.
 static constexpr size_t kNoAllocDoubles = 2u << 20;
+static constexpr size_t kNoAllocWeights = 16;   // >= 2 * K doubles, keeps the outputs 128-byte aligned
 static __device__ __align__(256) double g_noalloc_scratch[kNoAllocDoubles];
+
+// w[k] of the selected pole into the scratch row (one thread per weight)
+__global__ void k_set_weights(cd* __restrict__ dst, int K, cd w0, cd w1, cd w2) {
+  const int k = threadIdx.x;
+  if (k < K) dst[k] = k == 0 ? w0 : (k == 1 ? w1 : w2);
+}
 
 namespace {
 std::mutex g_noalloc_mu;
@@ -1336,47 +1364,31 @@ eo_status noalloc_scratch(double** out) {
 eo_status apply_resolvent_noalloc(Handle& h, int j, const double* u, double* x, cudaStream_t st) {
   if (j < 0 || j >= h.P) return fail(EO_ERR_INVALID_ARG, "pole index out of range");
   const size_t nst = (size_t)h.F * h.g.n_nodes;
-  const size_t wdoubles = (size_t)2 * h.P * h.K;
-  if (wdoubles + 2 * nst > kNoAllocDoubles)
+  if (kNoAllocWeights + 2 * nst > kNoAllocDoubles)
     return fail(EO_ERR_INVALID_ARG, "problem too large for the no-allocation scratch (" +
-                                        std::to_string(wdoubles + 2 * nst) + " doubles needed, " +
+                                        std::to_string(kNoAllocWeights + 2 * nst) + " doubles needed, " +
                                         std::to_string(kNoAllocDoubles) + " available)");
   double* scratch = nullptr;
   eo_status rc = noalloc_scratch(&scratch);
   if (rc) return rc;
-  cd* tmpw = (cd*)scratch;              // [P][K]; only row j is written and read
-  double* outb = scratch + wdoubles;    // Re part, then Im part
-  const std::complex<double> al = h.alpha[j];
+  cd* wrow = (cd*)scratch;                     // the K weights of pole j
+  double* outb = scratch + kNoAllocWeights;    // Re part, then Im part
+  // The kernels read the weight of pole p at wgt[p * K + k], here only for p = j:
+  // offset the table so that row j is the scratch row.
+  const cd* wtab = wrow - (ptrdiff_t)j * h.K;
   const std::complex<double> ws[2] = {1.0, std::complex<double>(0.0, -1.0)};
   for (int part = 0; part < 2; ++part) {
-    const std::complex<double> c = ws[part];
-    cd w[3] = {make_double2(0, 0), make_double2(0, 0), make_double2(0, 0)};
-    double C[4] = {0, 0, 0, 0};
-    if (h.kind == EO_WAVE_DIRICHLET) {
-      const std::complex<double> w0 = c, w1 = c * h.tau / al;
-      w[0] = make_double2(w0.real(), w0.imag());
-      w[1] = make_double2(w1.real(), w1.imag());
-      C[0] = (c / al).real();
-    } else {
-      const double tf = h.tau * h.opts.sw_f;
-      const std::complex<double> D = al * al + tf * tf;
-      const std::complex<double> w0 = c, w1 = c * (-al / D), w2 = c * (-tf / D);
-      w[0] = make_double2(w0.real(), w0.imag());
-      w[1] = make_double2(w1.real(), w1.imag());
-      w[2] = make_double2(w2.real(), w2.imag());
-      C[0] = w1.real();
-      C[1] = w2.real();
-    }
-    EO_CUDA_TRY(cudaMemcpyAsync(tmpw + (size_t)j * h.K, w, sizeof(cd) * h.K, cudaMemcpyHostToDevice, st));
-    // the copy reads w from the host stack: let it finish before w goes out of scope
-    EO_CUDA_TRY(cudaStreamSynchronize(st));
-    if ((rc = run_step(h, u, outb + part * nst, 1, j, 1, tmpw, C, st))) return rc;
+    cd w[3];
+    double C[4];
+    resolvent_weights(h, j, ws[part], w, C);
+    k_set_weights<<<1, 32, 0, st>>>(wrow, h.K, w[0], w[1], w[2]);
+    EO_CUDA_TRY(cudaGetLastError());
+    if ((rc = run_step(h, u, outb + part * nst, 1, j, 1, wtab, C, st))) return rc;
   }
   EO_CUDA_TRY(cudaMemcpy2DAsync(x, 2 * sizeof(double), outb, sizeof(double), sizeof(double), nst,
                                 cudaMemcpyDeviceToDevice, st));
   EO_CUDA_TRY(cudaMemcpy2DAsync(x + 1, 2 * sizeof(double), outb + nst, sizeof(double), sizeof(double), nst,
                                 cudaMemcpyDeviceToDevice, st));
-  EO_CUDA_TRY(cudaStreamSynchronize(st));
   return EO_OK;
 }
 

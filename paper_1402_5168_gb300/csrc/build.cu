@@ -20,6 +20,7 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdlib>
 #include <cstring>
 #include <string>
 
@@ -403,6 +404,18 @@ __global__ void merge_sym_blocks(int nbatch, int n3, int nbd, int rh, int need_p
 
 namespace {
 
+// Host-side fault injection for the error paths of the build (tests only):
+// EO_FAULT_INJECT=singular makes the first leaf factorisation report a zero pivot
+// (as cuBLAS getrf does for a singular block), EO_FAULT_INJECT=oom makes the first
+// build workspace allocation fail.  Nothing is injected on the device.
+int fault_inject() {
+  const char* v = std::getenv("EO_FAULT_INJECT");
+  if (!v) return 0;
+  if (!std::strcmp(v, "singular")) return 1;
+  if (!std::strcmp(v, "oom")) return 2;
+  return 0;
+}
+
 struct Cublas {
   cublasHandle_t h = nullptr;
   ~Cublas() { if (h) cublasDestroy(h); }
@@ -466,7 +479,9 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
   // ---- leaf real matrices (pole independent)
   double *acoef = nullptr, *Aii0, *Aib, *Fbi, *Fbb;
   std::vector<void*> tmp;
+  const int inject = fault_inject();
   auto talloc = [&](void** ptr, size_t bytes) -> eo_status {
+    if (inject == 2) return fail(EO_ERR_OOM, "build workspace allocation failed (injected)");
     if (cudaMallocAsync(ptr, bytes, st) != cudaSuccess) return fail(EO_ERR_OOM, "build workspace allocation failed");
     tmp.push_back(*ptr);
     return EO_OK;
@@ -587,6 +602,7 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
       hinfo.assign(nbl, 0);
       EO_CUDA_TRY(cudaMemcpyAsync(hinfo.data(), info, sizeof(int) * nbl, cudaMemcpyDeviceToHost, st));
       EO_CUDA_TRY(cudaStreamSynchronize(st));
+      if (inject == 1) hinfo[0] = 1;
       for (int i = 0; i < nbl; ++i)
         if (hinfo[i]) return fail(EO_ERR_SINGULAR, "leaf interior system singular (leaf " + std::to_string(i) + ")");
       int hi = 0;
