@@ -113,7 +113,25 @@ def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fi
     # a pole-count override (profiling cases) replaces the fixed step by tau = X(poles) / band
     return eo.Operator(g, eo.SW_WALLS, band=W.BAND[w.name], tau=0.0 if poles else w.tau, n_poles=poles,
                        f=pr["f"], g=pr["g"], H=pr["H"], shared_ops=True, max_rhs=R, precision=precision,
-                       dense_leaves=dense_leaves, fitter=fitter, root_dense=root_dense, merge_dense=merge_dense)
+                       dense_leaves=dense_leaves, fitter=fitter, root_dense=root_dense, merge_dense=merge_dense,
+                       sw_consistent=bool(pr.get("consistent", False)))
+
+
+def is_periodic(w):
+    return bool(w.params.get("periodic", False))
+
+
+def oracle_problem(w, tau, x, y):
+    """The oracle's discrete problem of workload w (test infrastructure: the CPU
+    baseline legs only)."""
+    from oracle import sem
+    from oracle.resolvent import Problem
+    og = sem.Grid(w.nlx, w.nly, w.p, periodic=is_periodic(w))
+    if w.kind == "wave":
+        c = W.wave_c(w, x, y)
+        return Problem(og, "wave", tau, c2=c * c)
+    pr = w.params
+    return Problem(og, "sw", tau, f=pr["f"], g=pr["g"], H=pr["H"], consistent=bool(pr.get("consistent", False)))
 
 
 def timed_steps(torch, op, u, steps, stream, dist, label="timed", trace=False):
@@ -169,13 +187,14 @@ def plan_levels(nlx, nly, q):
     return out
 
 
-def class_work(op, w, R, prec, fd, root_c4=False, merge_sym=False):
+def class_work(op, w, R, prec, fd, root_c4=False, merge_sym=False, periodic=False):
     """Algorithmic FP64-equivalent flops (8 per complex multiply-add) and bytes
     of one step, per kernel class, with the arithmetic precision of each.
     root_c4: the wall solve runs as four Fourier blocks of a quarter of the wall
     nodes each (square walled domain), a quarter of the dense inverse's entries.
     merge_sym: shared levels apply even/odd blocks (Z in two, U and S in four), which
-    every level of an even q has."""
+    every level of an even q has.  periodic: the root solve is the seam system of
+    half the root's boundary nodes, and a Dirichlet root keeps its parent blocks."""
     q = w.p - 2
     ni, nb = q * q, 4 * q
     P = int((op.alpha.imag >= 0).sum())
@@ -202,7 +221,7 @@ def class_work(op, w, R, prec, fd, root_c4=False, merge_sym=False):
     uf = ub = df = db = 0.0
     for i, l in enumerate(lv):
         root = i == len(lv) - 1
-        par = not (root and w.kind == "wave")
+        par = not (root and w.kind == "wave" and not periodic)
         zu = l["n3"] + (l["nbd"] if par else 0)
         nbo = 1 if shared else l["nbox"]
         sym = merge_sym and shared and q % 2 == 0
@@ -216,7 +235,10 @@ def class_work(op, w, R, prec, fd, root_c4=False, merge_sym=False):
             db += P * nbo * sent * esz + P * l["nbox"] * R * (l["nbd"] + l["n3"]) * 16
     work["up_merge"] = (uf, ub, prec)
     work["down_merge"] = (df, db, prec)
-    if w.kind == "sw":
+    if periodic:
+        nr = lv[-1]["nbd"] // 2
+        work["root"] = (8.0 * P * R * nr * nr, P * nr * nr * esz + P * R * 3 * nr * 16, prec)
+    elif w.kind == "sw":
         nr = lv[-1]["nbd"]
         ent = 4 * (nr // 4) ** 2 if root_c4 else nr * nr
         work["root"] = (8.0 * P * R * ent, P * ent * esz + P * R * 2 * nr * 16, prec)
@@ -237,12 +259,12 @@ def alu_peak(prec):
     return {"fp32": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS, "df32": FP32_PEAK_TFLOPS / 2 / 48 * 8}[prec]
 
 
-def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False, merge_sym=False):
+def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False, merge_sym=False, periodic=False):
     """Per kernel class: algorithmic work of one step over that class's device
     time per step (CUDA events around its launches), against the ALU peak of
     its arithmetic and the measured HBM copy bandwidth; the class with the
     largest time share is reported as the roofline of the step."""
-    work = class_work(op, w, R, prec, fd, root_c4, merge_sym)
+    work = class_work(op, w, R, prec, fd, root_c4, merge_sym, periodic)
     per = {}
     for cls, (flops, nbytes, pr) in work.items():
         n, ms = tim.get(cls, (0, 0.0))
@@ -260,7 +282,7 @@ def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False, merge_sym=Fals
     kname = {"up_leaf": "k_fd_up_leaf" if fd else "k_up_leaf", "down_leaf": "k_fd_down_leaf" if fd else "k_down_leaf",
              "up_merge": "k_up_merge_sym" if merge_sym else "k_up_merge",
              "down_merge": "k_down_merge_sym" if merge_sym else "k_down_merge",
-             "root": "k_root_sw_c4" if root_c4 else "k_root_sw"}[top]
+             "root": "k_root_periodic" if periodic else ("k_root_sw_c4" if root_c4 else "k_root_sw")}[top]
     tname = {"fp32": "float2", "fp64": "double2", "df32": "float4"}[d["precision"]]
     if not (fd and top in ("up_leaf", "down_leaf")):
         kname += "<NC, %s>" % tname
@@ -307,16 +329,20 @@ def run_ours(args):
         w = W.dataclasses.replace(w, nlx=args.leaves, nly=args.leaves)
     R = args.rhs
     reduced = args.precision != "fp64"
-    g = eo.Grid(w.nlx, w.nly, w.p)
+    per = is_periodic(w)
+    g = eo.Grid(w.nlx, w.nly, w.p, periodic=per)
     x, y = g.nodes()
     t0 = time.time()
     op = build_operator(eo, w, g, x, y, R, args.precision, args.poles, args.dense_leaves, args.fitter,
                         args.root_dense, args.merge_dense)
     # the library splits the wall solve of a square walled domain of square leaves into
     # four Fourier blocks unless told not to
-    root_c4 = w.kind == "sw" and w.nlx == w.nly and not args.root_dense
+    root_c4 = w.kind == "sw" and w.nlx == w.nly and not args.root_dense and not per
     # and applies the even/odd merge blocks on every level of a shared-operator grid
-    merge_sym = w.kind == "sw" and not args.merge_dense
+    # (not on periodic grids, nor with the consistent elimination's curl term)
+    consistent = bool(w.params.get("consistent", False))
+    merge_sym = w.kind == "sw" and not args.merge_dense and not per and not consistent
+    fd = w.kind == "sw" and not args.dense_leaves and not consistent
     torch.cuda.synchronize()
     build_s = time.time() - t0
     U0 = np.stack([np.stack(W.initial_fields(w, x, y, r)) for r in range(R)])
@@ -383,13 +409,19 @@ def run_ours(args):
         "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True, "scaling": "weak",
         "vs_baseline": None, "dtype": {"fp32": "f32", "fp64": "f64", "df32": "f32x2"}[args.precision],
         "data": "synthetic",
-        "config": {"workload": w.name, "kind": w.kind, "leaves": f"{w.nlx}x{w.nly}", "p": w.p,
+        "config": {"workload": w.name, "kind": w.kind, "p": w.p,
                    "fitter": {"line": "least-squares pole line", "gauss": "Gaussian sums + Table 1 "
                               "(two pole lines)"}[args.fitter],
+                   "boundary": "periodic square (seams are interfaces)" if per else "walls",
+                   "elimination": ("consistent (curl of the recovered gradient kept)" if consistent
+                                   else "as the paper writes it") if w.kind == "sw" else None,
+                   "leaves": f"{w.nlx}x{w.nly}",
+                   "leaf_solves": "fast diagonalisation" if fd else "dense leaf operators",
                    "merges": ("even/odd blocks of the reflection symmetries" if merge_sym else "dense blocks")
                    if w.kind == "sw" else "dense blocks",
-                   "root": ("four Fourier blocks of the quarter-turn-symmetric wall system" if root_c4
-                            else "dense wall inverse") if w.kind == "sw" else "none (Dirichlet)",
+                   "root": ("seam system of the root box merged with itself" if per else
+                            ("four Fourier blocks of the quarter-turn-symmetric wall system" if root_c4
+                             else "dense wall inverse") if w.kind == "sw" else "none (Dirichlet)"),
                    "precision": {"fp32": "FP32 operator blocks and products; FP64 vectors, pole sum, maps",
                                  "df32": "FP32-pair (hi, lo) operator blocks, exact split products and "
                                          "compensated sums on the FP32 pipe; FP64 vectors, pole sum, maps",
@@ -407,8 +439,8 @@ def run_ours(args):
         "gpu_launches": int(launches),
         **fp64,
         "kernel_share": shares,
-        "roofline": roofline(op, w, R, tim, args.precision, pk, pk_kind, fd=(w.kind == "sw" and not args.dense_leaves),
-                             root_c4=root_c4, merge_sym=merge_sym),
+        "roofline": roofline(op, w, R, tim, args.precision, pk, pk_kind, fd=fd, root_c4=root_c4, merge_sym=merge_sym,
+                             periodic=per),
         "clocks": clocks,
     }
     if args.cpu_baseline:
@@ -495,16 +527,8 @@ def cpu_baseline(w, op, x, y, u0, budget_s=30.0):
     """The FP64 oracle's apply phase on the host cores, on a bounded sample:
     the first few distinct poles of one step (factorisations are the oracle's
     build and are not timed), scaled to applies/s."""
-    from oracle import sem
-    from oracle.resolvent import Problem, Stepper
-    og = sem.Grid(w.nlx, w.nly, w.p)
-    if w.kind == "wave":
-        c = W.wave_c(w, x, y)
-        prob = Problem(og, "wave", op.tau, c2=c * c)
-    else:
-        pr = w.params
-        prob = Problem(og, "sw", op.tau, f=pr["f"], g=pr["g"], H=pr["H"])
-    st = Stepper(prob, op.alpha, op.b)
+    from oracle.resolvent import Stepper
+    st = Stepper(oracle_problem(w, op.tau, x, y), op.alpha, op.b)
     upper = np.flatnonzero(op.alpha.imag >= 0)
     P = upper.size
     done, solve_s, t_all = 0, 0.0, time.time()
@@ -541,17 +565,10 @@ def _oracle_pole_worker(args):
     pole's resolvent solve for budget_s seconds."""
     wname, tau, alpha, bj, u0, budget_s, barrier = args
     from oracle import sem
-    from oracle.resolvent import Problem, Stepper
+    from oracle.resolvent import Stepper
     w = W.WORKLOADS[wname]
-    og = sem.Grid(w.nlx, w.nly, w.p)
-    if w.kind == "wave":
-        x, y = og.x, og.y
-        c = W.wave_c(w, x, y)
-        prob = Problem(og, "wave", tau, c2=c * c)
-    else:
-        pr = w.params
-        prob = Problem(og, "sw", tau, f=pr["f"], g=pr["g"], H=pr["H"])
-    st = Stepper(prob, np.array([alpha]), np.array([bj]))
+    og = sem.Grid(w.nlx, w.nly, w.p, periodic=is_periodic(w))
+    st = Stepper(oracle_problem(w, tau, og.x, og.y), np.array([alpha]), np.array([bj]))
     st._solver(0)
     barrier.wait()
     n, t0 = 0, time.perf_counter()
@@ -597,8 +614,8 @@ def run_reference(args):
         return
     w = W.WORKLOADS[args.workload]
     from oracle import rational, sem
-    from oracle.resolvent import Problem, Stepper
-    g = sem.Grid(w.nlx, w.nly, w.p)
+    from oracle.resolvent import Stepper
+    g = sem.Grid(w.nlx, w.nly, w.p, periodic=is_periodic(w))
     # the oracle's own approximant for this workload's pole count; for a fixed
     # step (thousands of poles) the oracle's pole line of the same density
     # (sigma = 4.5, spacing 1, reaching 32 past the band): the timed sample is one
@@ -611,14 +628,8 @@ def run_reference(args):
         M = int(np.ceil(tau * W.BAND[w.name] + 32.0))
         alpha = rational.pole_line(2 * M + 1, 4.5, 1.0)
         b = np.ones(alpha.size, dtype=np.complex128)
-    if w.kind == "wave":
-        c = W.wave_c(w, g.x, g.y)
-        prob = Problem(g, "wave", tau, c2=c * c)
-    else:
-        pr = w.params
-        prob = Problem(g, "sw", tau, f=pr["f"], g=pr["g"], H=pr["H"])
     u0 = np.stack(W.initial_fields(w, g.x, g.y, 0))
-    st = Stepper(prob, alpha, b)
+    st = Stepper(oracle_problem(w, tau, g.x, g.y), alpha, b)
     M = (alpha.size - 1) // 2
     P = M + 1
     # one "step" of this arm = one distinct-pole resolvent solve with a factorised

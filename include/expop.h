@@ -139,6 +139,23 @@ typedef struct {
  * eo_grid_destroy; handles built from it keep their own copy. */
 eo_status eo_grid_create(int nlx, int nly, int p, double x0, double x1, double y0,
                          double y1, eo_grid_t *out);
+/* Periodic leaf grid: the square [x0,x1]x[y0,y1] with x1 identified with x0 and y1 with
+ * y0, the setting of the paper's examples (Section 4: "periodic boundary conditions").
+ * The seams x = x0 and y = y0 are interfaces between the last and the first leaf of each
+ * row and column (flux continuity, Section 2.2); there is no domain boundary.  Public
+ * numbering as above with nly horizontal and nlx vertical edge lines (line e = 0 is also
+ * the top / right edge of the last leaf row / column): n_h = nlx*nly*q,
+ *   vertical edge nodes: id = n_int + n_h + (b*nlx + e)*q + (j-1),  e = 0..nlx-1,
+ * and seam nodes carry the coordinates x0 (vertical seam) and y0 (horizontal seam).
+ * Built operators then have no walls: EO_SW_WALLS is rotating shallow water on the
+ * torus, EO_WAVE_DIRICHLET the wave equation on the torus; the root solve is the
+ * seam system of the root box merged with itself (half its boundary nodes).
+ * eo_apply_adjoint is not built for periodic grids (EO_ERR_UNSUPPORTED), and merges
+ * use the dense blocks (opts.merge_dense is implied).  Errors as eo_grid_create. */
+eo_status eo_grid_create_periodic(int nlx, int nly, int p, double x0, double x1, double y0,
+                                  double y1, eo_grid_t *out);
+/* 1 for a periodic grid, 0 for a walled one. */
+eo_status eo_grid_periodic(eo_grid_t grid, int *periodic);
 /* Sizes: total nodes, interior nodes, edge nodes.  Any pointer may be NULL. */
 eo_status eo_grid_info(eo_grid_t grid, int64_t *n_nodes, int64_t *n_interior,
                        int64_t *n_edge);

@@ -71,12 +71,15 @@ def _stream_ptr(stream):
 
 
 class Grid:
-    """nlx x nly leaves of p x p Chebyshev nodes on [x0,x1] x [y0,y1]."""
+    """nlx x nly leaves of p x p Chebyshev nodes on [x0,x1] x [y0,y1]; periodic=True
+    identifies x1 with x0 and y1 with y0 (eo_grid_create_periodic)."""
 
-    def __init__(self, nlx, nly, p, x0=0.0, x1=1.0, y0=0.0, y1=1.0):
+    def __init__(self, nlx, nly, p, x0=0.0, x1=1.0, y0=0.0, y1=1.0, periodic=False):
         L = _capi.lib()
         self._h = C.c_void_p()
-        check(L.eo_grid_create(nlx, nly, p, x0, x1, y0, y1, C.byref(self._h)))
+        create = L.eo_grid_create_periodic if periodic else L.eo_grid_create
+        check(create(nlx, nly, p, x0, x1, y0, y1, C.byref(self._h)))
+        self.periodic = bool(periodic)
         n, ni, ne = C.c_int64(), C.c_int64(), C.c_int64()
         check(L.eo_grid_info(self._h, C.byref(n), C.byref(ni), C.byref(ne)))
         self.nlx, self.nly, self.p = nlx, nly, p

@@ -14,7 +14,7 @@ STATUS_CODES = {v: k for k, v in STATUS.items()}
 WAVE_DIRICHLET, SW_WALLS = 0, 1
 
 # every symbol include/expop.h declares
-SYMBOLS = ("eo_fit", "eo_grid_create", "eo_grid_info", "eo_grid_nodes", "eo_grid_destroy", "eo_build_operator",
+SYMBOLS = ("eo_fit", "eo_grid_create", "eo_grid_create_periodic", "eo_grid_periodic", "eo_grid_info", "eo_grid_nodes", "eo_grid_destroy", "eo_build_operator",
            "eo_get_poles", "eo_memory", "eo_apply", "eo_apply_adjoint", "eo_apply_host", "eo_apply_resolvent", "eo_apply_resolvent_noalloc", "eo_set_timing", "eo_get_timing", "eo_destroy",
            "eo_last_error", "eo_leaf_basis", "eo_batch_create", "eo_batch_apply", "eo_batch_destroy",
            "eo_fit_function", "eo_apply_functions", "eo_fit_gauss")
@@ -45,6 +45,9 @@ def lib() -> C.CDLL:
     sig = {
         "eo_grid_create": [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
                            C.POINTER(vp)],
+        "eo_grid_create_periodic": [C.c_int, C.c_int, C.c_int, C.c_double, C.c_double, C.c_double, C.c_double,
+                                    C.POINTER(vp)],
+        "eo_grid_periodic": [vp, C.POINTER(C.c_int)],
         "eo_grid_info": [vp, i64p, i64p, i64p],
         "eo_grid_nodes": [vp, dp, dp],
         "eo_grid_destroy": [vp],

@@ -316,12 +316,15 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   h.lv.resize(L + 1);
   std::vector<std::vector<int>> sym_orb(L + 1), sym_osg(L + 1), sym_mem(L + 1);
   std::vector<double> gx, gy;
-  if (h.shared && !curl && !o.merge_dense) g.coords(gx, gy);
+  // (a periodic square's seam nodes carry the coordinates of lines x0, y0, so the
+  // reflection maps of boxes that reach a seam are not found from them: periodic
+  // grids keep the dense merge blocks)
+  if (h.shared && !curl && !o.merge_dense && !g.periodic) g.coords(gx, gy);
   for (int l = 1; l <= L; ++l) {
     const Level& lv = plan.lv[l];
     LevelDev& ld = h.lv[l];
     const bool root = l == L;
-    const bool need_par = !(root && h.kind == EO_WAVE_DIRICHLET);
+    const bool need_par = !(root && h.kind == EO_WAVE_DIRICHLET && !g.periodic);
     const int nbo = h.shared ? 1 : lv.nbox;
     ld.zu_rows = lv.n3 + (need_par ? lv.nbd : 0);
     ld.zu_bstride = h.shared ? 0 : (int64_t)ld.zu_rows * lv.n3;
@@ -343,7 +346,12 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
     }
   }
   std::vector<int> c4idx;
-  if (h.kind == EO_SW_WALLS) {
+  if (g.periodic) {
+    // seam system of the root box merged with itself: half of its boundary nodes
+    h.nroot = plan.lv[L].nbd / 2;
+    h.binv_pstride = (int64_t)h.nroot * h.nroot;
+    ops += P * h.binv_pstride;
+  } else if (h.kind == EO_SW_WALLS) {
     h.nroot = plan.lv[L].nbd;
     if (!o.root_dense && L >= 1 && root_c4_map(g, plan.lv[L], c4idx)) h.c4 = h.nroot / 4;
     h.binv_pstride = h.c4 ? 4LL * h.c4 * h.c4 : (int64_t)h.nroot * h.nroot;
@@ -373,7 +381,8 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
       }
     }
   }
-  if (h.kind == EO_SW_WALLS && (rc = h.alloc((void**)&h.Binv, sizeof(cd) * P * h.binv_pstride, true)))
+  if ((h.kind == EO_SW_WALLS || g.periodic) &&
+      (rc = h.alloc((void**)&h.Binv, sizeof(cd) * P * h.binv_pstride, true)))
     return rc;
   if (h.c4) {
     std::vector<int> inv(h.nroot, -1);
@@ -447,16 +456,32 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
 
 extern "C" {
 
-eo_status eo_grid_create(int nlx, int nly, int p, double x0, double x1, double y0, double y1,
-                         eo_grid_t* out) {
+static eo_status grid_create(int nlx, int nly, int p, double x0, double x1, double y0, double y1, int periodic,
+                             eo_grid_t* out) {
   if (!out) return fail(EO_ERR_INVALID_ARG, "null output pointer");
   *out = nullptr;
   eo_grid_s* gs = new (std::nothrow) eo_grid_s;
   if (!gs) return fail(EO_ERR_OOM, "host allocation failed");
-  eo_status rc = make_grid(nlx, nly, p, x0, x1, y0, y1, gs->g);
+  eo_status rc = make_grid(nlx, nly, p, x0, x1, y0, y1, gs->g, periodic);
   if (rc) { delete gs; return rc; }
   *out = gs;
   set_error("");
+  return EO_OK;
+}
+
+eo_status eo_grid_create(int nlx, int nly, int p, double x0, double x1, double y0, double y1,
+                         eo_grid_t* out) {
+  return grid_create(nlx, nly, p, x0, x1, y0, y1, 0, out);
+}
+
+eo_status eo_grid_create_periodic(int nlx, int nly, int p, double x0, double x1, double y0, double y1,
+                                  eo_grid_t* out) {
+  return grid_create(nlx, nly, p, x0, x1, y0, y1, 1, out);
+}
+
+eo_status eo_grid_periodic(eo_grid_t grid, int* periodic) {
+  if (!grid || !periodic) return fail(EO_ERR_INVALID_ARG, "null argument");
+  *periodic = grid->g.periodic;
   return EO_OK;
 }
 
@@ -656,6 +681,7 @@ eo_status eo_apply(eo_handle_t hd, double* u_dev, int n_rhs, int n_steps, void* 
 
 eo_status eo_apply_adjoint(eo_handle_t hd, double* y_dev, int n_rhs, int n_steps, void* stream) {
   if (!hd) return fail(EO_ERR_INVALID_ARG, "null handle");
+  if (hd->h.g.periodic) return fail(EO_ERR_UNSUPPORTED, "the transposed sweeps are built for walled grids only");
   return apply_adjoint(hd->h, y_dev, n_rhs, n_steps, (cudaStream_t)stream);
 }
 

@@ -348,6 +348,50 @@ __global__ void __launch_bounds__(256) k_root_sw_c4(Sweep s, RootArgs ra, const 
   }
 }
 
+// Root of a periodic square: the seams are interfaces of the root box with itself.
+// With the root's particular fluxes h (boundary order S, E, N, W) the seam values are
+// s = -Binv P^T h, P^T adding the two sides that meet at a seam (S with N, W with E);
+// they are the edge values of the seam segments (the S and W segments of the root,
+// which are also its N and E segments).  ra.n = root boundary nodes, Binv (n/2)^2.
+template <int NC, typename TA>
+__global__ void __launch_bounds__(256) k_root_periodic(Sweep s, RootArgs ra, const cd* __restrict__ hroot,
+                                                       cd* __restrict__ E) {
+  extern __shared__ cd smem[];
+  const int pl = blockIdx.y, p = s.p0 + pl;
+  const int c0 = blockIdx.x * NC;
+  const int n = ra.n, m = n / 2, sxq = ra.sxq, syq = ra.syq;
+  TA* Bs = (TA*)smem;
+  cd* Cs = after(Bs, (size_t)NC * m);
+  cd* red = Cs + NC * m;
+  for (int e = threadIdx.x; e < NC * m; e += blockDim.x) {
+    const int c = e / m, r = e - c * m;
+    cd v = make_double2(0.0, 0.0);
+    const int rr = c0 + c;
+    if (rr < s.R) {
+      int i1, i2;
+      if (r < sxq) { i1 = r; i2 = sxq + syq + r; }
+      else { i1 = 2 * sxq + syq + (r - sxq); i2 = sxq + (r - sxq); }
+      const cd* hr = hroot + ((long long)pl * s.R + rr) * n;
+      const cd a = hr[i1], b = hr[i2];
+      v = make_double2(-(a.x + b.x), -(a.y + b.y));
+    }
+    Bs[e] = Cv<TA>::from(v);
+  }
+  __syncthreads();
+  // rows [r_lo, r_lo + nr) of the seam solve (blocks along z split the rows)
+  const int rows_per = (m + gridDim.z - 1) / gridDim.z;
+  const int r_lo = blockIdx.z * rows_per, nr = min(rows_per, m - r_lo);
+  if (nr <= 0) return;
+  cmv<NC, TA>((const TA*)ra.Binv + (long long)p * m * m + r_lo, m, nr, m, Bs, m, Cs, red);
+  for (int e = threadIdx.x; e < NC * nr; e += blockDim.x) {
+    const int c = e / nr, r = r_lo + (e - c * nr);
+    const int rr = c0 + c;
+    if (rr >= s.R) continue;
+    const int i = r < sxq ? r : 2 * sxq + syq + (r - sxq);   // the S or W node of seam node r
+    E[((long long)pl * s.R + rr) * s.n_edge + (long long)ra.bseg[i / ra.q] * ra.q + (i % ra.q)] = Cs[e];
+  }
+}
+
 // ---------------------------------------------------------------- down: merges
 template <int NC, typename TA>
 __global__ void __launch_bounds__(256) k_down_merge(Sweep s, MergeArgs m, cd* __restrict__ E) {
@@ -617,7 +661,7 @@ __global__ void k_pre_sw(LeafGeo g, int R, long long n_nodes, const double* __re
 // shallow-water post-map: h = A0,
 //   U = C1 F1 + C2 F2 + tau g (dA1/dx + dA2/dy), V = -C2 F1 + C1 F2 + tau g (-dA2/dx + dA1/dy)
 // Interior nodes by leaf differentiation; edge nodes owned by this leaf (S and W,
-// plus E / N on the domain boundary): normal derivative = mean of the one-sided
+// plus E / N on the walls of a walled square): normal derivative = mean of the one-sided
 // derivatives of the leaves that touch the edge, tangential = edge interpolant.
 __global__ void k_post_sw(LeafGeo g, int R, long long n_nodes, int K, const double* __restrict__ afull,
                           const double* __restrict__ uin, double* __restrict__ uout, double C1, double C2,
@@ -638,10 +682,11 @@ __global__ void k_post_sw(LeafGeo g, int R, long long n_nodes, int K, const doub
     long long id = gnode(g, a, b, k, j);
     A1[t] = id < 0 ? 0.0 : a1g[id];
     A2[t] = id < 0 ? 0.0 : a2g[id];
-    id = a > 0 ? gnode(g, a - 1, b, k, j) : -1;
+    // west / south neighbours (across the seam on a periodic square)
+    id = a > 0 ? gnode(g, a - 1, b, k, j) : (g.per ? gnode(g, g.nlx - 1, b, k, j) : -1);
     W1[t] = id < 0 ? 0.0 : a1g[id];
     W2[t] = id < 0 ? 0.0 : a2g[id];
-    id = b > 0 ? gnode(g, a, b - 1, k, j) : -1;
+    id = b > 0 ? gnode(g, a, b - 1, k, j) : (g.per ? gnode(g, a, g.nly - 1, k, j) : -1);
     S1[t] = id < 0 ? 0.0 : a1g[id];
     S2[t] = id < 0 ? 0.0 : a2g[id];
   }
@@ -663,8 +708,10 @@ __global__ void k_post_sw(LeafGeo g, int R, long long n_nodes, int K, const doub
   // owned edges
   for (int t = threadIdx.x; t < 4 * q; t += blockDim.x) {
     const int side = t / q, o = t % q + 1;
-    if (side == 1 && a != g.nlx - 1) continue;   // E edge owned by the east neighbour
-    if (side == 2 && b != g.nly - 1) continue;   // N edge owned by the north neighbour
+    // E / N edges are owned by the east / north neighbour (on a periodic square always,
+    // the last column's E edge being the first column's W edge)
+    if (side == 1 && (g.per || a != g.nlx - 1)) continue;
+    if (side == 2 && (g.per || b != g.nly - 1)) continue;
     double d1x, d1y, d2x, d2y;
     long long id;
     if (side == 0 || side == 2) {                // horizontal edge: normal y, tangential x
@@ -672,7 +719,7 @@ __global__ void k_post_sw(LeafGeo g, int R, long long n_nodes, int K, const doub
       id = gnode(g, a, b, k, j);
       d1y = ddy(g, A1, k, j);
       d2y = ddy(g, A2, k, j);
-      if (side == 0 && b > 0) {
+      if (side == 0 && (b > 0 || g.per)) {
         d1y = 0.5 * (d1y + ddy(g, S1, k, p - 1));
         d2y = 0.5 * (d2y + ddy(g, S2, k, p - 1));
       }
@@ -686,7 +733,7 @@ __global__ void k_post_sw(LeafGeo g, int R, long long n_nodes, int K, const doub
       id = gnode(g, a, b, k, j);
       d1x = ddx(g, A1, k, j);
       d2x = ddx(g, A2, k, j);
-      if (side == 3 && a > 0) {
+      if (side == 3 && (a > 0 || g.per)) {
         d1x = 0.5 * (d1x + ddx(g, W1, p - 1, j));
         d2x = 0.5 * (d2x + ddx(g, W2, p - 1, j));
       }
@@ -823,6 +870,22 @@ struct RootSW {
 };
 
 template <int NC, typename TA>
+struct RootPer {
+  static eo_status run(const Sweep& s, const RootArgs& ra, const cd* hroot, cd* E, int nt, int rsplit,
+                       cudaStream_t st) {
+    const int m = ra.n / 2;
+    const size_t smem = sizeof(cd) * ((size_t)NC * 2 * m + 256 * NC) + 64;
+    rsplit = std::max(1, rsplit);
+    dim3 grid((s.R + NC - 1) / NC, s.P, rsplit);
+    const int rows_per = (m + rsplit - 1) / rsplit;
+    EO_SET_SMEM((k_root_periodic<NC, TA>), smem);
+    k_root_periodic<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(rows_per), smem, st>>>(s, ra, hroot, E);
+    EO_CUDA_TRY(cudaGetLastError());
+    return EO_OK;
+  }
+};
+
+template <int NC, typename TA>
 struct DownLeaf {
   static eo_status run(const Sweep& s, const Handle& h, int nleaf, int nchunk, int ppc, const cd* E,
                        double* part, cudaStream_t st) {
@@ -867,7 +930,7 @@ LeafGeo leaf_geo(const Handle& h) {
   const Grid& g = h.g;
   const int q = g.q;
   return LeafGeo{g.nlx, g.nly, g.p, q, g.n_int, g.n_hseg, h.dDx, h.dDx + g.p * g.p, h.dDx + 2 * g.p * g.p,
-                 h.dDx + 2 * g.p * g.p + q * q};
+                 h.dDx + 2 * g.p * g.p + q * q, g.periodic};
 }
 
 // First part of a step: pre-map, upward sweep, root, downward merges.  Leaves
@@ -921,7 +984,15 @@ eo_status sweep_to_edges(Handle& h, const double* uin, int R, int p0, int np, co
     std::swap(hcur, hnext);
   }
   // root
-  if (h.kind == EO_WAVE_DIRICHLET) {
+  if (g.periodic) {
+    const Level& rl = h.plan.lv[L];
+    RootArgs ra{rl.nbd, q, rl.sx * q, rl.sy * q, h.lv[L].bseg, h.aBinv, nullptr, nullptr, uin, h.F};
+    if ((rc = h.trace_begin(st))) return rc;
+    const int nc = h.root_tuned.nc ? h.root_tuned.nc : pick_nc(0, R, rl.nbd / 2, rl.nbd / 2);
+    if ((rc = dispatch<RootPer>(h.root_fp32, nc, s, ra, hcur, h.E, h.root_tuned.nt, h.root_tuned.rs, st)))
+      return rc;
+    if ((rc = h.trace_end(TR_ROOT, st))) return rc;
+  } else if (h.kind == EO_WAVE_DIRICHLET) {
     // wall values are zero: reset them every step (other users of the edge
     // workspace, such as the adjoint sweeps, leave data there)
     const Level& rl = h.plan.lv[L];
@@ -1104,7 +1175,20 @@ eo_status autotune(Handle& h, int R, cudaStream_t st) {
       if (t < bd) { bd = t; h.fd_ncol_down = nc; }
     }
   }
-  if (h.kind == EO_SW_WALLS) {
+  if (h.g.periodic) {
+    const Level& rl = h.plan.lv[L];
+    RootArgs ra{rl.nbd, h.g.q, rl.sx * h.g.q, rl.sy * h.g.q, h.lv[L].bseg, h.aBinv, nullptr, nullptr, h.ustate, h.F};
+    const int m = rl.nbd / 2;
+    float best = 1e30f;
+    for (int nc = 1; nc <= 8 && nc <= R; nc *= 2)
+      for (int rs = 1; rs <= 4; rs *= 2)
+        for (int nt : nt_list((m + rs - 1) / rs)) {
+          if ((size_t)nc * (2 * m + 256) * sizeof(cd) > 200 * 1024) continue;
+          const float t = timeit([&] { return dispatch<RootPer>(h.root_fp32, nc, s, ra, h.hA, h.E, nt, rs, st); });
+          if (t < 0) return fail(EO_ERR_CUDA, "autotune: root launch failed");
+          if (t < best) { best = t; h.root_tuned = Tuned{nc, nt, rs}; }
+        }
+  } else if (h.kind == EO_SW_WALLS) {
     const Level& rl = h.plan.lv[L];
     RootArgs ra{rl.nbd, h.g.q, rl.sx * h.g.q, rl.sy * h.g.q, h.lv[L].bseg, h.aBinv, h.bcoef, h.nu, h.ustate, 3,
                 h.c4, h.c4idx, h.c4inv};

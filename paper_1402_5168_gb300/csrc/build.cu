@@ -44,19 +44,24 @@ __device__ __forceinline__ int bidx(int k, int j, int p, int q) {
   return -1;
 }
 
+// global node id of local node (k, j) of leaf (a, b); per: periodic square, whose
+// top / right edge lines are lines 0
 __device__ __forceinline__ long long dnode(int a, int b, int k, int j, int nlx, int nly, int p,
-                                           long long n_int, long long n_hseg) {
+                                           long long n_int, long long n_hseg, int per) {
   const int q = p - 2;
   const bool kin = k > 0 && k < p - 1, jin = j > 0 && j < p - 1;
   if (kin && jin) return ((long long)b * nlx + a) * q * q + (long long)(j - 1) * q + (k - 1);
-  if (kin) return n_int + ((long long)(j == 0 ? b : b + 1) * nlx + a) * q + (k - 1);
-  if (jin) return n_int + (n_hseg + (long long)b * (nlx + 1) + (k == 0 ? a : a + 1)) * q + (j - 1);
+  if (kin) return n_int + ((long long)(j == 0 ? b : ((per && b + 1 == nly) ? 0 : b + 1)) * nlx + a) * q + (k - 1);
+  if (jin) {
+    const int nvl = per ? nlx : nlx + 1;
+    return n_int + (n_hseg + (long long)b * nvl + (k == 0 ? a : ((per && a + 1 == nlx) ? 0 : a + 1))) * q + (j - 1);
+  }
   return -1;
 }
 
 // Real leaf matrices, column-major: Aii0 (n_i x n_i), Aib (n_i x n_b),
 // Fbi (n_b x n_i), Fbb (n_b x n_b).  One block per leaf.
-__global__ void leaf_real_ops(int nlx, int nly, int p, long long n_int, long long n_hseg,
+__global__ void leaf_real_ops(int nlx, int nly, int p, long long n_int, long long n_hseg, int per,
                               const double* __restrict__ Dx, const double* __restrict__ Dy,
                               const double* __restrict__ acoef, double* Aii0, double* Aib,
                               double* Fbi, double* Fbb) {
@@ -67,7 +72,7 @@ __global__ void leaf_real_ops(int nlx, int nly, int p, long long n_int, long lon
   double* al = sm;   // a at local nodes, [j*p + k]
   for (int t = threadIdx.x; t < p * p; t += blockDim.x) {
     const int k = t % p, j = t / p;
-    const long long id = dnode(a, b, k, j, nlx, nly, p, n_int, n_hseg);
+    const long long id = dnode(a, b, k, j, nlx, nly, p, n_int, n_hseg, per);
     al[t] = (id < 0) ? 0.0 : (acoef ? acoef[id] : 1.0);
   }
   __syncthreads();
@@ -274,6 +279,35 @@ __global__ void root_system(int nbatch, int n, int q, int sxq, int syq, const cd
   }
 }
 
+// Root of a periodic square.  The root box's sides S and N are one seam (the same
+// nodes, both in ascending x) and so are W and E (ascending y).  With the seam values
+// s = [s_S (sxq); s_W (syq)] the boundary data are u_b = P s (u_S = u_N = s_S,
+// u_W = u_E = s_W), and flux continuity across the seams (Section 2.2, the seams are
+// interfaces between the last and the first leaf of a row or column) adds the outward
+// fluxes of the two sides that meet there: P^T (T u_b + h) = 0.  So B = P^T T P
+// (m x m, m = n / 2) and s = -B^{-1} P^T h.  B is column-major like T.
+__device__ __forceinline__ void seam_pair(int r, int sxq, int syq, int& i1, int& i2) {
+  if (r < sxq) { i1 = r; i2 = sxq + syq + r; }                      // S, N
+  else { const int t = r - sxq; i1 = 2 * sxq + syq + t; i2 = sxq + t; }   // W, E
+}
+
+__global__ void root_periodic_system(int nbatch, int n, int sxq, int syq, const cd* __restrict__ T, cd* B) {
+  const int m = n / 2;
+  const size_t mm = (size_t)m * m, nn = (size_t)n * n;
+  for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < (size_t)nbatch * mm;
+       t += (size_t)gridDim.x * blockDim.x) {
+    const size_t gi = t / mm, e = t % mm;
+    const int r = (int)(e % m), c = (int)(e / m);
+    int i1, i2, j1, j2;
+    seam_pair(r, sxq, syq, i1, i2);
+    seam_pair(c, sxq, syq, j1, j2);
+    const cd* Tg = T + gi * nn;
+    const cd a = Tg[i1 + (size_t)j1 * n], b = Tg[i1 + (size_t)j2 * n];
+    const cd d = Tg[i2 + (size_t)j1 * n], f = Tg[i2 + (size_t)j2 * n];
+    B[t] = make_double2(a.x + b.x + d.x + f.x, a.y + b.y + d.y + f.y);
+  }
+}
+
 // Fourier blocks of the rotation-symmetric wall system (square walled domain).  With
 // the wall rows put in the rotation-covariant form (side k's rows times c4s(k)) and
 // both rows and columns in counterclockwise side order, C_{k,l}[s][u] =
@@ -459,6 +493,7 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
   const int nleaf = g.nlx * g.nly;
   const int nlo = h.shared ? 1 : nleaf;     // leaves with their own operators
   const int P = h.P;
+  const int g_per = g.periodic;
   Cublas cbh;
   EO_CUBLAS_TRY(cublasCreate(&cbh.h));
   cublasHandle_t cb = cbh.h;
@@ -503,8 +538,8 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
   EO_CUDA_TRY(cudaMemsetAsync(Aib, 0, sizeof(double) * nlo * ni * nb, st));
   EO_CUDA_TRY(cudaMemsetAsync(Fbi, 0, sizeof(double) * nlo * nb * ni, st));
   EO_CUDA_TRY(cudaMemsetAsync(Fbb, 0, sizeof(double) * nlo * nb * nb, st));
-  leaf_real_ops<<<nlo, 256, sizeof(double) * p * p, st>>>(g.nlx, g.nly, p, g.n_int, g.n_hseg, dDx, dDy,
-                                                        acoef, Aii0, Aib, Fbi, Fbb);
+  leaf_real_ops<<<nlo, 256, sizeof(double) * p * p, st>>>(g.nlx, g.nly, p, g.n_int, g.n_hseg, g.periodic, dDx,
+                                                        dDy, acoef, Aii0, Aib, Fbi, Fbb);
   EO_CUDA_TRY(cudaGetLastError());
   if (h.fd && (rc = fd_setup(h, Aii0, Aib, Fbi, st))) return rc;
   // consistent shallow-water elimination: the leaf coupling of Curl(G h)
@@ -540,7 +575,7 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
   unsigned long long* c4stat = nullptr;
   unsigned long long* symstat = nullptr;
   if ((rc = talloc((void**)&symstat, sizeof(unsigned long long) * 2))) return rc;
-  if (h.kind == EO_SW_WALLS) {
+  if (h.kind == EO_SW_WALLS || g_per) {
     maxpiv = std::max(maxpiv, (size_t)G * h.nroot);
     maxinfo = std::max(maxinfo, (size_t)G * (h.c4 ? 4 : 1));
     ws_merge = std::max(ws_merge, (size_t)G * h.nroot * h.nroot);
@@ -629,8 +664,9 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
       const int nbt = g * nbo;   // batch entries at this level
       const int n3 = lv.n3, npar = lv.nbd;
       const bool root = (l == L);
-      const bool need_par = !(root && h.kind == EO_WAVE_DIRICHLET);
-      const bool need_T = !root || h.kind == EO_SW_WALLS;
+      // a Dirichlet root keeps only Z; walls and periodic seams need the root's T
+      const bool need_par = !(root && h.kind == EO_WAVE_DIRICHLET && !g_per);
+      const bool need_T = !root || h.kind == EO_SW_WALLS || g_per;
       cd* M33 = mw;
       cd* Z = M33 + (size_t)nbt * n3 * n3;
       cd* Qm = Z + (size_t)nbt * n3 * n3;
@@ -687,8 +723,17 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
       nbd_prev = npar;
       nbo_prev = nbo;
     }
-    // ---- root oblique system (shallow-water walls)
-    if (h.kind == EO_SW_WALLS) {
+    // ---- periodic seams: the root box merged with itself across both seams
+    if (g_per) {
+      const Level& rl = plan.lv[L];
+      cd* Broot = mw;
+      cd* Bi = h.Binv + (size_t)p0 * h.binv_pstride;
+      root_periodic_system<<<2048, 256, 0, st>>>(g, rl.nbd, rl.sx * q, rl.sy * q, Tprev, Broot);
+      EO_CUDA_TRY(cudaGetLastError());
+      if ((rc = batched_inverse(cb, st, rl.nbd / 2, g, Broot, Bi, piv, info, hinfo, "periodic seam system")))
+        return rc;
+    } else if (h.kind == EO_SW_WALLS) {
+      // ---- root oblique system (shallow-water walls)
       const Level& rl = plan.lv[L];
       const int n = rl.nbd;
       cd* Broot = mw;

@@ -20,19 +20,24 @@ struct Grid {
   int nlx = 0, nly = 0, p = 0, q = 0;
   double x0 = 0, x1 = 1, y0 = 0, y1 = 1, hx = 0, hy = 0;
   int64_t n_int = 0, n_hseg = 0, n_vseg = 0, n_seg = 0, n_edge = 0, n_nodes = 0;
+  // periodic square (the setting of the paper's examples): the lines y = y1 and
+  // x = x1 are the lines y = y0 and x = x0, so there are nhl = nly horizontal and
+  // nvl = nlx vertical edge lines (walled square: nly + 1 and nlx + 1)
+  int periodic = 0;
+  int nhl = 0, nvl = 0;
   std::vector<double> xi;        // Chebyshev-Lobatto points on [-1, 1], ascending
   std::vector<double> D;         // p x p differentiation matrix on [-1,1], row-major D[i*p+j]
   std::vector<double> Ed;        // q x q differentiation matrix through the q inner points
 
   // global node id of local node (k, j) of leaf (a, b); -1 at a corner
   int64_t node_id(int a, int b, int k, int j) const;
-  int64_t hseg(int e, int a) const { return (int64_t)e * nlx + a; }
-  int64_t vseg(int b, int e) const { return n_hseg + (int64_t)b * (nlx + 1) + e; }
+  int64_t hseg(int e, int a) const { return (int64_t)(e % nhl) * nlx + a; }
+  int64_t vseg(int b, int e) const { return n_hseg + (int64_t)b * nvl + (e % nvl); }
   void coords(std::vector<double>& x, std::vector<double>& y) const;
 };
 
 eo_status make_grid(int nlx, int nly, int p, double x0, double x1, double y0, double y1,
-                    Grid& g);
+                    Grid& g, int periodic = 0);
 
 // ---------------------------------------------------------------- tree plan
 // Level 0: leaves.  Level l >= 1: boxes made by merging pairs of level-(l-1)

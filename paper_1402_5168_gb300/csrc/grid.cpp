@@ -39,7 +39,7 @@ static std::vector<double> diffmat(const std::vector<double>& x) {
 static bool pow2(int v) { return v >= 1 && (v & (v - 1)) == 0; }
 
 eo_status make_grid(int nlx, int nly, int p, double x0, double x1, double y0, double y1,
-                    Grid& g) {
+                    Grid& g, int periodic) {
   if (!pow2(nlx) || !pow2(nly)) return fail(EO_ERR_INVALID_ARG, "nlx, nly must be powers of two");
   if (p < 4 || p > 24) return fail(EO_ERR_INVALID_ARG, "p must be in [4, 24]");
   if (!(x1 > x0) || !(y1 > y0)) return fail(EO_ERR_INVALID_ARG, "empty domain");
@@ -57,8 +57,11 @@ eo_status make_grid(int nlx, int nly, int p, double x0, double x1, double y0, do
   g.Ed = diffmat(inner);
   const int64_t q = g.q;
   g.n_int = (int64_t)nlx * nly * q * q;
-  g.n_hseg = (int64_t)nlx * (nly + 1);
-  g.n_vseg = (int64_t)(nlx + 1) * nly;
+  g.periodic = periodic ? 1 : 0;
+  g.nhl = periodic ? nly : nly + 1;
+  g.nvl = periodic ? nlx : nlx + 1;
+  g.n_hseg = (int64_t)nlx * g.nhl;
+  g.n_vseg = (int64_t)g.nvl * nly;
   g.n_seg = g.n_hseg + g.n_vseg;
   g.n_edge = g.n_seg * q;
   g.n_nodes = g.n_int + g.n_edge;
@@ -82,8 +85,11 @@ void Grid::coords(std::vector<double>& x, std::vector<double>& y) const {
         for (int k = 0; k < p; ++k) {
           int64_t id = node_id(a, b, k, j);
           if (id < 0) continue;
-          x[id] = x0 + (a + 0.5 * (xi[k] + 1.0)) * hx;
-          y[id] = y0 + (b + 0.5 * (xi[j] + 1.0)) * hy;
+          // on a periodic square the seams x = x1, y = y1 are the lines x = x0, y = y0
+          const bool seam_x = periodic && a == nlx - 1 && k == p - 1;
+          const bool seam_y = periodic && b == nly - 1 && j == p - 1;
+          x[id] = seam_x ? x0 : x0 + (a + 0.5 * (xi[k] + 1.0)) * hx;
+          y[id] = seam_y ? y0 : y0 + (b + 0.5 * (xi[j] + 1.0)) * hy;
         }
 }
 

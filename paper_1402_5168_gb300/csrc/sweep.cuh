@@ -273,14 +273,23 @@ struct LeafGeo {
   const double* Dy;
   const double* Ex;   // q x q
   const double* Ey;
+  int per = 0;        // periodic square: the top / right edge lines are lines 0
 };
 
+// global node id of local node (k, j) of leaf (a, b) in the public numbering; -1 at a corner
 __device__ __forceinline__ long long gnode(const LeafGeo& g, int a, int b, int k, int j) {
   const int p = g.p, q = g.q;
   const bool kin = k > 0 && k < p - 1, jin = j > 0 && j < p - 1;
   if (kin && jin) return ((long long)b * g.nlx + a) * q * q + (long long)(j - 1) * q + (k - 1);
-  if (kin) return g.n_int + ((long long)(j == 0 ? b : b + 1) * g.nlx + a) * q + (k - 1);
-  if (jin) return g.n_int + (g.n_hseg + (long long)b * (g.nlx + 1) + (k == 0 ? a : a + 1)) * q + (j - 1);
+  if (kin) {
+    const int e = j == 0 ? b : ((g.per && b + 1 == g.nly) ? 0 : b + 1);
+    return g.n_int + ((long long)e * g.nlx + a) * q + (k - 1);
+  }
+  if (jin) {
+    const int nvl = g.per ? g.nlx : g.nlx + 1;
+    const int e = k == 0 ? a : ((g.per && a + 1 == g.nlx) ? 0 : a + 1);
+    return g.n_int + (g.n_hseg + (long long)b * nvl + e) * q + (j - 1);
+  }
   return -1;
 }
 

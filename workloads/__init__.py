@@ -78,7 +78,16 @@ WAVE_32X32_P16 = Workload(
                 amp_range=(0.1, 1.0), centre_range=(0.2, 0.8)),
 )
 
-WORKLOADS = {w.name: w for w in (WAVE_4X4_P12, SW_16X16_P16, WAVE_32X32_P16)}
+# Configuration 1 on a periodic square (the setting of the paper's shallow-water
+# examples, Section 4.1): the same sizes, f, g, H, tau and Gaussian draws, summed over
+# their periodic images so that the data are smooth across the seams; the consistent
+# elimination of the velocities (its discrete step is stable on a periodic square).
+SW_PERIODIC_16X16_P16 = dataclasses.replace(
+    SW_16X16_P16, name="sw_periodic_16x16_p16_tau20T",
+    params=dict(SW_16X16_P16.params, periodic=True, consistent=True),
+)
+
+WORKLOADS = {w.name: w for w in (WAVE_4X4_P12, SW_16X16_P16, WAVE_32X32_P16, SW_PERIODIC_16X16_P16)}
 
 # Uneven batch (after configuration 3, scaled to fit the batch's operators in a
 # few tens of GB): independent instances, alternately wave (variable c, per-box
@@ -118,6 +127,7 @@ def _init_bands():
     BAND[WAVE_4X4_P12.name] = 320.0
     BAND[SW_16X16_P16.name] = sw_band(SW_16X16_P16)
     BAND[WAVE_32X32_P16.name] = wave_band(WAVE_32X32_P16)
+    BAND[SW_PERIODIC_16X16_P16.name] = sw_band(SW_PERIODIC_16X16_P16)
 
 
 def sw_band(w: Workload) -> float:
@@ -209,13 +219,18 @@ def draw_gaussians(seed: int, n: int, sigma_range, amp_range, centre_range):
     return c, s, a
 
 
-def gaussian_sum(x, y, centres, sigmas, amps) -> np.ndarray:
-    """Sum_j a_j exp(-|x - c_j|^2 / (2 s_j^2))."""
+def gaussian_sum(x, y, centres, sigmas, amps, periodic: bool = False) -> np.ndarray:
+    """Sum_j a_j exp(-|x - c_j|^2 / (2 s_j^2)); periodic=True sums each Gaussian over
+    its images shifted by -1, 0, 1 in x and y (period 1), smooth across the seams of
+    the periodic unit square."""
     x = np.asarray(x, dtype=np.float64)
     y = np.asarray(y, dtype=np.float64)
     out = np.zeros(np.broadcast(x, y).shape)
+    shifts = (-1.0, 0.0, 1.0) if periodic else (0.0,)
     for (cx, cy), s, a in zip(centres, sigmas, amps):
-        out += a * np.exp(-((x - cx) ** 2 + (y - cy) ** 2) / (2 * s * s))
+        for sx in shifts:
+            for sy in shifts:
+                out += a * np.exp(-((x - cx - sx) ** 2 + (y - cy - sy) ** 2) / (2 * s * s))
     return out
 
 
@@ -236,5 +251,5 @@ def initial_fields(w: Workload, x: np.ndarray, y: np.ndarray, rhs: int = 0) -> l
         return [u, np.zeros_like(u)]
     c, s, a = draw_gaussians(w.seed + rhs, pr["n_gauss"], pr["sigma_range"],
                              pr["amp_range"], pr["centre_range"])
-    h = gaussian_sum(x, y, c, s, a)
+    h = gaussian_sum(x, y, c, s, a, periodic=bool(pr.get("periodic", False)))
     return [np.zeros_like(h), np.zeros_like(h), h]
