@@ -98,7 +98,9 @@ class Clocks:
 
 
 def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fitter="line", root_dense=False,
-                   merge_dense=False):
+                   merge_dense=False, tensor_leaves=False):
+    # the tensor-core leaf path is a reduced-precision path of the dense leaf operators
+    tl = bool(tensor_leaves) and precision == "df32"
     if w.kind == "wave":
         c = W.wave_c(w, x, y)
         if fitter == "gauss":
@@ -108,13 +110,13 @@ def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fi
             return eo.Operator(g, eo.WAVE_DIRICHLET, band=W.BAND[w.name], tau=tau, c2=c * c, max_rhs=R,
                                precision=precision, fitter="gauss")
         return eo.Operator(g, eo.WAVE_DIRICHLET, band=W.BAND[w.name], n_poles=poles or w.n_poles, c2=c * c,
-                           max_rhs=R, precision=precision)
+                           max_rhs=R, precision=precision, tensor_leaves=tl)
     pr = w.params
     # a pole-count override (profiling cases) replaces the fixed step by tau = X(poles) / band
     return eo.Operator(g, eo.SW_WALLS, band=W.BAND[w.name], tau=0.0 if poles else w.tau, n_poles=poles,
                        f=pr["f"], g=pr["g"], H=pr["H"], shared_ops=True, max_rhs=R, precision=precision,
-                       dense_leaves=dense_leaves, fitter=fitter, root_dense=root_dense, merge_dense=merge_dense,
-                       sw_consistent=bool(pr.get("consistent", False)))
+                       dense_leaves=dense_leaves or tl, fitter=fitter, root_dense=root_dense, merge_dense=merge_dense,
+                       sw_consistent=bool(pr.get("consistent", False)), tensor_leaves=tl)
 
 
 def is_periodic(w):
@@ -250,7 +252,11 @@ def class_work(op, w, R, prec, fd, root_c4=False, merge_sym=False, periodic=Fals
 # distinct), FP32-pair precision, even/odd merge blocks and the four-block root.  Traffic
 # grows with the number of distinct poles (one block set per pole, read once), so a full
 # step scales it by P / 151.  Keys: (workload, precision, class).
-NCU_TRAFFIC_151 = {}
+NCU_TRAFFIC_151 = {
+    ("sw_walls_16x16_p16_tau20T", "df32", "up_merge"): 0.4365e9,
+    ("sw_walls_16x16_p16_tau20T", "df32", "down_merge"): 0.2945e9,
+    ("sw_walls_16x16_p16_tau20T", "df32", "root"): 0.4877e9,
+}
 
 
 def alu_peak(prec):
@@ -334,7 +340,7 @@ def run_ours(args):
     x, y = g.nodes()
     t0 = time.time()
     op = build_operator(eo, w, g, x, y, R, args.precision, args.poles, args.dense_leaves, args.fitter,
-                        args.root_dense, args.merge_dense)
+                        args.root_dense, args.merge_dense, args.tensor_leaves)
     # the library splits the wall solve of a square walled domain of square leaves into
     # four Fourier blocks unless told not to
     root_c4 = w.kind == "sw" and w.nlx == w.nly and not args.root_dense and not per
@@ -342,7 +348,8 @@ def run_ours(args):
     # (not on periodic grids, nor with the consistent elimination's curl term)
     consistent = bool(w.params.get("consistent", False))
     merge_sym = w.kind == "sw" and not args.merge_dense and not per and not consistent
-    fd = w.kind == "sw" and not args.dense_leaves and not consistent
+    tl = bool(args.tensor_leaves) and args.precision == "df32"
+    fd = w.kind == "sw" and not args.dense_leaves and not consistent and not tl
     torch.cuda.synchronize()
     build_s = time.time() - t0
     U0 = np.stack([np.stack(W.initial_fields(w, x, y, r)) for r in range(R)])
@@ -416,7 +423,9 @@ def run_ours(args):
                    "elimination": ("consistent (curl of the recovered gradient kept)" if consistent
                                    else "as the paper writes it") if w.kind == "sw" else None,
                    "leaves": f"{w.nlx}x{w.nly}",
-                   "leaf_solves": "fast diagonalisation" if fd else "dense leaf operators",
+                   "leaf_solves": "fast diagonalisation" if fd else (
+                       "dense leaf operators on the tensor cores (tcgen05, 5 bf16 slices of 7 bits, FP32 "
+                       "accumulation in TMEM, pole sum in FP32 pairs)" if tl else "dense leaf operators"),
                    "merges": ("even/odd blocks of the reflection symmetries" if merge_sym else "dense blocks")
                    if w.kind == "sw" else "dense blocks",
                    "root": ("seam system of the root box merged with itself" if per else
@@ -693,6 +702,8 @@ def main():
                     help="apply the dense merge blocks instead of the even/odd reflection blocks")
     ap.add_argument("--fitter", default="line", choices=["line", "gauss"],
                     help="line: our least-squares approximant; gauss: the paper's Gaussian-sum construction")
+    ap.add_argument("--tensor-leaves", action="store_true",
+                    help="leaf interior solves and pole sum on the tensor cores (bf16 slices, tcgen05)")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
