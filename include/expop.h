@@ -132,6 +132,20 @@ typedef struct {
                           checks the symmetry to 1e-9 and fails with
                           EO_ERR_UNSUPPORTED if it does not hold; the dense blocks stay
                           for eo_apply_adjoint).  1: dense merge blocks only        */
+  int tensor_leaves;   /* 1: the leaf interior solves and the pole sum run on the tensor
+                          cores (tcgen05.mma on bf16 slices, FP32 accumulation in TMEM):
+                          the dense leaf operators of every pole, times the pre-map
+                          coefficients, [c_0 X | ... | c_{K-1} X | Y], are split at build
+                          time into 5 bf16 slices of 7 bits per real part with a
+                          power-of-two scale per row (about 2^-34 relative per entry); the
+                          right-hand sides are split the same way per column on every step;
+                          the two leading product levels are summed exactly in FP32, the
+                          rest rounded at about 2^-38, and the pole sum is kept in FP32
+                          pairs.  Needs EO_PREC_DF32, dense leaves (per-box operators, or
+                          opts.dense_leaves with shared ones) and p <= 18; otherwise the
+                          build fails with EO_ERR_UNSUPPORTED.  Holds 2 x 5 x 2 bytes per
+                          entry of [c_0 X | ... | Y] (rows padded to 256) besides the
+                          dense operators, which eo_apply_adjoint keeps using.  0: off */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.
@@ -338,6 +352,12 @@ eo_status eo_batch_destroy(eo_batch_t batch);
 eo_status eo_set_timing(eo_handle_t h, int on);
 eo_status eo_get_timing(eo_handle_t h, int *n_classes, const char **names, int64_t *launches,
                         double *ms);
+
+/* Device status of the handle's kernels: every wait of the tensor-core kernels is
+ * bounded; a wait that gave up sets a status word and the kernel returns.  This call
+ * synchronises `stream`, reads the word, and returns EO_ERR_TIMEOUT (*flag = 1) if any
+ * kernel of the handle gave up since the build, EO_OK (*flag = 0) otherwise. */
+eo_status eo_device_status(eo_handle_t h, void *stream, int *flag);
 
 /* Release device memory.  Idempotent on NULL. */
 eo_status eo_destroy(eo_handle_t h);

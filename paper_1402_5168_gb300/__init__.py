@@ -105,7 +105,7 @@ class Operator:
                  c2=None, f=0.0, g=1.0, H=1.0, delta=1e-10, shared_ops=False, max_rhs=1,
                  mem_budget_gb=0.0, precision="fp64", fp64_top_levels=0, use_graphs=True, dense_leaves=False,
                  autotune=True, sw_consistent=False, fitter="line", gauss_h=0.0, root_dense=False,
-                 merge_dense=False, stream=None):
+                 merge_dense=False, tensor_leaves=False, stream=None):
         L = _capi.lib()
         prec = {"fp64": 0, "fp32": 1, "df32": 2}[precision]
         fit_kind = {"line": 0, "gauss": 1}[fitter]
@@ -113,7 +113,8 @@ class Operator:
                  shared_ops=int(shared_ops), max_rhs=max_rhs, mem_budget_gb=mem_budget_gb,
                  fp64_top_levels=fp64_top_levels, use_graphs=int(use_graphs), dense_leaves=int(dense_leaves),
                  autotune=int(autotune), sw_consistent=int(sw_consistent), fitter=fit_kind,
-                 gauss_h=gauss_h, root_dense=int(root_dense), merge_dense=int(merge_dense))
+                 gauss_h=gauss_h, root_dense=int(root_dense), merge_dense=int(merge_dense),
+                 tensor_leaves=int(tensor_leaves))
         coeff = None
         if c2 is not None:
             self._c2 = np.ascontiguousarray(c2, dtype=np.float64)

@@ -532,6 +532,12 @@ eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double* coeff, c
   cudaStream_t st = (cudaStream_t)stream;
   eo_status rc = setup(h, *opts, st);
   if (!rc) rc = build(h, coeff, st);
+  if (!rc && opts->tensor_leaves) {
+    // split the FP64 leaf operators for the tensor cores before reduced copies replace them
+    std::string why;
+    if (!tc_eligible(h, &why)) rc = fail(EO_ERR_UNSUPPORTED, "tensor_leaves: " + why);
+    else rc = tc_build(h, st);
+  }
   if (!rc && opts->precision != EO_PREC_FP64) rc = to_reduced(h, opts->precision, st);
   if (rc) {
     delete hs;
@@ -677,6 +683,15 @@ eo_status eo_memory(eo_handle_t hd, int64_t* operator_bytes, int64_t* workspace_
 eo_status eo_apply(eo_handle_t hd, double* u_dev, int n_rhs, int n_steps, void* stream) {
   if (!hd) return fail(EO_ERR_INVALID_ARG, "null handle");
   return apply(hd->h, u_dev, n_rhs, n_steps, (cudaStream_t)stream);
+}
+
+eo_status eo_device_status(eo_handle_t hd, void* stream, int* flag) {
+  if (!hd || !flag) return fail(EO_ERR_INVALID_ARG, "null argument");
+  eo_status rc = tc_status(hd->h, (cudaStream_t)stream, flag);
+  if (rc) return rc;
+  if (*flag) return fail(EO_ERR_TIMEOUT, "a bounded device wait gave up");
+  set_error("");
+  return EO_OK;
 }
 
 eo_status eo_apply_adjoint(eo_handle_t hd, double* y_dev, int n_rhs, int n_steps, void* stream) {

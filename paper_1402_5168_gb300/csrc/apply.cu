@@ -1034,6 +1034,8 @@ eo_status finish_step(Handle& h, const Sweep& s, const double* uin, double* uout
   if ((rc = h.trace_begin(st))) return rc;
   if (h.fd) {
     if ((rc = fd_down_leaf(h, s, nleaf, h.fd_ncol_down, nchunk, st))) return rc;
+  } else if (h.tc) {
+    if ((rc = tc_down_leaf(h, s, nchunk, st))) return rc;
   } else {
     const int nc = pick_nc(h.shared, R, ni + nb, ni, nleaf);
     const int ncg = (nleaf * R + nc - 1) / nc;

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 
 #include <complex>
+#include <string>
 #include <vector>
 
 #include "engine.h"
@@ -142,6 +143,15 @@ struct Handle {
   cd* fd_wd = nullptr;          // workspace [P][K][q*q] pole-sum weight * dinv_p
   double* fd_gsum = nullptr;    // workspace [K][K][q*q] pole-summed particular part
   double* fd_ghat = nullptr;    // workspace [rhs][K][n_int] sources in the eigenbasis
+  // tensor-core leaf down-solves (tc.cu): bf16 slices of [c_0 X | ... | Y] per pole
+  // and operator box, split exponents, per-step source slices, device status word
+  int tc = 0;                   // slices per value (0: off)
+  int tc_nks = 0, tc_nke = 0;   // K steps of the source block and of the edge block
+  void* tc_A = nullptr;
+  int* tc_Aexp = nullptr;
+  void* tc_B = nullptr;
+  int* tc_Bexp = nullptr;
+  int* tc_status = nullptr;
   int64_t op_bytes = 0, ws_bytes = 0;
   Tuned root_tuned;             // autotuned launch shape of the root wall solve
   int tuned_R = 0;              // n_rhs the launch shapes were tuned for (0: not tuned)
@@ -206,5 +216,11 @@ eo_status fd_up_leaf(Handle& h, const Sweep& s, int nleaf, cd* h0, cudaStream_t 
 eo_status fd_up_kernel(Handle& h, const Sweep& s, int nleaf, cd* h0, int ncol, cudaStream_t st);
 eo_status fd_down_leaf(Handle& h, const Sweep& s, int nleaf, int ncol, int& nchunk, cudaStream_t st);
 std::vector<int> fd_ncol_candidates(const Handle& h);
+
+// tensor-core leaf down-solves (tc.cu)
+bool tc_eligible(const Handle& h, std::string* why);
+eo_status tc_build(Handle& h, cudaStream_t st);
+eo_status tc_down_leaf(Handle& h, const Sweep& s, int& nchunk, cudaStream_t st);
+eo_status tc_status(Handle& h, cudaStream_t st, int* out);
 
 }  // namespace eo
