@@ -134,18 +134,18 @@ typedef struct {
                           for eo_apply_adjoint).  1: dense merge blocks only        */
   int tensor_leaves;   /* 1: the leaf interior solves and the pole sum run on the tensor
                           cores (tcgen05.mma on bf16 slices, FP32 accumulation in TMEM):
-                          the dense leaf operators of every pole, times the pre-map
-                          coefficients, [c_0 X | ... | c_{K-1} X | Y], are split at build
-                          time into 5 bf16 slices of 7 bits per real part with a
-                          power-of-two scale per row (about 2^-34 relative per entry); the
-                          right-hand sides are split the same way per column on every step;
-                          the two leading product levels are summed exactly in FP32, the
-                          rest rounded at about 2^-38, and the pole sum is kept in FP32
-                          pairs.  Needs EO_PREC_DF32, dense leaves (per-box operators, or
-                          opts.dense_leaves with shared ones) and p <= 18; otherwise the
-                          build fails with EO_ERR_UNSUPPORTED.  Holds 2 x 5 x 2 bytes per
-                          entry of [c_0 X | ... | Y] (rows padded to 256) besides the
-                          dense operators, which eo_apply_adjoint keeps using.  0: off */
+                          the dense leaf operators [X | Y] of every pole are split at build
+                          time into 5 bf16 slices of 7 bits per real part, with a
+                          power-of-two scale per row and block (about 2^-34 relative per
+                          entry); per step and pole the right-hand sides g = sum_k c_k s_k
+                          (formed in FP32 pairs) and the edge values are split the same way
+                          per column and block; the two leading product levels are summed
+                          exactly in FP32, the rest rounded at about 2^-38, and the pole sum
+                          is kept in FP32 pairs.  Needs EO_PREC_DF32, dense leaves (per-box
+                          operators, or opts.dense_leaves with shared ones) and p <= 18;
+                          otherwise the build fails with EO_ERR_UNSUPPORTED.  Holds 20 bytes
+                          per entry of [X | Y] (rows padded to 256) besides the dense
+                          operators, which eo_apply_adjoint keeps using.  0: off          */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.

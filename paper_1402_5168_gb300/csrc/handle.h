@@ -143,14 +143,13 @@ struct Handle {
   cd* fd_wd = nullptr;          // workspace [P][K][q*q] pole-sum weight * dinv_p
   double* fd_gsum = nullptr;    // workspace [K][K][q*q] pole-summed particular part
   double* fd_ghat = nullptr;    // workspace [rhs][K][n_int] sources in the eigenbasis
-  // tensor-core leaf down-solves (tc.cu): bf16 slices of [c_0 X | ... | Y] per pole
-  // and operator box, split exponents, per-step source slices, device status word
+  // tensor-core leaf down-solves (tc.cu): bf16 slices of [X | Y] per pole and operator
+  // box with their row exponents, the sources as FP32 pairs, a device status word
   int tc = 0;                   // slices per value (0: off)
-  int tc_nks = 0, tc_nke = 0;   // K steps of the source block and of the edge block
+  int tc_nks = 0, tc_nke = 0;   // K steps of the X block and of the Y block
   void* tc_A = nullptr;
   int* tc_Aexp = nullptr;
-  void* tc_B = nullptr;
-  int* tc_Bexp = nullptr;
+  void* tc_B = nullptr;         // float2 [R][K][n_int]
   int* tc_status = nullptr;
   int64_t op_bytes = 0, ws_bytes = 0;
   Tuned root_tuned;             // autotuned launch shape of the root wall solve

@@ -3,7 +3,7 @@
 //
 // Split (an error-free transformation in the style of Ozaki et al.): a real value v
 // with |v| < 2^(e-1) is written as v = 2^e * sum_{i=1..S} t_i 2^(-7 i) + r with
-// integers |t_1| <= 63, |t_i| <= 127 (truncation of the fixed-point expansion of
+// integers |t_1| <= 64, |t_i| <= 127 (truncation of the fixed-point expansion of
 // v / 2^e, sign carried by every t_i) and |r| < 2^(e - 7 S).  Each slice
 // t_i 2^(-7 i) is exact in bf16.  A product of two slices is t_i u_j 2^(-7 (i+j));
 // all products of one level l = i + j share the factor 2^(-7 l), so their sum over
@@ -14,6 +14,7 @@
 
 #include <cuda_bf16.h>
 
+#include <cmath>
 #include <cstdint>
 
 namespace eo {
@@ -64,6 +65,34 @@ __device__ __forceinline__ void split_value(double v, int e, float* out) {
   for (int i = 1; i <= S; ++i) {
     const int t = (int)((T >> (BITS * (S - i))) & 127);
     out[i - 1] = sg * __int2float_rn(t) * __int_as_float((127 - BITS * i) << 23);   // t 2^(-7 i)
+  }
+}
+
+// Exponent e with |x| < 2^(e-1) for a float magnitude x > 0 (0: INT_MIN / 2, below
+// every other exponent).
+__device__ __forceinline__ int split_exponent_f(float x) {
+  const int b = __float_as_int(x) & 0x7FFFFFFF;
+  if (b == 0) return -(1 << 30);
+  return ((b >> 23) & 0xFF) - 126 + 1;   // x in [2^(E-127), 2^(E-126))
+}
+
+// The S slices of the FP32 pair value hi + lo relative to 2^e (|hi + lo| < 2^(e-1),
+// up to a relative 2^-20), by rounding to nearest instead of truncation: digit i is
+// y rounded to a multiple of 2^(-7 i) by adding and subtracting 1.5 * 2^(23 - 7 i)
+// (exact in FP32 for |y| below 2^(22 - 7 i)), and the remainder y - digit is exact.
+// The low part joins the remainder after the third digit (rounding there is below
+// 2^-46 of 2^e).  |t_i| <= 64 for every digit.  FP32 additions only.
+template <int S>
+__device__ __forceinline__ void split_pair_rn(float hi, float lo, int e, float* out) {
+  float y = ldexpf(hi, -e);
+  const float yl = ldexpf(lo, -e);
+#pragma unroll
+  for (int i = 1; i <= S; ++i) {
+    if (i == 4) y = __fadd_rn(y, yl);
+    const float c = __int_as_float((127 + 23 - BITS * i) << 23) * 1.5f;   // 1.5 * 2^(23 - 7 i)
+    const float t = __fsub_rn(__fadd_rn(y, c), c);
+    y = __fsub_rn(y, t);
+    out[i - 1] = t;
   }
 }
 
