@@ -189,6 +189,22 @@ def plan_levels(nlx, nly, q):
     return out
 
 
+TC_SLICES, TC_MT, TC_NT, TC_KS = 6, 128, 32, 16
+
+
+def tensor_flops(w, P, R, shared):
+    """bf16 MMA flops the tensor-core leaf down-solve issues in one step: per pole,
+    right-hand-side tile (32 columns) and M tile (128 operator rows), every slice pair
+    (i + j <= S + 1) of every K step of the X and Y blocks, four real products each."""
+    q = w.p - 2
+    ni, nb = q * q, 4 * q
+    nleaf = w.nlx * w.nly
+    tiles = -(-nleaf * R // TC_NT) if shared else nleaf * (-(-R // TC_NT))
+    ksteps = -(-ni // TC_KS) + -(-nb // TC_KS)
+    pairs = TC_SLICES * (TC_SLICES + 1) // 2
+    return float(P) * tiles * 2 * ksteps * pairs * 4 * 2.0 * TC_MT * TC_NT * TC_KS
+
+
 def class_work(op, w, R, prec, fd, root_c4=False, merge_sym=False, periodic=False):
     """Algorithmic FP64-equivalent flops (8 per complex multiply-add) and bytes
     of one step, per kernel class, with the arithmetic precision of each.
@@ -265,7 +281,7 @@ def alu_peak(prec):
     return {"fp32": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS, "df32": FP32_PEAK_TFLOPS / 2 / 48 * 8}[prec]
 
 
-def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False, merge_sym=False, periodic=False):
+def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False, merge_sym=False, periodic=False, tl=False):
     """Per kernel class: algorithmic work of one step over that class's device
     time per step (CUDA events around its launches), against the ALU peak of
     its arithmetic and the measured HBM copy bandwidth; the class with the
@@ -304,6 +320,17 @@ def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False, merge_sym=Fals
                                           "multiply-add (this algorithm's instruction count, not a chip roof)"}[
                                       d["precision"]]}}
     P = int((op.alpha.imag >= 0).sum())
+    if tl and top == "down_leaf":
+        # the tensor-core leaf kernel: issued bf16 MMA work against the measured bf16 peak
+        # (sustained: the kernel runs inside a long step)
+        tf = tensor_flops(w, P, R, shared=(w.kind == "sw")) / (d["ms_per_step"] / 1e3) / 1e12
+        peak = pk.get("bf16_tflops_sustained", pk.get("bf16_tflops", 1900.0))
+        rf = {"bound": "tensor", "achieved": tf, "peak": peak, "unit": "TFLOP/s", "frac": tf / peak,
+              "peak_source": pk_kind + " (MEASURED_PEAKS.json bf16_tflops_sustained, cuBLAS bf16 GEMM)",
+              "work": "bf16 tcgen05.mma flops issued (6 slices, 21 slice pairs, 4 real products per "
+                      "complex product)", "hbm": {"achieved_gbs": d["gbs"], "frac": d["hbm_frac"]},
+              "alu": rf["alu"]}
+        kname = "k_tc_down_leaf<6>"
     tr = NCU_TRAFFIC_151.get((w.name, prec, top)) if R == 1 else None
     rf.update({"kernel": kname, "class": top, "traffic": None if tr is None else tr * P / 151 / d["launches_per_step"],
                "traffic_note": None if tr is None else
@@ -449,7 +476,7 @@ def run_ours(args):
         **fp64,
         "kernel_share": shares,
         "roofline": roofline(op, w, R, tim, args.precision, pk, pk_kind, fd=fd, root_c4=root_c4, merge_sym=merge_sym,
-                             periodic=per),
+                             periodic=per, tl=tl),
         "clocks": clocks,
     }
     if args.cpu_baseline:

@@ -300,6 +300,8 @@ eo_status eo_apply_resolvent_noalloc(eo_handle_t h, int j, const double *u_dev, 
  * sum_m b_m / (z - alpha_m) approximates, on the handle's band z = i x, |x| <= X:
  *   kind EO_FN_EXP (0):    exp(c z), 0 < c <= 1   (exp(c tau L): output inside the step)
  *   kind EO_FN_PHI1 (1):   phi1(z) = (exp(z) - 1) / z
+ *   kind EO_FN_PHI2 (3):   phi2(z) = (exp(z) - 1 - z) / z^2 (both the phi-functions of
+ *                          exponential integrators, Section 3.1)
  *   kind EO_FN_FILTER (2): EO_FIT_GAUSS only: the rational partition of unity
  *                          chi(x) = sum_{|m|<=M0} psi_h(x + m h), x = z / (2 pi i),
  *                          M0 = floor(c M), 0 < c <= 1 (the filter S of Section 3.3,
@@ -314,6 +316,7 @@ eo_status eo_apply_resolvent_noalloc(eo_handle_t h, int j, const double *u_dev, 
 #define EO_FN_EXP 0
 #define EO_FN_PHI1 1
 #define EO_FN_FILTER 2
+#define EO_FN_PHI2 3
 eo_status eo_fit_function(eo_handle_t h, int kind, double c, double *b, double *err);
 
 /* out_dev[k] = f_k(tau L) u for n_out residue sets b_sets[k] (each n complex

@@ -87,6 +87,20 @@ def phi1_coeffs(M: int, h: float, n_quad: int = 400) -> np.ndarray:
     return c
 
 
+def phi2_coeffs(M: int, h: float, n_quad: int = 400) -> np.ndarray:
+    """c_m of phi2(2 pi i x) = (e^{2 pi i x} - 1 - 2 pi i x) / (2 pi i x)^2
+    = int_0^1 (1 - s) e^{2 pi i s x} ds: the exp coefficients weighted by (1 - s),
+    integrated over s by Gauss-Legendre quadrature (Section 3.1, the phi-functions)."""
+    s, w = np.polynomial.legendre.leggauss(n_quad)
+    s = 0.5 * (s + 1.0)
+    w = 0.5 * w
+    m = np.arange(-M, M + 1)
+    c = np.zeros(2 * M + 1, dtype=np.complex128)
+    for k in range(n_quad):
+        c += w[k] * (1.0 - s[k]) * h * np.exp(-2j * np.pi * m * h * s[k]) / psi_h_hat(s[k], h)
+    return c
+
+
 def window_coeffs(M: int, M0: int) -> np.ndarray:
     """c_m of the partition of unity chi(x) = sum_{|m|<=M0} psi_h(x + m h)
     (eq. "partition of unity-1"), embedded in m = -M..M."""

@@ -177,13 +177,13 @@ class Operator:
 
     def fit_function(self, kind: str = "exp", c: float = 1.0):
         """Residues (numpy complex, eo_get_poles order) of exp(c z) ("exp"), phi1(z)
-        ("phi1") or, for fitter="gauss", the partition-of-unity filter keeping a
+        ("phi1"), phi2(z) ("phi2") or, for fitter="gauss", the partition-of-unity filter keeping a
         fraction c of the Gaussians ("filter") on this operator's poles, and the
         band error."""
         n = self.alpha.size
         b = np.zeros(2 * n)
         err = C.c_double()
-        check(_capi.lib().eo_fit_function(self._h, {"exp": 0, "phi1": 1, "filter": 2}[kind], c,
+        check(_capi.lib().eo_fit_function(self._h, {"exp": 0, "phi1": 1, "filter": 2, "phi2": 3}[kind], c,
                                           b.ctypes.data_as(C.POINTER(C.c_double)), C.byref(err)))
         return b[0::2] + 1j * b[1::2], err.value
 

@@ -606,6 +606,48 @@ static void phi1_coeffs(int M, double h, std::vector<cplx>& c) {
   c[M] = c[M].real();
 }
 
+// c_m of phi2(2 pi i x) = int_0^1 (1 - s) e^{2 pi i s x} ds: the exp coefficients
+// weighted by (1 - s) and integrated over s, by the same panels as phi1_coeffs.
+static void phi2_coeffs(int M, double h, std::vector<cplx>& c) {
+  std::vector<double> gx, gw;
+  gauss_legendre01(16, gx, gw);
+  const int panels = std::max(4, (int)std::ceil(2.0 * M_PI * M * h / 2.0) + 1);
+  c.assign(2 * (size_t)M + 1, cplx(0, 0));
+  par_for(M + 1, [&](int64_t m0, int64_t m1) {
+    for (int64_t m = m0; m < m1; ++m) {
+      cplx acc(0, 0);
+      for (int pnl = 0; pnl < panels; ++pnl)
+        for (int k = 0; k < 16; ++k) {
+          const double s = (pnl + gx[k]) / panels;
+          acc += (gw[k] / panels) * (1.0 - s) * std::exp(4.0 * M_PI * M_PI * h * h * s * s) *
+                 std::exp(cplx(0.0, -2.0 * M_PI * m * h * s));
+        }
+      c[M + m] = acc;
+    }
+  });
+  for (int m = 1; m <= M; ++m) c[M - m] = std::conj(c[M + m]);
+  c[M] = c[M].real();
+}
+
+// phi1(z) = (e^z - 1) / z and phi2(z) = (e^z - 1 - z) / z^2 on z = i theta, by their
+// Taylor series near 0 (where the closed forms cancel)
+static cplx phi_value(int j, double th) {
+  const cplx z(0.0, th);
+  if (std::abs(th) < 0.5) {
+    // sum_k z^k / (k + j)!, k = 0 .. 20 (remainder below 1e-25)
+    cplx term = 1.0, acc = 0.0;
+    double fact = j == 1 ? 1.0 : 2.0;   // j!
+    for (int k = 0; k <= 20; ++k) {
+      acc += term / fact;
+      term *= z;
+      fact *= (double)(k + j + 1);
+    }
+    return acc;
+  }
+  if (j == 1) return (std::exp(z) - 1.0) / z;
+  return (std::exp(z) - 1.0 - z) / (z * z);
+}
+
 // max over theta in [t0, t1] (step dt) of |g(theta) - R(i theta)|.
 static double band_err(const std::vector<cplx>& al, const std::vector<cplx>& b, double t0, double t1,
                        double dt, const std::function<cplx(double)>& g) {
@@ -671,10 +713,10 @@ static eo_status fit_function_gauss(const Fit& f, int kind, double c, std::vecto
     g = [c](double th) { return std::exp(cplx(0.0, c * th)); };
   } else if (kind == 1) {
     phi1_coeffs(M, h, cm);
-    g = [](double th) {
-      if (std::abs(th) < 1e-6) return cplx(1.0 - th * th / 6.0, th / 2.0 - th * th * th / 24.0);
-      return (std::exp(cplx(0.0, th)) - 1.0) / cplx(0.0, th);
-    };
+    g = [](double th) { return phi_value(1, th); };
+  } else if (kind == 3) {
+    phi2_coeffs(M, h, cm);
+    g = [](double th) { return phi_value(2, th); };
   } else {
     if (!(c > 0 && c <= 1)) return fail(EO_ERR_INVALID_ARG, "filter fraction must be in (0, 1]");
     const int M0 = (int)std::floor(c * M);
@@ -700,11 +742,11 @@ static eo_status fit_function_gauss(const Fit& f, int kind, double c, std::vecto
 // ---------------------------------------------------------------- other functions, same poles
 // Values on the imaginary axis of the functions the same poles can carry
 // (dense output and phi-functions, Section 1.2 remarks on reusing the solves):
-//   kind 0: exp(c z), 0 < c <= 1;   kind 1: phi1(z) = (exp(z) - 1) / z.
+//   kind 0: exp(c z), 0 < c <= 1;   kind 1: phi1(z) = (exp(z) - 1) / z;
+//   kind 3: phi2(z) = (exp(z) - 1 - z) / z^2.
 static cplx fn_value(int kind, double c, double th) {
   if (kind == 0) return std::exp(cplx(0.0, c * th));
-  if (std::abs(th) < 1e-6) return cplx(1.0 - th * th / 6.0, th / 2.0 - th * th * th / 24.0);
-  return (std::exp(cplx(0.0, th)) - 1.0) / cplx(0.0, th);
+  return phi_value(kind == 3 ? 2 : 1, th);
 }
 
 // Residues b of sum_m b_m / (z - alpha_m) on the poles of `f` for the function
@@ -713,10 +755,11 @@ static cplx fn_value(int kind, double c, double th) {
 // the Cauchy integral of the function along the pole line (spacing s),
 //   exp(c z):  b_m = -(s / 2 pi) exp(c alpha_m),
 //   phi1(z):   b_m = -(s / 2 pi) (exp(alpha_m) - 1) / alpha_m  (the integral over c in [0, 1]),
+//   phi2(z):   b_m = -(s / 2 pi) (exp(alpha_m) - 1 - alpha_m) / alpha_m^2,
 // and the E outermost pairs by least squares, as for exp(z) itself.
 // err: max |f(i x) - R(i x)| on [0, X] (both signs by conjugate symmetry).
 eo_status fit_function(const Fit& f, int kind, double c, std::vector<cplx>& b, double& err) {
-  if (kind != 0 && kind != 1 && kind != 2) return fail(EO_ERR_INVALID_ARG, "unknown function kind");
+  if (kind < 0 || kind > 3) return fail(EO_ERR_INVALID_ARG, "unknown function kind");
   if (kind == 0 && !(c > 0 && c <= 1)) return fail(EO_ERR_INVALID_ARG, "c must be in (0, 1]");
   if (f.gh > 0) return fit_function_gauss(f, kind, c, b, err);
   if (kind == 2) return fail(EO_ERR_UNSUPPORTED, "the filter needs the Gaussian-sum fitter");
@@ -729,7 +772,9 @@ eo_status fit_function(const Fit& f, int kind, double c, std::vector<cplx>& b, d
   if (f.E > 0) {
     for (int m = 0; m <= M; ++m) {
       const cplx a = al[m + M];
-      b[m + M] = kind == 0 ? -(s / (2 * M_PI)) * std::exp(c * a) : -(s / (2 * M_PI)) * (std::exp(a) - 1.0) / a;
+      const cplx fa = kind == 0 ? std::exp(c * a)
+                                : (kind == 1 ? (std::exp(a) - 1.0) / a : (std::exp(a) - 1.0 - a) / (a * a));
+      b[m + M] = -(s / (2 * M_PI)) * fa;
       b[M - m] = std::conj(b[m + M]);
     }
     b[M] = b[M].real();

@@ -25,6 +25,14 @@ def phi1(th):
     return out
 
 
+def phi2(th):
+    z = 1j * th
+    out = 0.5 + z / 6 + z * z / 24 + z ** 3 / 120 + z ** 4 / 720
+    nz = np.abs(th) > 1e-2
+    out[nz] = (np.exp(z[nz]) - 1 - z[nz]) / z[nz] ** 2
+    return out
+
+
 @pytest.fixture(scope="module")
 def wave():
     import paper_1402_5168_gb300 as eo
@@ -45,7 +53,7 @@ def test_function_residues_meet_their_band_error(n_poles):
     op = eo.Operator(g, eo.SW_WALLS, band=60.0, n_poles=n_poles, f=10.0, g=1.0, H=1.0, shared_ops=True)
     th = np.linspace(-op.X, op.X, 20001)
     for kind, c, f in [("exp", 0.5, lambda t: np.exp(0.5j * t)), ("exp", 0.25, lambda t: np.exp(0.25j * t)),
-                       ("exp", 1.0, lambda t: np.exp(1j * t)), ("phi1", 1.0, phi1)]:
+                       ("exp", 1.0, lambda t: np.exp(1j * t)), ("phi1", 1.0, phi1), ("phi2", 1.0, phi2)]:
         b, err = op.fit_function(kind, c)
         assert np.array_equal(b[::-1], np.conj(b))
         brute = np.abs(f(th) - rational.R_eval(1j * th, op.alpha, b)).max()
@@ -54,13 +62,17 @@ def test_function_residues_meet_their_band_error(n_poles):
         # exp(cz) to the step's own accuracy; phi1 on wide pole sets (trapezoidal
         # centre + fitted ends) reaches ~3e-8
         assert err <= (1e-8 if kind == "exp" or n_poles <= 101 else 1e-7)
+        if kind == "phi2":
+            # phi2 is not phi1: the residue sets differ on the band
+            b1, _ = op.fit_function("phi1", 1.0)
+            assert np.abs(rational.R_eval(1j * th, op.alpha, b1) - f(th)).max() > 1e-2
 
 
 def test_shared_sweep_outputs_match_the_oracle(wave):
     eo, g, op, prob, u0 = wave
-    sets = [op.fit_function("exp", 0.5)[0], op.b, op.fit_function("phi1")[0]]
+    sets = [op.fit_function("exp", 0.5)[0], op.b, op.fit_function("phi1")[0], op.fit_function("phi2")[0]]
     u = torch.tensor(u0, device="cuda")
-    out = torch.zeros((3, 2, g.n_nodes), dtype=torch.float64, device="cuda")
+    out = torch.zeros((4, 2, g.n_nodes), dtype=torch.float64, device="cuda")
     op.apply_functions(sets, u, out)
     got = out.cpu().numpy()
     for k, b in enumerate(sets):

@@ -87,10 +87,11 @@ def test_wave_step_and_function_residues(wave):
     e = rel(u.cpu().numpy(), Stepper(prob, alpha, b).step(u0))
     print(f"wave gauss step: rel L2 vs oracle {e:.2e}")
     assert e <= 1e-10
-    # exp(c z), phi1 and the filter on the same poles: the library's residues are the
+    # exp(c z), phi1, phi2 and the filter on the same poles: the library's residues are the
     # oracle's Gaussian coefficients composed through Table 1
     ae = gauss.even_table(A)
     for kind, c, coef in [("exp", 0.5, gauss.exp_coeffs(M, H, 0.5)), ("phi1", 1.0, gauss.phi1_coeffs(M, H)),
+                          ("phi2", 1.0, gauss.phi2_coeffs(M, H)),
                           ("filter", 0.9, gauss.window_coeffs(M, int(np.floor(0.9 * M))))]:
         bl, err = op.fit_function(kind, c)
         bo = gauss.compose(coef, H, MU, ae)[1]

@@ -70,6 +70,20 @@ def test_phi1_coefficients():
     assert err.max() <= 1e-10
 
 
+def test_phi2_coefficients():
+    # phi2(z) = (e^z - 1 - z) / z^2 at z = 2 pi i x; near 0 by its series 1/2 + z/6 + z^2/24
+    h, M = 0.18, 120
+    x = np.linspace(-(M - 10) * h, (M - 10) * h, 4001)
+    z = 2j * np.pi * x
+    want = np.where(np.abs(z) > 1e-3, (np.exp(z) - 1 - z) / np.where(z == 0, 1, z) ** 2,
+                    0.5 + z / 6 + z * z / 24 + z ** 3 / 120)
+    err = np.abs(gauss.gauss_sum(x, gauss.phi2_coeffs(M, h), h) - want)
+    assert err.max() <= 1e-10
+    # a plausible slip (the phi1 weight) is caught
+    err1 = np.abs(gauss.gauss_sum(x, gauss.phi1_coeffs(M, h), h) - want)
+    assert err1.max() > 0.1
+
+
 def test_even_table_is_no_worse_and_conjugate_symmetric():
     ae = gauss.even_table(A)
     assert np.array_equal(ae[::-1], np.conj(ae))

@@ -1,5 +1,6 @@
 """Leaf interior solves with the pole sum on the tensor cores (opts.tensor_leaves):
-bf16 slices of [c_0 X | ... | Y], tcgen05.mma with FP32 accumulation in TMEM.
+bf16 slices of the dense leaf operators [X | Y] and of the right-hand sides,
+tcgen05.mma with FP32 accumulation in TMEM.
 
 Against the FP64 oracle, column by column (tolerance TOL: the precision class of the
 bf16 split, between FP32 and FP64):
