@@ -98,7 +98,7 @@ class Clocks:
 
 
 def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fitter="line", root_dense=False,
-                   merge_dense=False, tensor_leaves=False):
+                   merge_dense=False, tensor_leaves=False, merge_fuse=0):
     # the tensor-core leaf path is a reduced-precision path of the dense leaf operators
     tl = bool(tensor_leaves) and precision == "df32"
     if w.kind == "wave":
@@ -110,13 +110,13 @@ def build_operator(eo, w, g, x, y, R, precision, poles=0, dense_leaves=False, fi
             return eo.Operator(g, eo.WAVE_DIRICHLET, band=W.BAND[w.name], tau=tau, c2=c * c, max_rhs=R,
                                precision=precision, fitter="gauss")
         return eo.Operator(g, eo.WAVE_DIRICHLET, band=W.BAND[w.name], n_poles=poles or w.n_poles, c2=c * c,
-                           max_rhs=R, precision=precision, tensor_leaves=tl)
+                           max_rhs=R, precision=precision, tensor_leaves=tl, merge_fuse=merge_fuse)
     pr = w.params
     # a pole-count override (profiling cases) replaces the fixed step by tau = X(poles) / band
     return eo.Operator(g, eo.SW_WALLS, band=W.BAND[w.name], tau=0.0 if poles else w.tau, n_poles=poles,
                        f=pr["f"], g=pr["g"], H=pr["H"], shared_ops=True, max_rhs=R, precision=precision,
                        dense_leaves=dense_leaves or tl, fitter=fitter, root_dense=root_dense, merge_dense=merge_dense,
-                       sw_consistent=bool(pr.get("consistent", False)), tensor_leaves=tl)
+                       sw_consistent=bool(pr.get("consistent", False)), tensor_leaves=tl, merge_fuse=merge_fuse)
 
 
 def is_periodic(w):
@@ -281,7 +281,8 @@ def alu_peak(prec):
     return {"fp32": FP32_PEAK_TFLOPS, "fp64": FP64_PEAK_TFLOPS, "df32": FP32_PEAK_TFLOPS / 2 / 48 * 8}[prec]
 
 
-def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False, merge_sym=False, periodic=False, tl=False):
+def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False, merge_sym=False, periodic=False, tl=False,
+             fused=0):
     """Per kernel class: algorithmic work of one step over that class's device
     time per step (CUDA events around its launches), against the ALU peak of
     its arithmetic and the measured HBM copy bandwidth; the class with the
@@ -302,8 +303,8 @@ def roofline(op, w, R, tim, prec, pk, pk_kind, fd, root_c4=False, merge_sym=Fals
     top = max(per, key=lambda c: per[c]["ms_per_step"])
     d = per[top]
     kname = {"up_leaf": "k_fd_up_leaf" if fd else "k_up_leaf", "down_leaf": "k_fd_down_leaf" if fd else "k_down_leaf",
-             "up_merge": "k_up_merge_sym" if merge_sym else "k_up_merge",
-             "down_merge": "k_down_merge_sym" if merge_sym else "k_down_merge",
+             "up_merge": ("k_up_fused + " if fused else "") + ("k_up_merge_sym" if merge_sym else "k_up_merge"),
+             "down_merge": ("k_down_fused + " if fused else "") + ("k_down_merge_sym" if merge_sym else "k_down_merge"),
              "root": "k_root_periodic" if periodic else ("k_root_sw_c4" if root_c4 else "k_root_sw")}[top]
     tname = {"fp32": "float2", "fp64": "double2", "df32": "float4"}[d["precision"]]
     if not (fd and top in ("up_leaf", "down_leaf")):
@@ -367,7 +368,7 @@ def run_ours(args):
     x, y = g.nodes()
     t0 = time.time()
     op = build_operator(eo, w, g, x, y, R, args.precision, args.poles, args.dense_leaves, args.fitter,
-                        args.root_dense, args.merge_dense, args.tensor_leaves)
+                        args.root_dense, args.merge_dense, args.tensor_leaves, args.merge_fuse)
     # the library splits the wall solve of a square walled domain of square leaves into
     # four Fourier blocks unless told not to
     root_c4 = w.kind == "sw" and w.nlx == w.nly and not args.root_dense and not per
@@ -377,6 +378,7 @@ def run_ours(args):
     merge_sym = w.kind == "sw" and not args.merge_dense and not per and not consistent
     tl = bool(args.tensor_leaves) and args.precision == "df32"
     fd = w.kind == "sw" and not args.dense_leaves and not consistent and not tl
+    fused = op.fused_levels(R)
     torch.cuda.synchronize()
     build_s = time.time() - t0
     U0 = np.stack([np.stack(W.initial_fields(w, x, y, r)) for r in range(R)])
@@ -409,7 +411,7 @@ def run_ours(args):
     fp64 = None
     if reduced and args.compare_fp64:
         op64 = build_operator(eo, w, g, x, y, R, "fp64", args.poles, args.dense_leaves, args.fitter,
-                              args.root_dense, args.merge_dense)
+                              args.root_dense, args.merge_dense, merge_fuse=args.merge_fuse)
         u64 = torch.tensor(U0, device=dev)
         for _ in range(args.warmup):
             op64.apply(u64, 1)
@@ -451,10 +453,11 @@ def run_ours(args):
                                    else "as the paper writes it") if w.kind == "sw" else None,
                    "leaves": f"{w.nlx}x{w.nly}",
                    "leaf_solves": "fast diagonalisation" if fd else (
-                       "dense leaf operators on the tensor cores (tcgen05, 5 bf16 slices of 7 bits, FP32 "
+                       "dense leaf operators on the tensor cores (tcgen05, 6 bf16 slices of 7 bits, FP32 "
                        "accumulation in TMEM, pole sum in FP32 pairs)" if tl else "dense leaf operators"),
-                   "merges": ("even/odd blocks of the reflection symmetries" if merge_sym else "dense blocks")
-                   if w.kind == "sw" else "dense blocks",
+                   "merges": ("even/odd blocks of the reflection symmetries" +
+                              (f", levels 1-{fused} in one launch per sweep" if fused else "")
+                              if merge_sym else "dense blocks") if w.kind == "sw" else "dense blocks",
                    "root": ("seam system of the root box merged with itself" if per else
                             ("four Fourier blocks of the quarter-turn-symmetric wall system" if root_c4
                              else "dense wall inverse") if w.kind == "sw" else "none (Dirichlet)"),
@@ -476,6 +479,7 @@ def run_ours(args):
         **fp64,
         "kernel_share": shares,
         "roofline": roofline(op, w, R, tim, args.precision, pk, pk_kind, fd=fd, root_c4=root_c4, merge_sym=merge_sym,
+                             fused=fused,
                              periodic=per, tl=tl),
         "clocks": clocks,
     }
@@ -731,6 +735,8 @@ def main():
                     help="line: our least-squares approximant; gauss: the paper's Gaussian-sum construction")
     ap.add_argument("--tensor-leaves", action="store_true",
                     help="leaf interior solves and pole sum on the tensor cores (bf16 slices, tcgen05)")
+    ap.add_argument("--merge-fuse", type=int, default=0, choices=[-1, 0, 1, 2, 3, 4],
+                    help="low merge levels fused into one launch per sweep (0: automatic, -1: none)")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=30.0)

@@ -135,17 +135,26 @@ typedef struct {
   int tensor_leaves;   /* 1: the leaf interior solves and the pole sum run on the tensor
                           cores (tcgen05.mma on bf16 slices, FP32 accumulation in TMEM):
                           the dense leaf operators [X | Y] of every pole are split at build
-                          time into 5 bf16 slices of 7 bits per real part, with a
-                          power-of-two scale per row and block (about 2^-34 relative per
-                          entry); per step and pole the right-hand sides g = sum_k c_k s_k
-                          (formed in FP32 pairs) and the edge values are split the same way
-                          per column and block; the two leading product levels are summed
-                          exactly in FP32, the rest rounded at about 2^-38, and the pole sum
-                          is kept in FP32 pairs.  Needs EO_PREC_DF32, dense leaves (per-box
-                          operators, or opts.dense_leaves with shared ones) and p <= 18;
-                          otherwise the build fails with EO_ERR_UNSUPPORTED.  Holds 20 bytes
-                          per entry of [X | Y] (rows padded to 256) besides the dense
-                          operators, which eo_apply_adjoint keeps using.  0: off          */
+                          time into 6 bf16 slices of 7 bits per real part (41 bits), with
+                          a power-of-two scale per row and block; per step and pole the
+                          right-hand sides g = sum_k c_k s_k (formed in FP32 pairs) and the
+                          edge values are split the same way per column and block; the
+                          product levels i + j = 2, 3, 4 are summed exactly in FP32, the
+                          deeper ones rounded (about 2^-40 of the leading level), and the
+                          pole sum is kept in FP32 pairs.  Needs EO_PREC_DF32, dense leaves
+                          (per-box operators, or opts.dense_leaves with shared ones) and
+                          p <= 18; otherwise the build fails with EO_ERR_UNSUPPORTED.
+                          Holds 24 bytes per entry of [X | Y] (rows padded to a multiple
+                          of 128, columns to a multiple of 16) besides the dense
+                          operators, which eo_apply_adjoint keeps using.  0: off     */
+  int merge_fuse;      /* reflection-symmetric merge levels (opts.merge_dense = 0) of the
+                          forward apply: 0 runs the lowest levels 1 .. min(4, L - 1) in one
+                          launch per sweep (one block per pole and box of the highest fused
+                          level, boundary data of the levels below it in shared memory,
+                          the arithmetic of the per-level kernels); k = 1 .. 4 fuses at most
+                          k levels; -1 keeps one launch per level.  Fewer levels are fused
+                          where the shared memory of a block (R right-hand sides) would
+                          exceed 200 KB, none where a level is not symmetric        */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.
@@ -154,7 +163,7 @@ typedef struct {
 eo_status eo_grid_create(int nlx, int nly, int p, double x0, double x1, double y0,
                          double y1, eo_grid_t *out);
 /* Periodic leaf grid: the square [x0,x1]x[y0,y1] with x1 identified with x0 and y1 with
- * y0, the setting of the paper's examples (Section 4: "periodic boundary conditions").
+ * y0, the setting of the examples of Section 4.
  * The seams x = x0 and y = y0 are interfaces between the last and the first leaf of each
  * row and column (flux continuity, Section 2.2); there is no domain boundary.  Public
  * numbering as above with nly horizontal and nlx vertical edge lines (line e = 0 is also
@@ -361,6 +370,11 @@ eo_status eo_get_timing(eo_handle_t h, int *n_classes, const char **names, int64
  * synchronises `stream`, reads the word, and returns EO_ERR_TIMEOUT (*flag = 1) if any
  * kernel of the handle gave up since the build, EO_OK (*flag = 0) otherwise. */
 eo_status eo_device_status(eo_handle_t h, void *stream, int *flag);
+
+/* Merge levels 1 .. *levels that eo_apply runs in one launch per sweep for n_rhs
+ * right-hand sides (opts.merge_fuse; 0: one launch per level).  Host only, no device
+ * work.  Errors: EO_ERR_INVALID_ARG (null argument, n_rhs outside [1, max_rhs]). */
+eo_status eo_fused_levels(eo_handle_t h, int n_rhs, int *levels);
 
 /* Release device memory.  Idempotent on NULL. */
 eo_status eo_destroy(eo_handle_t h);

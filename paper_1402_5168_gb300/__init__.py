@@ -105,7 +105,7 @@ class Operator:
                  c2=None, f=0.0, g=1.0, H=1.0, delta=1e-10, shared_ops=False, max_rhs=1,
                  mem_budget_gb=0.0, precision="fp64", fp64_top_levels=0, use_graphs=True, dense_leaves=False,
                  autotune=True, sw_consistent=False, fitter="line", gauss_h=0.0, root_dense=False,
-                 merge_dense=False, tensor_leaves=False, stream=None):
+                 merge_dense=False, tensor_leaves=False, merge_fuse=0, stream=None):
         L = _capi.lib()
         prec = {"fp64": 0, "fp32": 1, "df32": 2}[precision]
         fit_kind = {"line": 0, "gauss": 1}[fitter]
@@ -114,7 +114,7 @@ class Operator:
                  fp64_top_levels=fp64_top_levels, use_graphs=int(use_graphs), dense_leaves=int(dense_leaves),
                  autotune=int(autotune), sw_consistent=int(sw_consistent), fitter=fit_kind,
                  gauss_h=gauss_h, root_dense=int(root_dense), merge_dense=int(merge_dense),
-                 tensor_leaves=int(tensor_leaves))
+                 tensor_leaves=int(tensor_leaves), merge_fuse=int(merge_fuse))
         coeff = None
         if c2 is not None:
             self._c2 = np.ascontiguousarray(c2, dtype=np.float64)
@@ -212,6 +212,12 @@ class Operator:
             self.apply_functions([self._filter[1]], u, out, stream)
             u.copy_(out[0])
         return u
+
+    def fused_levels(self, n_rhs: int = 1) -> int:
+        """Merge levels 1 .. n run in one launch per sweep for n_rhs right-hand sides."""
+        n = C.c_int(-1)
+        check(_capi.lib().eo_fused_levels(self._h, n_rhs, C.byref(n)))
+        return n.value
 
     def set_timing(self, on: bool):
         check(_capi.lib().eo_set_timing(self._h, int(on)))

@@ -17,7 +17,7 @@ WAVE_DIRICHLET, SW_WALLS = 0, 1
 SYMBOLS = ("eo_fit", "eo_grid_create", "eo_grid_create_periodic", "eo_grid_periodic", "eo_grid_info", "eo_grid_nodes", "eo_grid_destroy", "eo_build_operator",
            "eo_get_poles", "eo_memory", "eo_apply", "eo_apply_adjoint", "eo_apply_host", "eo_apply_resolvent", "eo_apply_resolvent_noalloc", "eo_set_timing", "eo_get_timing", "eo_destroy",
            "eo_last_error", "eo_leaf_basis", "eo_batch_create", "eo_batch_apply", "eo_batch_destroy",
-           "eo_fit_function", "eo_apply_functions", "eo_fit_gauss", "eo_device_status")
+           "eo_fit_function", "eo_apply_functions", "eo_fit_gauss", "eo_device_status", "eo_fused_levels")
 
 
 class Opts(C.Structure):
@@ -27,7 +27,7 @@ class Opts(C.Structure):
                 ("fp64_top_levels", C.c_int), ("use_graphs", C.c_int), ("dense_leaves", C.c_int),
                 ("autotune", C.c_int), ("sw_consistent", C.c_int), ("fitter", C.c_int),
                 ("gauss_h", C.c_double), ("root_dense", C.c_int),
-                ("merge_dense", C.c_int), ("tensor_leaves", C.c_int)]
+                ("merge_dense", C.c_int), ("tensor_leaves", C.c_int), ("merge_fuse", C.c_int)]
 
 
 _lib = None
@@ -71,6 +71,7 @@ def lib() -> C.CDLL:
         "eo_apply_functions": [vp, C.c_int, dp, vp, vp, vp],
         "eo_fit_gauss": [C.c_double, C.c_double, C.c_double, C.c_int, dp, dp, C.POINTER(C.c_int),
                          C.POINTER(C.c_int)],
+        "eo_fused_levels": [vp, C.c_int, C.POINTER(C.c_int)],
         "eo_device_status": [vp, vp, C.POINTER(C.c_int)],
     }
     for name, args in sig.items():

@@ -233,6 +233,7 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   if (!(o.band > 0)) return fail(EO_ERR_INVALID_ARG, "opts.band must be positive");
   eo_status rc;
   if (o.fitter != EO_FIT_LINE && o.fitter != EO_FIT_GAUSS) return fail(EO_ERR_INVALID_ARG, "unknown opts.fitter");
+  if (o.merge_fuse < -1 || o.merge_fuse > 4) return fail(EO_ERR_INVALID_ARG, "opts.merge_fuse must be in -1 .. 4");
   if (o.fitter == EO_FIT_GAUSS) {
     if (o.n_poles > 0) return fail(EO_ERR_INVALID_ARG, "the Gaussian-sum fitter takes tau, not n_poles");
     if (!(o.tau > 0)) return fail(EO_ERR_INVALID_ARG, "opts.tau must be positive");
@@ -690,6 +691,14 @@ eo_status eo_device_status(eo_handle_t hd, void* stream, int* flag) {
   eo_status rc = tc_status(hd->h, (cudaStream_t)stream, flag);
   if (rc) return rc;
   if (*flag) return fail(EO_ERR_TIMEOUT, "a bounded device wait gave up");
+  set_error("");
+  return EO_OK;
+}
+
+eo_status eo_fused_levels(eo_handle_t hd, int n_rhs, int* levels) {
+  if (!hd || !levels) return fail(EO_ERR_INVALID_ARG, "null argument");
+  if (n_rhs < 1 || n_rhs > hd->h.R) return fail(EO_ERR_INVALID_ARG, "n_rhs out of range [1, max_rhs]");
+  *levels = fused_levels(hd->h, n_rhs);
   set_error("");
   return EO_OK;
 }

@@ -20,6 +20,7 @@
 #include <string>
 #include <vector>
 
+#include "fused.cuh"
 #include "sweep.cuh"
 
 namespace eo {
@@ -917,6 +918,94 @@ MergeArgs merge_args(const Handle& h, int l) {
   return m;
 }
 
+// ---------------------------------------------------------------- fused low levels
+// Shared memory of the fused kernels for R right-hand sides (k_up_fused, k_down_fused).
+struct FusedSmem {
+  size_t up = 0, down = 0;
+};
+
+static FusedSmem fused_smem(const FusedLevels& f, int R, int prec) {
+  const size_t ta = prec == 1 ? sizeof(float2) : prec == 2 ? sizeof(float4) : sizeof(double2);
+  int n3max = 0, rhmax = 0, kmax = 0;
+  for (int l = 1; l <= f.Lf; ++l) {
+    n3max = std::max(n3max, f.m[l].n3);
+    rhmax = std::max(rhmax, f.m[l].rh);
+    kmax = std::max(kmax, 2 * f.m[l].nbq);
+  }
+  FusedSmem z;
+  z.up = sizeof(cd) * (2 * (size_t)f.hs + 2 * 8 * rhmax + 256 * 8) + ta * 8 * n3max + 64;
+  z.down = sizeof(cd) * ((size_t)8 * n3max + 256 * 8) + ta * 8 * kmax + 64;
+  (void)R;
+  return z;
+}
+
+// Levels 1 .. Lf of both sweeps fused (Lf = 0: none): every level reflection-symmetric
+// with even/odd blocks for both sweeps, one block precision, at least one level above,
+// and the blocks' shared memory within 200 KB.
+FusedLevels fused_plan(const Handle& h, int R) {
+  FusedLevels f;
+  const int L = h.plan.L();
+  int want = h.opts.merge_fuse == 0 ? FUSED_MAX : h.opts.merge_fuse;
+  want = std::min(std::min(want, FUSED_MAX), L - 1);
+  if (want < 1 || !h.shared || h.g.periodic) return f;
+  int Lf = 0;
+  for (int l = 1; l <= want; ++l) {
+    const LevelDev& ld = h.lv[l];
+    if (!ld.sym || !ld.aZUs || !ld.aSs || ld.fp32 != h.lv[1].fp32) break;
+    Lf = l;
+  }
+  for (; Lf >= 1; --Lf) {
+    f = FusedLevels{};
+    f.Lf = Lf;
+    for (int l = 0; l <= Lf; ++l) {
+      f.nbx[l] = h.lv[l].nbx;
+      f.nby[l] = h.lv[l].nbox / h.lv[l].nbx;
+      if (l >= 1) f.m[l] = merge_args(h, l);
+    }
+    const int nsub = h.lv[Lf].nbox;
+    f.hs = 0;
+    for (int l = 1; l < Lf; ++l)
+      f.hs = std::max(f.hs, h.lv[l].nbox / nsub * R * h.lv[l].nbd);
+    const FusedSmem z = fused_smem(f, R, h.lv[1].fp32);
+    if (std::max(z.up, z.down) <= 200 * 1024) return f;
+  }
+  return FusedLevels{};
+}
+
+template <typename TA>
+static eo_status run_up_fused(const Sweep& s, const FusedLevels& f, const cd* h0, cd* hout, size_t smem,
+                              cudaStream_t st) {
+  EO_SET_SMEM((k_up_fused<TA>), smem);
+  k_up_fused<TA><<<dim3(f.nbx[f.Lf] * f.nby[f.Lf], s.P), 256, smem, st>>>(s, f, h0, hout);
+  EO_CUDA_TRY(cudaGetLastError());
+  return EO_OK;
+}
+
+template <typename TA>
+static eo_status run_down_fused(const Sweep& s, const FusedLevels& f, cd* E, size_t smem, cudaStream_t st) {
+  EO_SET_SMEM((k_down_fused<TA>), smem);
+  k_down_fused<TA><<<dim3(f.nbx[f.Lf] * f.nby[f.Lf], s.P), 256, smem, st>>>(s, f, E);
+  EO_CUDA_TRY(cudaGetLastError());
+  return EO_OK;
+}
+
+static eo_status up_fused(const Handle& h, const Sweep& s, const FusedLevels& f, const cd* h0, cd* hout,
+                          cudaStream_t st) {
+  const int prec = h.lv[1].fp32;
+  const size_t smem = fused_smem(f, s.R, prec).up;
+  if (prec == 1) return run_up_fused<float2>(s, f, h0, hout, smem, st);
+  if (prec == 2) return run_up_fused<float4>(s, f, h0, hout, smem, st);
+  return run_up_fused<double2>(s, f, h0, hout, smem, st);
+}
+
+static eo_status down_fused(const Handle& h, const Sweep& s, const FusedLevels& f, cd* E, cudaStream_t st) {
+  const int prec = h.lv[1].fp32;
+  const size_t smem = fused_smem(f, s.R, prec).down;
+  if (prec == 1) return run_down_fused<float2>(s, f, E, smem, st);
+  if (prec == 2) return run_down_fused<float4>(s, f, E, smem, st);
+  return run_down_fused<double2>(s, f, E, smem, st);
+}
+
 Sweep base_sweep(const Handle& h, int R, int p0, int np, const cd* wgt) {
   const Grid& g = h.g;
   Sweep s{};
@@ -973,8 +1062,15 @@ eo_status sweep_to_edges(Handle& h, const double* uin, int R, int p0, int np, co
     return rc;
   }
   if ((rc = h.trace_end(TR_UP_LEAF, st))) return rc;
-  // up: merges
-  for (int l = 1; l <= L; ++l) {
+  // up: merges (the lowest fused into one launch where fused_plan allows)
+  const FusedLevels fl = fused_plan(h, R);
+  if (fl.Lf) {
+    if ((rc = h.trace_begin(st))) return rc;
+    if ((rc = up_fused(h, s, fl, hcur, hnext, st))) return rc;
+    if ((rc = h.trace_end(TR_UP_MERGE, st))) return rc;
+    std::swap(hcur, hnext);
+  }
+  for (int l = fl.Lf + 1; l <= L; ++l) {
     MergeArgs m = merge_args(h, l);
     if ((rc = h.trace_begin(st))) return rc;
     const Tuned tu = h.lv[l].up;
@@ -1008,12 +1104,17 @@ eo_status sweep_to_edges(Handle& h, const double* uin, int R, int p0, int np, co
     if ((rc = h.trace_end(TR_ROOT, st))) return rc;
   }
   // down: merges
-  for (int l = L; l >= 1; --l) {
+  for (int l = L; l > fl.Lf; --l) {
     MergeArgs m = merge_args(h, l);
     if ((rc = h.trace_begin(st))) return rc;
     const Tuned tu = h.lv[l].down;
     const int nc = tu.nc ? tu.nc : pick_nc(h.shared, R, m.nbd, m.n3, m.nbox);
     if ((rc = dispatch<DownMerge>(h.lv[l].fp32, nc, s, m, h.E, tu.nt, st))) return rc;
+    if ((rc = h.trace_end(TR_DOWN_MERGE, st))) return rc;
+  }
+  if (fl.Lf) {
+    if ((rc = h.trace_begin(st))) return rc;
+    if ((rc = down_fused(h, s, fl, h.E, st))) return rc;
     if ((rc = h.trace_end(TR_DOWN_MERGE, st))) return rc;
   }
   return EO_OK;
@@ -1477,5 +1578,7 @@ eo_status apply_resolvent_noalloc(Handle& h, int j, const double* u, double* x, 
                                 cudaMemcpyDeviceToDevice, st));
   return EO_OK;
 }
+
+int fused_levels(const Handle& h, int R) { return fused_plan(h, R).Lf; }
 
 }  // namespace eo

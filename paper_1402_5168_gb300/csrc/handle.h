@@ -221,5 +221,7 @@ bool tc_eligible(const Handle& h, std::string* why);
 eo_status tc_build(Handle& h, cudaStream_t st);
 eo_status tc_down_leaf(Handle& h, const Sweep& s, int& nchunk, cudaStream_t st);
 eo_status tc_status(Handle& h, cudaStream_t st, int* out);
+// merge levels 1 .. n fused into one launch per sweep for R right-hand sides (apply.cu)
+int fused_levels(const Handle& h, int R);
 
 }  // namespace eo
