@@ -496,25 +496,49 @@ def run_ours(args):
 def run_uneven_batch(args):
     """The uneven batch: independent instances (wave and shallow water, different
     leaf grids, p, pole and rhs counts) advanced together through one CUDA graph
-    (eo_batch_*), against the same instances stepped one after another."""
+    (eo_batch_*), against the same instances stepped one after another.  The
+    64-instance draw admits instances in order under an operator budget: each is
+    built with the budget still left, and one the library rejects with
+    EO_ERR_BUDGET (or whose workspace no longer fits the device) is left out."""
     import torch
     import paper_1402_5168_gb300 as eo
-    ws = W.uneven_instances()
-    ops, states, U0 = [], [], []
+    from paper_1402_5168_gb300 import ExpopError
+    big = args.workload == W.UNEVEN_BATCH_64
+    ws_all = W.uneven_instances_64() if big else W.uneven_instances()
+    budget = W.UNEVEN_64_BUDGET_GB if big else 0.0
+    ops, states, U0, ws, rejected = [], [], [], [], []
+    used_gb = 0.0
     t0 = time.time()
-    for w in ws:
+    for w in ws_all:
         g = eo.Grid(w.nlx, w.nly, w.p)
         x, y = g.nodes()
-        if w.kind == "wave":
-            c = W.wave_c(w, x, y)
-            op = eo.Operator(g, eo.WAVE_DIRICHLET, band=W.wave_band(w), n_poles=w.n_poles, c2=c * c,
-                             max_rhs=w.n_rhs, precision=args.precision)
-        else:
-            pr = w.params
-            op = eo.Operator(g, eo.SW_WALLS, band=W.sw_band(w), n_poles=w.n_poles, f=pr["f"], g=pr["g"],
-                             H=pr["H"], shared_ops=True, max_rhs=w.n_rhs, precision=args.precision)
+        left = budget - used_gb if budget else 0.0
+        if budget and left <= 0.0:
+            rejected.append({"instance": w.name, "reason": "budget spent"})
+            continue
+        try:
+            if w.kind == "wave":
+                c = W.wave_c(w, x, y)
+                op = eo.Operator(g, eo.WAVE_DIRICHLET, band=W.wave_band(w), n_poles=w.n_poles, c2=c * c,
+                                 max_rhs=w.n_rhs, precision=args.precision, mem_budget_gb=left)
+            else:
+                pr = w.params
+                op = eo.Operator(g, eo.SW_WALLS, band=W.sw_band(w), n_poles=w.n_poles, f=pr["f"], g=pr["g"],
+                                 H=pr["H"], shared_ops=True, max_rhs=w.n_rhs, precision=args.precision,
+                                 mem_budget_gb=left)
+        except ExpopError as e:
+            rejected.append({"instance": w.name, "reason": str(e)[:160]})
+            continue
         u0 = np.stack([np.stack(W.initial_fields(w, x, y, r)) for r in range(w.n_rhs)])
+        free = torch.cuda.mem_get_info()[0]
+        if big and free < u0.nbytes + (16 << 30):
+            # keep room for the graph and the states of the instances already in
+            rejected.append({"instance": w.name, "reason": "device memory"})
+            op.close()
+            continue
+        used_gb += op.memory()[0] / 1e9
         ops.append(op)
+        ws.append(w)
         U0.append(u0)
         states.append(torch.tensor(u0, device="cuda"))
     torch.cuda.synchronize()
@@ -551,7 +575,9 @@ def run_uneven_batch(args):
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
         "scaling": "weak", "vs_baseline": None,
         "dtype": {"fp32": "f32", "fp64": "f64", "df32": "f32x2"}[args.precision], "data": "synthetic",
-        "config": {"workload": W.UNEVEN_BATCH, "instances": [w.name for w in ws], "rhs_total": rhs_total,
+        "config": {"workload": args.workload, "instances": [w.name for w in ws], "rhs_total": rhs_total,
+                   "drawn": len(ws_all), "admitted": len(ws), "rejected": rejected,
+                   "budget_gb": budget or None,
                    "operator_gb": ob / 1e9, "build_s": build_s,
                    "sequential": {"ms_per_step": ms_seq / args.steps,
                                   "value": rhs_total * args.steps / (ms_seq / 1e3)},
@@ -719,7 +745,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=30)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--workload", default=DEFAULT, choices=sorted(W.WORKLOADS) + [W.UNEVEN_BATCH])
+    ap.add_argument("--workload", default=DEFAULT,
+                    choices=sorted(W.WORKLOADS) + [W.UNEVEN_BATCH, W.UNEVEN_BATCH_64])
     ap.add_argument("--rhs", type=int, default=1)
     ap.add_argument("--poles", type=int, default=0, help="override the pole count (profiling cases)")
     ap.add_argument("--leaves", type=int, default=0, help="override leaves per side (profiling cases)")
@@ -735,15 +762,15 @@ def main():
                     help="line: our least-squares approximant; gauss: the paper's Gaussian-sum construction")
     ap.add_argument("--tensor-leaves", action="store_true",
                     help="leaf interior solves and pole sum on the tensor cores (bf16 slices, tcgen05)")
-    ap.add_argument("--merge-fuse", type=int, default=0, choices=[-1, 0, 1, 2, 3, 4],
-                    help="low merge levels fused into one launch per sweep (0: automatic, -1: none)")
+    ap.add_argument("--merge-fuse", type=int, default=0, choices=[0, 1, 2, 3, 4],
+                    help="low merge levels fused into one launch per sweep (0: one launch per level)")
     ap.add_argument("--no-fp64-compare", dest="compare_fp64", action="store_false")
     ap.add_argument("--no-cpu-baseline", dest="cpu_baseline", action="store_false")
     ap.add_argument("--cpu-budget", type=float, default=30.0)
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)
-    elif args.workload == W.UNEVEN_BATCH:
+    elif args.workload in (W.UNEVEN_BATCH, W.UNEVEN_BATCH_64):
         run_uneven_batch(args)
     else:
         run_ours(args)

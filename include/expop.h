@@ -148,13 +148,15 @@ typedef struct {
                           of 128, columns to a multiple of 16) besides the dense
                           operators, which eo_apply_adjoint keeps using.  0: off     */
   int merge_fuse;      /* reflection-symmetric merge levels (opts.merge_dense = 0) of the
-                          forward apply: 0 runs the lowest levels 1 .. min(4, L - 1) in one
-                          launch per sweep (one block per pole and box of the highest fused
-                          level, boundary data of the levels below it in shared memory,
-                          the arithmetic of the per-level kernels); k = 1 .. 4 fuses at most
-                          k levels; -1 keeps one launch per level.  Fewer levels are fused
-                          where the shared memory of a block (R right-hand sides) would
-                          exceed 200 KB, none where a level is not symmetric        */
+                          forward apply: 0 (default) runs one launch per level; k = 1 .. 4
+                          runs levels 1 .. min(k, L - 1) in one launch per sweep (one block
+                          per pole and box of the highest fused level, boundary data of the
+                          levels below it in shared memory, the arithmetic of the per-level
+                          kernels).  Fewer levels are fused where the shared memory of a
+                          block (R right-hand sides) would exceed 200 KB, none where a level
+                          is not symmetric.  On GB300 the per-level launches are faster for
+                          the shallow-water workload (their FP32-pair products are
+                          issue-bound and need the occupancy of many small blocks)      */
 } eo_opts;
 
 /* Leaf grid.  nlx, nly powers of two (>= 1), 4 <= p <= 24, x0 < x1, y0 < y1.
@@ -372,7 +374,7 @@ eo_status eo_get_timing(eo_handle_t h, int *n_classes, const char **names, int64
 eo_status eo_device_status(eo_handle_t h, void *stream, int *flag);
 
 /* Merge levels 1 .. *levels that eo_apply runs in one launch per sweep for n_rhs
- * right-hand sides (opts.merge_fuse; 0: one launch per level).  Host only, no device
+ * right-hand sides (opts.merge_fuse; *levels = 0: one launch per level).  Host only, no device
  * work.  Errors: EO_ERR_INVALID_ARG (null argument, n_rhs outside [1, max_rhs]). */
 eo_status eo_fused_levels(eo_handle_t h, int n_rhs, int *levels);
 

@@ -233,7 +233,7 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   if (!(o.band > 0)) return fail(EO_ERR_INVALID_ARG, "opts.band must be positive");
   eo_status rc;
   if (o.fitter != EO_FIT_LINE && o.fitter != EO_FIT_GAUSS) return fail(EO_ERR_INVALID_ARG, "unknown opts.fitter");
-  if (o.merge_fuse < -1 || o.merge_fuse > 4) return fail(EO_ERR_INVALID_ARG, "opts.merge_fuse must be in -1 .. 4");
+  if (o.merge_fuse < 0 || o.merge_fuse > 4) return fail(EO_ERR_INVALID_ARG, "opts.merge_fuse must be in 0 .. 4");
   if (o.fitter == EO_FIT_GAUSS) {
     if (o.n_poles > 0) return fail(EO_ERR_INVALID_ARG, "the Gaussian-sum fitter takes tau, not n_poles");
     if (!(o.tau > 0)) return fail(EO_ERR_INVALID_ARG, "opts.tau must be positive");

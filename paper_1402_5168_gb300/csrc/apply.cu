@@ -945,8 +945,7 @@ static FusedSmem fused_smem(const FusedLevels& f, int R, int prec) {
 FusedLevels fused_plan(const Handle& h, int R) {
   FusedLevels f;
   const int L = h.plan.L();
-  int want = h.opts.merge_fuse == 0 ? FUSED_MAX : h.opts.merge_fuse;
-  want = std::min(std::min(want, FUSED_MAX), L - 1);
+  const int want = std::min(std::min(h.opts.merge_fuse, FUSED_MAX), L - 1);
   if (want < 1 || !h.shared || h.g.periodic) return f;
   int Lf = 0;
   for (int l = 1; l <= want; ++l) {

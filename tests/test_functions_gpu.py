@@ -17,20 +17,33 @@ def rel(a, b):
     return float(np.linalg.norm(a - b) / np.linalg.norm(b))
 
 
-def phi1(th):
-    z = 1j * th
-    out = np.ones_like(z)
-    nz = np.abs(th) > 1e-6
-    out[nz] = (np.exp(z[nz]) - 1) / z[nz]
+def _phi(j, th):
+    """phi_j(i theta), j = 1, 2: the closed form where it has no cancellation
+    (|theta| >= 0.5, rounding below 1e-15) and the Taylor series sum_k z^k / (k + j)!
+    (30 terms) inside, so that the reference is accurate well below the band errors."""
+    z = 1j * np.asarray(th, dtype=np.float64)
+    out = np.zeros(z.shape, dtype=np.complex128)
+    small = np.abs(th) < 0.5
+    zs = z[small]
+    term = np.ones_like(zs)
+    fact = float(np.prod(np.arange(1, j + 1)))
+    acc = np.zeros_like(zs)
+    for k in range(30):
+        acc += term / fact
+        term = term * zs
+        fact *= k + j + 1
+    out[small] = acc
+    zb = z[~small]
+    out[~small] = (np.exp(zb) - 1) / zb if j == 1 else (np.exp(zb) - 1 - zb) / zb ** 2
     return out
+
+
+def phi1(th):
+    return _phi(1, th)
 
 
 def phi2(th):
-    z = 1j * th
-    out = 0.5 + z / 6 + z * z / 24 + z ** 3 / 120 + z ** 4 / 720
-    nz = np.abs(th) > 1e-2
-    out[nz] = (np.exp(z[nz]) - 1 - z[nz]) / z[nz] ** 2
-    return out
+    return _phi(2, th)
 
 
 @pytest.fixture(scope="module")

@@ -1,5 +1,5 @@
 """Fused low merge levels (opts.merge_fuse): levels 1 .. Lf of both sweeps in one launch
-each, against one launch per level (merge_fuse = -1) of the same build and against
+each, against one launch per level (merge_fuse = 0, the default) of the same build and against
 the oracle.  Shared per-level operators exist for shallow water (constant
 coefficients), so that is the problem kind fused.
 
@@ -59,7 +59,7 @@ def test_fused_levels_match_one_launch_per_level(nlx, nly, p, precision, R):
     kw = dict(band=60.0, n_poles=21, f=10.0, g=1.0, H=1.0, shared_ops=True, precision=precision, max_rhs=R)
     L = levels(nlx, nly)
     u0 = state(g, R=R)
-    base = eo.Operator(g, eo.SW_WALLS, merge_fuse=-1, **kw)
+    base = eo.Operator(g, eo.SW_WALLS, **kw)
     b = torch.tensor(u0, device="cuda")
     nu, nd = up_merge_launches(base, b)
     assert nu == L and nd == L and base.fused_levels(R) == 0
@@ -67,7 +67,7 @@ def test_fused_levels_match_one_launch_per_level(nlx, nly, p, precision, R):
     base.apply(b, 3)
     want = b.cpu().numpy()
     tol = 1e-12 if precision == "fp64" else 1e-10
-    for k in (0, 1, 2, 3, 4):
+    for k in (1, 2, 3, 4):
         op = eo.Operator(g, eo.SW_WALLS, merge_fuse=k, **kw)
         a = torch.tensor(u0, device="cuda")
         nu, nd = up_merge_launches(op, a)
@@ -78,8 +78,8 @@ def test_fused_levels_match_one_launch_per_level(nlx, nly, p, precision, R):
               f"vs one launch per level after 3 steps {e:.1e}")
         lf = op.fused_levels(R)
         assert nu == nd == L - lf + (1 if lf else 0), (nu, nd, lf)
-        if p % 2 == 0:   # even q: every level symmetric, fused depth min(k or 4, L - 1)
-            assert lf == min(4 if k == 0 else k, L - 1), (lf, k)
+        if p % 2 == 0:   # even q: every level symmetric, fused depth min(k, L - 1)
+            assert lf == min(k, L - 1), (lf, k)
         else:            # q odd: level 1 (n3 = q) has no even/odd split, nothing fused
             assert lf == 0
         assert e <= tol, (k, e)
@@ -90,7 +90,7 @@ def test_fused_levels_match_the_oracle_multi_rhs():
     g = eo.Grid(8, 4, 8)
     R = 3
     op = eo.Operator(g, eo.SW_WALLS, band=60.0, n_poles=21, f=10.0, g=1.0, H=1.0, shared_ops=True, max_rhs=R,
-                     precision="df32")
+                     precision="df32", merge_fuse=4)
     U0 = state(g, 1003, R=R)
     u = torch.tensor(U0, device="cuda")
     nu, _ = up_merge_launches(op, u)
@@ -109,6 +109,6 @@ def test_merge_fuse_out_of_range_rejected():
     import paper_1402_5168_gb300 as eo
     from paper_1402_5168_gb300 import ExpopError
     g = eo.Grid(2, 2, 8)
-    for k in (-2, 5):
+    for k in (-1, 5):
         with pytest.raises(ExpopError, match="merge_fuse"):
             eo.Operator(g, eo.SW_WALLS, band=60.0, n_poles=21, f=10.0, shared_ops=True, merge_fuse=k)

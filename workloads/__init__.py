@@ -87,6 +87,15 @@ SW_PERIODIC_16X16_P16 = dataclasses.replace(
     params=dict(SW_16X16_P16.params, periodic=True, consistent=True),
 )
 
+# Configuration 4: the adjoint of configuration 1's problem on 32x32 leaves, p = 16,
+# 61 poles (the step tau = X(61) / band follows from the pole count): a misfit of h at
+# 512 seeded sensor nodes after each of 50 steps, data from a second seeded draw,
+# checkpoints every 10 steps, 20 seeded central-difference directions.
+SW_ADJOINT_32X32_P16 = dataclasses.replace(
+    SW_16X16_P16, name="sw_walls_adjoint_32x32_p16_N61", nlx=32, nly=32, n_poles=61, tau=0.0, steps=50,
+    seed=4000, params=dict(SW_16X16_P16.params, n_sensors=512, checkpoint_every=10, fd_directions=20),
+)
+
 WORKLOADS = {w.name: w for w in (WAVE_4X4_P12, SW_16X16_P16, WAVE_32X32_P16, SW_PERIODIC_16X16_P16)}
 
 # Uneven batch (after configuration 3, scaled to fit the batch's operators in a
@@ -115,6 +124,31 @@ def uneven_instances(n: int = 16, seed: int = 3000) -> list:
                                            p=p, n_poles=npol, tau=0.0, n_rhs=rhs, seed=seed + i))
     return out
 
+# Configuration 3 at its stated size: 64 seeded instances, alternately wave (variable c,
+# per-box operators) and shallow water (walls, shared operators), leaves 8^2 .. 64^2,
+# p in {8, 12, 16}, 2M+1 in [41, 201], 1-64 right-hand sides, admitted in draw order
+# while their operators fit a 150 GB budget (an instance over the rest is rejected
+# by the library with EO_ERR_BUDGET).
+UNEVEN_BATCH_64 = "uneven_batch_64"
+UNEVEN_64_BUDGET_GB = 150.0
+
+
+def uneven_instances_64(n: int = 64, seed: int = 3000) -> list:
+    """Seeded instance list of configuration 3 (see UNEVEN_BATCH_64)."""
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        nl = int(rng.choice([8, 16, 32, 64]))
+        p = int(rng.choice([8, 12, 16]))
+        npol = int(rng.integers(20, 101)) * 2 + 1
+        rhs = int(rng.integers(1, 65))
+        base = WAVE_32X32_P16 if i % 2 == 0 else SW_16X16_P16
+        kind = "wave" if i % 2 == 0 else "sw"
+        out.append(dataclasses.replace(base, name=f"{kind}_{nl}x{nl}_p{p}_N{npol}_r{rhs}", nlx=nl, nly=nl, p=p,
+                                       n_poles=npol, tau=0.0, n_rhs=rhs, seed=seed + i))
+    return out
+
+
 # Band Lambda (largest resolved |eigenvalue|) per workload.  4x4/p12 wave: the
 # content of the Gaussian bump above |lambda| = 320 of the discrete operator is
 # below 1e-10 (dense eigendecomposition of that 4000-unknown operator); the
@@ -128,6 +162,7 @@ def _init_bands():
     BAND[SW_16X16_P16.name] = sw_band(SW_16X16_P16)
     BAND[WAVE_32X32_P16.name] = wave_band(WAVE_32X32_P16)
     BAND[SW_PERIODIC_16X16_P16.name] = sw_band(SW_PERIODIC_16X16_P16)
+    BAND[SW_ADJOINT_32X32_P16.name] = sw_band(SW_ADJOINT_32X32_P16)
 
 
 def sw_band(w: Workload) -> float:
