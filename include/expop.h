@@ -339,6 +339,26 @@ eo_status eo_fit_function(eo_handle_t h, int kind, double c, double *b, double *
 eo_status eo_apply_functions(eo_handle_t h, int n_out, const double *b_sets, const double *u_dev,
                              double *out_dev, void *stream);
 
+/* The filter S(k0 Delta) of Section 3.3 (the variant applied after the conjugate-pole
+ * step to damp only the highest wavenumbers), in place on n_rhs x n_fields real fields
+ * u_dev (DEVICE [n_rhs][n_fields][n_nodes], fields of any state on the handle's grid).
+ * Reading: for a rational Q(z) = sum_m s_m / (z - alpha_m) approximating an even window
+ * chi on the imaginary axis, S(k0 Delta) := Q(i (-k0 Delta)^{1/2}), i.e. a mode of
+ * wavenumber |k| is multiplied by about chi(sqrt(k0) |k| / 2 pi); since chi is even this
+ * is sum_m s_m alpha_m (k0 Delta - alpha_m^2)^{-1}, one shifted-Laplacian solve per pole
+ * (real part over the upper poles, weight 2 per pair).  h must be an EO_SW_WALLS handle
+ * built with sw_f = 0: its solve (tau^2 g H Delta - alpha^2) w = alpha r is that one with
+ * k0 = tau^2 g H, with the natural condition d_n w = 0 on walls (constants pass) and none
+ * on a periodic grid.  s_set: n complex residues interleaved (eo_get_poles order), e.g.
+ * eo_fit_function(h, EO_FN_FILTER, c, ...) on an EO_FIT_GAUSS handle, whose window keeps
+ * sqrt(k0) |k| / 2 pi below about floor(c M) h.  The fields go through in groups of
+ * max_rhs; the first call allocates two staging states of max_rhs x 3 x n_nodes doubles
+ * in the handle.  Synchronises the stream.  Errors: EO_ERR_INVALID_ARG (null pointer,
+ * n_fields or n_rhs < 1, non-finite residue), EO_ERR_UNSUPPORTED (not a shallow-water
+ * handle with f = 0), EO_ERR_CUDA. */
+eo_status eo_apply_laplacian_filter(eo_handle_t h, const double *s_set, double *u_dev, int n_fields,
+                                    int n_rhs, void *stream);
+
 /* Batches of independent instances (the paper has no counterpart).  n built handles -- any
  * grids, kinds, pole counts and precisions, each with its own DEVICE state u_dev[i]
  * ([n_rhs[i]][fields][n_nodes], caller-owned, 1 <= n_rhs[i] <= max_rhs) -- are advanced

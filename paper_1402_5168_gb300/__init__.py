@@ -213,6 +213,20 @@ class Operator:
             u.copy_(out[0])
         return u
 
+    def apply_laplacian_filter(self, s, u, stream=None):
+        """u <- S(k0 Delta) u field by field, in place (eo_apply_laplacian_filter): s the
+        filter's residues on this operator's poles; this operator a shallow-water one
+        with f = 0 (k0 = tau^2 g H); u: CUDA float64 [n_rhs, fields, n_nodes] or
+        [fields, n_nodes] of any state on this grid."""
+        if not (u.is_cuda and u.element_size() == 8 and u.is_contiguous()) or u.shape[-1] != self.grid.n_nodes:
+            raise ValueError("u must be a contiguous CUDA float64 tensor [..., fields, n_nodes]")
+        n_fields = u.shape[-2]
+        n_rhs = 1 if u.dim() == 2 else u.shape[0]
+        ss = np.ascontiguousarray(np.stack([np.real(s), np.imag(s)], axis=1).ravel())
+        check(_capi.lib().eo_apply_laplacian_filter(self._h, ss.ctypes.data_as(C.POINTER(C.c_double)),
+                                                    C.c_void_p(u.data_ptr()), n_fields, n_rhs, _stream_ptr(stream)))
+        return u
+
     def fused_levels(self, n_rhs: int = 1) -> int:
         """Merge levels 1 .. n run in one launch per sweep for n_rhs right-hand sides."""
         n = C.c_int(-1)
@@ -238,6 +252,37 @@ class Operator:
 
     def __del__(self):
         self.close()
+
+
+class LaplacianFilter:
+    """S(k0 Delta) of Section 3.3 on a grid: the rational partition of unity of the
+    Gaussian-sum construction (M Gaussians of width h fitted on |theta| <= X; the window
+    keeps M0 = floor(keep M) of them) applied to the Laplacian.  It runs through a
+    shallow-water operator with f = 0, g = H = 1 and tau = sqrt(k0), whose per-pole
+    solve is (k0 Delta - alpha^2) w = alpha r: a mode of wavenumber |k| is multiplied by
+    about chi(sqrt(k0) |k| / 2 pi), flat (to 1e-10) for sqrt(k0) |k| / 2 pi below about
+    (M0 - 10) h and zero beyond (M0 + 10) h."""
+
+    def __init__(self, grid: Grid, k0: float, X: float = 30.0, keep: float = 0.9, h: float = 0.18,
+                 precision: str = "fp64", max_rhs: int = 1):
+        if not k0 > 0:
+            raise ValueError("k0 must be positive")
+        tau = float(np.sqrt(k0))
+        self.k0, self.h = float(k0), float(h)
+        self.op = Operator(grid, SW_WALLS, band=X / tau, tau=tau, f=0.0, g=1.0, H=1.0, shared_ops=True,
+                           fitter="gauss", gauss_h=h, precision=precision, max_rhs=max_rhs)
+        self.s, self.err = self.op.fit_function("filter", keep)
+        self.M = (self.op.alpha.size // 2 - 1) // 2 - 11
+        self.M0 = int(np.floor(keep * self.M))
+
+    @staticmethod
+    def k0_keeping(k_over_2pi: float, M0: int, h: float = 0.18) -> float:
+        """k0 that keeps the window flat up to |k| / 2 pi = k_over_2pi (edge margin 10 h)."""
+        return float(((M0 - 10) * h / k_over_2pi) ** 2)
+
+    def apply(self, u, stream=None):
+        """u <- S(k0 Delta) u, every field of every right-hand side, in place."""
+        return self.op.apply_laplacian_filter(self.s, u, stream)
 
 
 class Batch:

@@ -17,7 +17,8 @@ WAVE_DIRICHLET, SW_WALLS = 0, 1
 SYMBOLS = ("eo_fit", "eo_grid_create", "eo_grid_create_periodic", "eo_grid_periodic", "eo_grid_info", "eo_grid_nodes", "eo_grid_destroy", "eo_build_operator",
            "eo_get_poles", "eo_memory", "eo_apply", "eo_apply_adjoint", "eo_apply_host", "eo_apply_resolvent", "eo_apply_resolvent_noalloc", "eo_set_timing", "eo_get_timing", "eo_destroy",
            "eo_last_error", "eo_leaf_basis", "eo_batch_create", "eo_batch_apply", "eo_batch_destroy",
-           "eo_fit_function", "eo_apply_functions", "eo_fit_gauss", "eo_device_status", "eo_fused_levels")
+           "eo_fit_function", "eo_apply_functions", "eo_fit_gauss", "eo_device_status", "eo_fused_levels",
+           "eo_apply_laplacian_filter")
 
 
 class Opts(C.Structure):
@@ -72,6 +73,7 @@ def lib() -> C.CDLL:
         "eo_fit_gauss": [C.c_double, C.c_double, C.c_double, C.c_int, dp, dp, C.POINTER(C.c_int),
                          C.POINTER(C.c_int)],
         "eo_fused_levels": [vp, C.c_int, C.POINTER(C.c_int)],
+        "eo_apply_laplacian_filter": [vp, dp, vp, C.c_int, C.c_int, vp],
         "eo_device_status": [vp, vp, C.POINTER(C.c_int)],
     }
     for name, args in sig.items():

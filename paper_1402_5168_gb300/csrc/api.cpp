@@ -592,6 +592,37 @@ eo_status eo_apply_functions(eo_handle_t hd, int n_out, const double* b_sets, co
   return rc;
 }
 
+eo_status eo_apply_laplacian_filter(eo_handle_t hd, const double* s_set, double* u_dev, int n_fields, int n_rhs,
+                                    void* stream) {
+  if (!hd || !s_set || !u_dev) return fail(EO_ERR_INVALID_ARG, "null argument");
+  if (n_fields < 1 || n_rhs < 1) return fail(EO_ERR_INVALID_ARG, "n_fields and n_rhs must be >= 1");
+  Handle& h = hd->h;
+  if (h.kind != EO_SW_WALLS || h.opts.sw_f != 0.0)
+    return fail(EO_ERR_UNSUPPORTED, "the Laplacian filter needs a shallow-water handle built with f = 0");
+  std::vector<cx> cw(h.P);
+  for (int j = 0; j < h.P; ++j) {
+    const int i = h.pole_index[j];
+    if (!std::isfinite(s_set[2 * i]) || !std::isfinite(s_set[2 * i + 1]))
+      return fail(EO_ERR_INVALID_ARG, "non-finite residue");
+    cw[j] = (h.fit.aim[i] == 0.0 ? 1.0 : 2.0) * cx(s_set[2 * i], s_set[2 * i + 1]);
+  }
+  std::vector<cd> w;
+  double C[4];
+  pole_weights(h, cw, w, C);
+  cudaStream_t st = (cudaStream_t)stream;
+  cd* dw = nullptr;
+  EO_CUDA_TRY(cudaMallocAsync(&dw, sizeof(cd) * w.size(), st));
+  eo_status rc = EO_OK;
+  const cudaError_t e = cudaMemcpyAsync(dw, w.data(), sizeof(cd) * w.size(), cudaMemcpyHostToDevice, st);
+  if (e != cudaSuccess) rc = fail(EO_ERR_CUDA, std::string("cudaMemcpyAsync: ") + cudaGetErrorString(e));
+  if (!rc) rc = apply_laplacian_filter(h, dw, C, u_dev, n_fields * n_rhs, st);
+  cudaFreeAsync(dw, st);
+  const cudaError_t e2 = cudaStreamSynchronize(st);
+  if (!rc && e2 != cudaSuccess) rc = fail(EO_ERR_CUDA, std::string("cudaStreamSynchronize: ") + cudaGetErrorString(e2));
+  if (!rc) set_error("");
+  return rc;
+}
+
 eo_status eo_batch_create(int n, const eo_handle_t* handles, double* const* u_dev, const int* n_rhs,
                           eo_batch_t* out) {
   if (!out) return fail(EO_ERR_INVALID_ARG, "null output pointer");

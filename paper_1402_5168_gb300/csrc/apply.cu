@@ -1371,6 +1371,55 @@ eo_status apply_functions(Handle& h, int n_out, const cd* wgts, const double* Cs
   return EO_OK;
 }
 
+// ---------------------------------------------------------------- the filter S(k0 Delta)
+// Field column c of u ([ncol][n_nodes]) into the shallow-water state c of st ([c][3][n]):
+// velocities zero, h = the field.
+__global__ void k_filter_stage(const double* __restrict__ u, int ncol, long long n, double* __restrict__ st) {
+  const long long tot = (long long)ncol * 3 * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i / (3 * n), rem = i - c * 3 * n;
+    st[i] = rem < 2 * n ? 0.0 : u[c * n + (rem - 2 * n)];
+  }
+}
+
+// h of state c of st back into field column c of u.
+__global__ void k_filter_unstage(const double* __restrict__ st, int ncol, long long n, double* __restrict__ u) {
+  const long long tot = (long long)ncol * n;
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < tot; i += (long long)gridDim.x * blockDim.x) {
+    const long long c = i / n, k = i - c * n;
+    u[i] = st[(c * 3 + 2) * n + k];
+  }
+}
+
+// S(k0 Delta) on ncol real fields, in place (Section 3.3).  The handle is a
+// shallow-water handle with f = 0: its per-pole elliptic solve is
+// (tau^2 g H Delta - alpha^2) w = alpha r for the state (0, 0, r), so the h field of
+// the pole sum with the filter's weights is sum_m s_m alpha_m (k0 Delta - alpha_m^2)^{-1} r
+// with k0 = tau^2 g H, the natural (Neumann) condition on walls.  Columns go through
+// in groups of at most max_rhs, staged in two handle buffers.
+eo_status apply_laplacian_filter(Handle& h, const cd* wgts, const double* C, double* u, int ncol,
+                                 cudaStream_t st) {
+  const long long n = h.g.n_nodes;
+  const size_t per = (size_t)h.R * 3 * n;
+  eo_status rc;
+  if (!h.fstage && (rc = h.alloc((void**)&h.fstage, sizeof(double) * 2 * per, false))) return rc;
+  double* in = h.fstage;
+  double* out = h.fstage + per;
+  for (int c0 = 0; c0 < ncol; c0 += h.R) {
+    const int c = std::min(h.R, ncol - c0);
+    const unsigned nb = (unsigned)std::min<long long>(4096, ((long long)c * 3 * n + 255) / 256);
+    k_filter_stage<<<nb, 256, 0, st>>>(u + (size_t)c0 * n, c, n, in);
+    EO_CUDA_TRY(cudaGetLastError());
+    if ((rc = autotune(h, c, st))) return rc;
+    Sweep s;
+    if ((rc = sweep_to_edges(h, in, c, 0, h.P, wgts, s, st))) return rc;
+    if ((rc = finish_step(h, s, in, out, C, st))) return rc;
+    k_filter_unstage<<<nb, 256, 0, st>>>(out, c, n, u + (size_t)c0 * n);
+    EO_CUDA_TRY(cudaGetLastError());
+  }
+  return EO_OK;
+}
+
 // ---------------------------------------------------------------- batches of instances
 Batch::~Batch() {
   if (exec) cudaGraphExecDestroy(exec);

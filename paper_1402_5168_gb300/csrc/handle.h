@@ -151,6 +151,7 @@ struct Handle {
   int* tc_Aexp = nullptr;
   void* tc_B = nullptr;         // float2 [R][K][n_int]
   int* tc_status = nullptr;
+  double* fstage = nullptr;     // S(k0 Delta): two staging states [max_rhs][3][n_nodes]
   int64_t op_bytes = 0, ws_bytes = 0;
   Tuned root_tuned;             // autotuned launch shape of the root wall solve
   int tuned_R = 0;              // n_rhs the launch shapes were tuned for (0: not tuned)
@@ -192,6 +193,7 @@ eo_status apply_adjoint(Handle& h, double* y, int n_rhs, int n_steps, cudaStream
 eo_status apply_resolvent_noalloc(Handle& h, int j, const double* u, double* x, cudaStream_t st);
 eo_status apply_functions(Handle& h, int n_out, const cd* wgts, const double* Cs, const double* u, double* out,
                           cudaStream_t st);
+eo_status apply_laplacian_filter(Handle& h, const cd* wgts, const double* C, double* u, int ncol, cudaStream_t st);
 void pole_weights(const Handle& h, const std::vector<std::complex<double>>& cw, std::vector<cd>& wgt, double C[4]);
 
 // independent instances advanced together through one CUDA graph (apply.cu)
