@@ -26,6 +26,16 @@ sw    linearised rotating shallow water u_t = f v - g h_x, v_t = -f u - g h_y,
         alpha h_x + tau f h_y = -(alpha F1 + tau f F2)/(tau g)   (x = 0, 1)
         alpha h_y - tau f h_x = (tau f F1 - alpha F2)/(tau g)    (y = 0, 1).
 
+kappa the three-field wave form of Section 2.1, Example 2 (eq. "forward oper, inhom"):
+      u_tt = kappa Delta u on a periodic square, state (w, z, v) = (u_x, u_y, u_t),
+      w_t = v_x, z_t = v_y, v_t = kappa (w_x + z_y).  With the data scaled by tau
+      (eqs. "operator for inhomog, inverse" to "v for inhomog, inverse" with
+      alpha -> alpha / tau), (tau L - alpha)(W, Z, V) = (f_w, f_z, f_v) gives
+        (Delta - alpha^2 / (tau^2 kappa)) V = alpha f_v / (tau^2 kappa) + (d_x f_w + d_y f_z) / tau,
+        W = (tau V_x - f_w) / alpha,   Z = (tau V_y - f_z) / alpha
+      (eq. "w and z eqns"), V_x, V_y the recovered node gradient.  kappa is given at
+      the nodes (c2=kappa).
+
 With consistent=True the interior rows carry the extra term (tau f / alpha) Curl(G h),
 G the recovered node gradient of the post-map: the exact elimination of (U, V) for this
 discretisation, where Curl(G h) does not vanish next to leaf edges.  The per-pole solves
@@ -47,8 +57,10 @@ class Problem:
 
     def __init__(self, grid: sem.Grid, kind: str, tau: float, c2=None,
                  f: float = 0.0, g: float = 1.0, H: float = 1.0, consistent: bool = False):
-        if kind not in ("wave", "sw"):
+        if kind not in ("wave", "sw", "kappa"):
             raise ValueError(kind)
+        if kind == "kappa" and not grid.periodic:
+            raise ValueError("the three-field wave form is set on a periodic square")
         self.grid, self.kind, self.tau = grid, kind, float(tau)
         self.f, self.g, self.H = float(f), float(g), float(H)
         self.cls, self.side = grid.classify()
@@ -56,6 +68,10 @@ class Problem:
         if kind == "wave":
             self.a = np.asarray(c2, dtype=np.float64)
             self.n_fields = 2
+        elif kind == "kappa":
+            self.kappa = np.asarray(c2, dtype=np.float64)
+            self.a = np.ones(n)
+            self.n_fields = 3
         else:
             self.a = np.ones(n)
             self.n_fields = 3
@@ -73,9 +89,12 @@ class Problem:
         self.P_bnd = sp.diags((self.cls == 2).astype(float))
 
     # -------------------------------------------------------------- system
-    def kappa2(self, alpha: complex) -> complex:
+    def kappa2(self, alpha: complex):
+        """The shift of the elliptic rows: a number, or for the kappa form one per node."""
         if self.kind == "wave":
             return (alpha / self.tau) ** 2
+        if self.kind == "kappa":
+            return (alpha / self.tau) ** 2 / self.kappa
         D = alpha * alpha + (self.tau * self.f) ** 2
         return D / (self.tau ** 2 * self.g * self.H)
 
@@ -84,7 +103,10 @@ class Problem:
         boundary rows (Dirichlet identity for wave, oblique condition for sw)."""
         k2 = self.kappa2(alpha)
         n = self.grid.n_nodes
-        B = self.P_int @ (self.Lap - k2 * sp.identity(n)) + self.Flux.astype(np.complex128)
+        shift = sp.diags(k2 * np.ones(n)) if np.ndim(k2) else k2 * sp.identity(n)
+        B = self.P_int @ (self.Lap - shift) + self.Flux.astype(np.complex128)
+        if self.kind == "kappa":
+            return sp.csc_matrix(B)
         if self.kind == "wave":
             B = B + self.P_bnd
         else:
@@ -102,6 +124,11 @@ class Problem:
         if self.kind == "wave":
             fu, fv = state
             s = (alpha * fv + tau * (self.Lap @ fu)) / tau ** 2
+            return np.where(self.cls == 0, s, 0.0).astype(np.complex128)
+        if self.kind == "kappa":
+            fw, fz, fv = state
+            div, _ = sem.interior_div_curl(self.grid, fw, fz)
+            s = alpha * fv / (tau ** 2 * self.kappa) + div / tau
             return np.where(self.cls == 0, s, 0.0).astype(np.complex128)
         F1, F2, r = state
         f, g, H = self.f, self.g, self.H
@@ -121,6 +148,10 @@ class Problem:
         if self.kind == "wave":
             fu = state[0]
             return np.stack([(tau * w - fu) / alpha, w])
+        if self.kind == "kappa":
+            fw, fz, _ = state
+            vx, vy = sem.gradient(self.grid, w)
+            return np.stack([(tau * vx - fw) / alpha, (tau * vy - fz) / alpha, w])
         F1, F2, _ = state
         f, g = self.f, self.g
         D = alpha * alpha + (tau * f) ** 2
