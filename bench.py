@@ -421,16 +421,26 @@ def run_ours(args):
         op.apply(a, 1)
         op64.apply(b, 1)
         err1 = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
-        op.apply(a, args.steps - 1)
-        op64.apply(b, args.steps - 1)
+        half = max(1, args.steps // 2)
+        op.apply(a, half - 1)
+        op64.apply(b, half - 1)
+        n_half = float(torch.linalg.vector_norm(b))
+        if args.steps - half:
+            op.apply(a, args.steps - half)
+            op64.apply(b, args.steps - half)
         err = float(torch.linalg.vector_norm(a - b) / torch.linalg.vector_norm(b))
         growth = float(torch.linalg.vector_norm(b) / torch.linalg.vector_norm(torch.tensor(U0, device=dev)))
+        growth_late = float(torch.linalg.vector_norm(b)) / n_half
         # the FP64 trajectory's growth says whether the multi-step comparison measures
-        # precision (a bounded trajectory) or rounding amplified by growing discrete modes
+        # precision (a bounded trajectory) or rounding amplified by growing discrete modes.
+        # The Euclidean norm of a bounded trajectory may still change by a fixed factor
+        # (a wave state starting at rest moves energy from u into v), so the test is on
+        # the second half of the steps, where growing modes keep growing
         fp64 = {"fp64_value": world * R * args.steps / (ms64 / 1e3), "fp64_ms_per_step": ms64 / args.steps,
                 "mixed_vs_fp64_rel_l2_one_step": err1, "mixed_vs_fp64_rel_l2_after_steps": err,
                 "mixed_vs_fp64_after_steps": args.steps, "fp64_state_norm_growth": growth,
-                "mixed_vs_fp64_after_steps_meaningful": bool(growth <= 2.0)}
+                "fp64_state_norm_growth_second_half": growth_late,
+                "mixed_vs_fp64_after_steps_meaningful": bool(growth_late <= 2.0)}
         del op64
     if rank != 0:
         dist.destroy_process_group()

@@ -53,9 +53,18 @@ typedef enum {
 typedef enum {
   EO_WAVE_DIRICHLET = 0, /* u_t = v, v_t = div(c^2 grad u), u = 0 on the walls
                             (two-field form of Example 2, Section 2.1)          */
-  EO_SW_WALLS = 1        /* u_t = f v - g h_x, v_t = -f u - g h_y,
+  EO_SW_WALLS = 1,       /* u_t = f v - g h_x, v_t = -f u - g h_y,
                             h_t = -H (u_x + v_y), no normal flow at the walls
                             (Example 1, Section 2.1, constant f, g, H)          */
+  EO_WAVE_KAPPA = 2      /* u_tt = kappa Delta u in the three-field form of Example 2
+                            (Section 2.1, eq. "forward oper, inhom"): state (w, z, v) =
+                            (u_x, u_y, u_t), w_t = v_x, z_t = v_y, v_t = kappa (w_x + z_y),
+                            on a periodic grid (Section 4.2); kappa > 0 at the nodes;
+                            per-box operators.  Its resolvent is the elliptic solve
+                            (Delta - alpha^2 / (tau^2 kappa)) v = alpha f_v / (tau^2 kappa)
+                            + (d_x f_w + d_y f_z) / tau, then w = (tau v_x - f_w) / alpha,
+                            z = (tau v_y - f_z) / alpha (eqs. "w and z eqns" to "v for
+                            inhomog, inverse" with the data scaled by tau)        */
 } eo_kind;
 
 typedef enum {
@@ -195,8 +204,11 @@ eo_status eo_grid_destroy(eo_grid_t grid);
  * operators, merge-level Schur complements, and for EO_SW_WALLS the root
  * oblique-boundary solve.  Operators stay resident in device memory until
  * eo_destroy.
- *   coeff: HOST array of n_nodes doubles with c^2 at the nodes (EO_WAVE_DIRICHLET);
- *          ignored (may be NULL) for EO_SW_WALLS.
+ *   coeff: HOST array of n_nodes doubles with c^2 (EO_WAVE_DIRICHLET) or kappa
+ *          (EO_WAVE_KAPPA) at the nodes, positive and finite; ignored (may be NULL)
+ *          for EO_SW_WALLS.  EO_WAVE_KAPPA needs a periodic grid and per-box
+ *          operators (shared_ops = 0) and does not take tensor_leaves
+ *          (EO_ERR_UNSUPPORTED); the sw_* options do not apply to it.
  * Synchronous: returns when the operators are built.
  * Errors: EO_ERR_INVALID_ARG, EO_ERR_FIT, EO_ERR_SINGULAR, EO_ERR_OOM,
  *         EO_ERR_BUDGET, EO_ERR_CUDA, EO_ERR_UNSUPPORTED. */

@@ -14,7 +14,7 @@ import ctypes as C
 import numpy as np
 
 from . import _capi
-from ._capi import SW_WALLS, WAVE_DIRICHLET, ExpopError, Opts, check
+from ._capi import SW_WALLS, WAVE_DIRICHLET, WAVE_KAPPA, ExpopError, Opts, check
 
 __all__ = ["Grid", "Operator", "Batch", "fit", "fit_gauss", "leaf_basis", "WAVE_DIRICHLET", "SW_WALLS", "ExpopError"]
 

@@ -11,7 +11,7 @@ EO_OK = 0
 STATUS = {0: "EO_OK", 1: "EO_ERR_INVALID_ARG", 2: "EO_ERR_FIT", 3: "EO_ERR_SINGULAR", 4: "EO_ERR_OOM",
           5: "EO_ERR_BUDGET", 6: "EO_ERR_CUDA", 7: "EO_ERR_TIMEOUT", 8: "EO_ERR_UNSUPPORTED"}
 STATUS_CODES = {v: k for k, v in STATUS.items()}
-WAVE_DIRICHLET, SW_WALLS = 0, 1
+WAVE_DIRICHLET, SW_WALLS, WAVE_KAPPA = 0, 1, 2
 
 # every symbol include/expop.h declares
 SYMBOLS = ("eo_fit", "eo_grid_create", "eo_grid_create_periodic", "eo_grid_periodic", "eo_grid_info", "eo_grid_nodes", "eo_grid_destroy", "eo_build_operator",

@@ -281,7 +281,7 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   } else {
     h.K = 3; h.F = 3;
     const double f = o.sw_f, gg = o.sw_g, H = o.sw_H, tf = tau * f;
-    if (!(gg > 0) || !(H > 0)) return fail(EO_ERR_INVALID_ARG, "sw_g and sw_H must be positive");
+    if (!h.kappa_form && (!(gg > 0) || !(H > 0))) return fail(EO_ERR_INVALID_ARG, "sw_g and sw_H must be positive");
     for (int j = 0; j < h.P; ++j) {
       const cx a = h.alpha[j];
       const cx D = a * a + tf * tf;
@@ -447,6 +447,7 @@ eo_status setup(Handle& h, const eo_opts& o, cudaStream_t st) {
   }
   if (h.kind == EO_SW_WALLS) {
     if ((rc = h.alloc((void**)&h.afull, sizeof(double) * R * h.K * g.n_nodes, false))) return rc;
+    if (h.kappa_form && (rc = h.alloc((void**)&h.hw, sizeof(double) * g.n_nodes, true))) return rc;
   } else {
     if ((rc = h.alloc((void**)&h.acoef, sizeof(double) * g.n_nodes, false))) return rc;
   }
@@ -512,26 +513,42 @@ eo_status eo_build_operator(eo_grid_t grid, eo_kind kind, const double* coeff, c
                             void* stream, eo_handle_t* out) {
   if (!grid || !opts || !out) return fail(EO_ERR_INVALID_ARG, "null argument");
   *out = nullptr;
-  if (kind != EO_WAVE_DIRICHLET && kind != EO_SW_WALLS) return fail(EO_ERR_INVALID_ARG, "unknown kind");
-  if (kind == EO_WAVE_DIRICHLET && !coeff) return fail(EO_ERR_INVALID_ARG, "wave kind needs c^2 at the nodes");
-  if (kind == EO_WAVE_DIRICHLET && opts->shared_ops)
+  if (kind != EO_WAVE_DIRICHLET && kind != EO_SW_WALLS && kind != EO_WAVE_KAPPA)
+    return fail(EO_ERR_INVALID_ARG, "unknown kind");
+  const bool kap = kind == EO_WAVE_KAPPA;
+  if (kap && !grid->g.periodic)
+    return fail(EO_ERR_UNSUPPORTED, "EO_WAVE_KAPPA is built on periodic grids (eo_grid_create_periodic)");
+  if (kap && opts->tensor_leaves) return fail(EO_ERR_UNSUPPORTED, "tensor_leaves: not built for EO_WAVE_KAPPA");
+  if (kind != EO_SW_WALLS && !coeff) return fail(EO_ERR_INVALID_ARG, "wave kinds need their coefficient at the nodes");
+  if (kind != EO_SW_WALLS && opts->shared_ops)
     return fail(EO_ERR_INVALID_ARG, "shared operators need constant coefficients (EO_SW_WALLS)");
   if (opts->precision != EO_PREC_FP64 && opts->precision != EO_PREC_FP32 && opts->precision != EO_PREC_DF32)
     return fail(EO_ERR_INVALID_ARG, "unknown precision");
   if (opts->max_rhs < 0) return fail(EO_ERR_INVALID_ARG, "max_rhs must be >= 1");
-  if (kind == EO_WAVE_DIRICHLET)
+  if (kind != EO_SW_WALLS)
     for (int64_t i = 0; i < grid->g.n_nodes; ++i)
       if (!(coeff[i] > 0) || !std::isfinite(coeff[i]))
-        return fail(EO_ERR_INVALID_ARG, "c^2 must be positive and finite at every node");
+        return fail(EO_ERR_INVALID_ARG, kap ? "kappa must be positive and finite at every node"
+                                            : "c^2 must be positive and finite at every node");
   eo_handle_s* hs = new (std::nothrow) eo_handle_s;
   if (!hs) return fail(EO_ERR_OOM, "host allocation failed");
   Handle& h = hs->h;
   h.g = grid->g;
   h.kind = kind;
   h.opts = *opts;
+  if (kap) {
+    // the three-field wave form is shallow water with f = 0, g = -1 and depth
+    // H(x) = -kappa(x): the shift and the source of v carry 1 / (g H) = 1 / kappa per node
+    h.kind = EO_SW_WALLS;
+    h.kappa_form = 1;
+    h.opts.sw_f = 0.0;
+    h.opts.sw_g = -1.0;
+    h.opts.sw_H = -1.0;
+    h.opts.sw_consistent = 0;
+  }
   make_plan(h.g, h.plan);
   cudaStream_t st = (cudaStream_t)stream;
-  eo_status rc = setup(h, *opts, st);
+  eo_status rc = setup(h, h.opts, st);
   if (!rc) rc = build(h, coeff, st);
   if (!rc && opts->tensor_leaves) {
     // split the FP64 leaf operators for the tensor cores before reduced copies replace them
@@ -597,7 +614,7 @@ eo_status eo_apply_laplacian_filter(eo_handle_t hd, const double* s_set, double*
   if (!hd || !s_set || !u_dev) return fail(EO_ERR_INVALID_ARG, "null argument");
   if (n_fields < 1 || n_rhs < 1) return fail(EO_ERR_INVALID_ARG, "n_fields and n_rhs must be >= 1");
   Handle& h = hd->h;
-  if (h.kind != EO_SW_WALLS || h.opts.sw_f != 0.0)
+  if (h.kind != EO_SW_WALLS || h.opts.sw_f != 0.0 || h.kappa_form)
     return fail(EO_ERR_UNSUPPORTED, "the Laplacian filter needs a shallow-water handle built with f = 0");
   std::vector<cx> cw(h.P);
   for (int j = 0; j < h.P; ++j) {

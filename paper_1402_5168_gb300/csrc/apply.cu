@@ -664,6 +664,18 @@ __global__ void k_pre_sw(LeafGeo g, int R, long long n_nodes, const double* __re
 // Interior nodes by leaf differentiation; edge nodes owned by this leaf (S and W,
 // plus E / N on the walls of a walled square): normal derivative = mean of the one-sided
 // derivatives of the leaves that touch the edge, tangential = edge interpolant.
+// Three-field wave form: pre[r][1][i] = v[r][i] / kappa[i] at the interior nodes (the
+// source of the elliptic solve; the slot of the curl, which the form does not use).
+__global__ void k_pre_kappa(int R, long long n_int, long long n_nodes, const double* __restrict__ state,
+                            const double* __restrict__ hw, double* __restrict__ pre) {
+  const long long tot = (long long)R * n_int;
+  for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < tot;
+       t += (long long)gridDim.x * blockDim.x) {
+    const long long r = t / n_int, i = t - r * n_int;
+    pre[(2 * r + 1) * n_int + i] = state[(3 * r + 2) * n_nodes + i] * hw[i];
+  }
+}
+
 __global__ void k_post_sw(LeafGeo g, int R, long long n_nodes, int K, const double* __restrict__ afull,
                           const double* __restrict__ uin, double* __restrict__ uout, double C1, double C2,
                           double taug) {
@@ -1046,10 +1058,18 @@ eo_status sweep_to_edges(Handle& h, const double* uin, int R, int p0, int np, co
     if ((rc = h.trace_begin(st))) return rc;
     k_pre_sw<<<dim3(nleaf, R), 128, sizeof(double) * 2 * g.p * g.p, st>>>(geo, R, g.n_nodes, uin, h.pre);
     EO_CUDA_TRY(cudaGetLastError());
+    if (h.kappa_form) {
+      // three-field wave form: the source of v is v / kappa (the curl slot is free,
+      // its coefficient tau f / (g alpha) vanishing with f = 0)
+      k_pre_kappa<<<(unsigned)std::min<long long>(4096, (R * g.n_int + 255) / 256), 256, 0, st>>>(
+          R, g.n_int, g.n_nodes, uin, h.hw, h.pre);
+      EO_CUDA_TRY(cudaGetLastError());
+    }
     if ((rc = h.trace_end(TR_PRE, st))) return rc;
     s.src[0] = uin + 2 * g.n_nodes; s.src_rs[0] = 3 * g.n_nodes;
     s.src[1] = h.pre;               s.src_rs[1] = 2 * g.n_int;
     s.src[2] = h.pre + g.n_int;     s.src_rs[2] = 2 * g.n_int;
+    if (h.kappa_form) { s.src[0] = h.pre + g.n_int; s.src_rs[0] = 2 * g.n_int; }
   }
   // up: leaves
   cd* hcur = h.hA;

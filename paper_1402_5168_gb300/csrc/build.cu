@@ -142,9 +142,12 @@ __global__ void leaf_curl_ops(int p, const double* __restrict__ Dx, const double
 // Batch entry i = (pole gi, leaf) with leaf = i % nleaf, gi = i / nleaf:
 // A = Aii0 - kappa2[gi] I; XY = [I | -Aib]; T = Fbb (complex).
 // With Cib (consistent shallow water): Y's right-hand side is -(Aib + beta[gi] Cib).
+// With hw (per-box operators, a weight per interior node, leaf-major like the public
+// interior numbering): the shift is kappa2[gi] diag(hw) instead.
 __global__ void leaf_assemble(int nbatch, int nleaf, int ni, int nb, const cd* __restrict__ kappa2,
                               const double* Aii0, const double* Aib, const double* Fbb, const double* Cib,
-                              const cd* __restrict__ beta, cd* A, cd* XY, cd* T) {
+                              const cd* __restrict__ beta, const double* __restrict__ hw, cd* A, cd* XY,
+                              cd* T) {
   const size_t nA = (size_t)ni * ni, nXY = (size_t)ni * (ni + nb), nT = (size_t)nb * nb;
   const size_t tot = (size_t)nbatch * (nA + nXY + nT);
   for (size_t t = blockIdx.x * (size_t)blockDim.x + threadIdx.x; t < tot;
@@ -155,8 +158,9 @@ __global__ void leaf_assemble(int nbatch, int nleaf, int ni, int nb, const cd* _
     if (e < nA) {
       const int i = e % ni, j = e / ni;
       const cd k2 = kappa2[bi / nleaf];
+      const double wt = hw ? hw[leaf * ni + i] : 1.0;
       const double v = Aii0[leaf * nA + e];
-      A[bi * nA + e] = make_double2(v - (i == j ? k2.x : 0.0), (i == j ? -k2.y : 0.0));
+      A[bi * nA + e] = make_double2(v - (i == j ? wt * k2.x : 0.0), (i == j ? -wt * k2.y : 0.0));
     } else if (e < nA + nXY) {
       e -= nA;
       const int i = e % ni, j = e / ni;
@@ -530,6 +534,13 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
     acoef = h.acoef;   // kept: the apply's pre-map differentiates c^2 grad u
     EO_CUDA_TRY(cudaMemcpyAsync(acoef, coeff, sizeof(double) * g.n_nodes, cudaMemcpyHostToDevice, st));
   }
+  if (h.kappa_form) {
+    // 1 / kappa at every node: the shift's weight here, the source weight in the pre-map
+    std::vector<double> w(g.n_nodes);
+    for (int64_t i = 0; i < g.n_nodes; ++i) w[i] = 1.0 / coeff[i];
+    EO_CUDA_TRY(cudaMemcpyAsync(h.hw, w.data(), sizeof(double) * g.n_nodes, cudaMemcpyHostToDevice, st));
+    EO_CUDA_TRY(cudaStreamSynchronize(st));
+  }
   if ((rc = talloc((void**)&Aii0, sizeof(double) * nlo * ni * ni))) return rc;
   if ((rc = talloc((void**)&Aib, sizeof(double) * nlo * ni * nb))) return rc;
   if ((rc = talloc((void**)&Fbi, sizeof(double) * nlo * nb * ni))) return rc;
@@ -623,7 +634,7 @@ eo_status build(Handle& h, const double* coeff, cudaStream_t st) {
       }
       EO_CUDA_TRY(cudaMemcpyAsync(dbeta, hb.data(), sizeof(cd) * g, cudaMemcpyHostToDevice, st));
     }
-    leaf_assemble<<<2048, 256, 0, st>>>(nbl, nlo, ni, nb, kap, Aii0, Aib, Fbb, Cib, dbeta, Aw, XYp, T0);
+    leaf_assemble<<<2048, 256, 0, st>>>(nbl, nlo, ni, nb, kap, Aii0, Aib, Fbb, Cib, dbeta, h.hw, Aw, XYp, T0);
     EO_CUDA_TRY(cudaGetLastError());
     {
       std::vector<cd*> pa(nbl), pb(nbl);

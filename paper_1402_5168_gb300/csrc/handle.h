@@ -152,6 +152,10 @@ struct Handle {
   void* tc_B = nullptr;         // float2 [R][K][n_int]
   int* tc_status = nullptr;
   double* fstage = nullptr;     // S(k0 Delta): two staging states [max_rhs][3][n_nodes]
+  // three-field wave form (EO_WAVE_KAPPA), run as shallow water with f = 0, g = -1,
+  // H(x) = -kappa(x): per-node weight 1 / kappa on the shift and on the source of v
+  int kappa_form = 0;
+  double* hw = nullptr;         // 1 / kappa at every node (device)
   int64_t op_bytes = 0, ws_bytes = 0;
   Tuned root_tuned;             // autotuned launch shape of the root wall solve
   int tuned_R = 0;              // n_rhs the launch shapes were tuned for (0: not tuned)
