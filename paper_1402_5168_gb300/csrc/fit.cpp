@@ -221,14 +221,17 @@ static eo_status fit_for_poles_grid(int N, double delta, Fit& out, const double*
 eo_status fit_for_poles(int N, double delta, Fit& out) {
   if (N < 3 || N % 2 == 0) return fail(EO_ERR_INVALID_ARG, "n_poles must be odd and >= 3");
   // beyond ~100 poles the dense search is slow and the wide construction is as good
-  if (N > 101) return fit_wide_poles(N, delta, out);
-  if (fit_for_poles_grid(N, delta, out, kS, (int)(sizeof(kS) / sizeof(kS[0])), kRatio,
-                         (int)(sizeof(kRatio) / sizeof(kRatio[0]))) == EO_OK)
-    return EO_OK;
-  if (fit_for_poles_grid(N, delta, out, kSFine, (int)(sizeof(kSFine) / sizeof(kSFine[0])), kRatioFine,
-                         (int)(sizeof(kRatioFine) / sizeof(kRatioFine[0]))) == EO_OK)
-    return EO_OK;
-  if (fit_wide_poles(N, delta, out) == EO_OK) return EO_OK;
+  if (N > 101) {
+    if (fit_wide_poles(N, delta, out) == EO_OK) return EO_OK;
+  } else {
+    if (fit_for_poles_grid(N, delta, out, kS, (int)(sizeof(kS) / sizeof(kS[0])), kRatio,
+                           (int)(sizeof(kRatio) / sizeof(kRatio[0]))) == EO_OK)
+      return EO_OK;
+    if (fit_for_poles_grid(N, delta, out, kSFine, (int)(sizeof(kSFine) / sizeof(kSFine[0])), kRatioFine,
+                           (int)(sizeof(kRatioFine) / sizeof(kRatioFine[0]))) == EO_OK)
+      return EO_OK;
+    if (fit_wide_poles(N, delta, out) == EO_OK) return EO_OK;
+  }
   // Last resort: the approximant with N - 2 poles plus one more conjugate pole
   // pair on the same line with zero residues.  R is unchanged, so eqs. RM_prop1
   // and RM_prop2 hold with the band of the smaller fit.

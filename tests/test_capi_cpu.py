@@ -53,7 +53,7 @@ def test_bad_arguments_are_rejected(capi):
     assert L.eo_destroy(None) == 0
 
 
-@pytest.mark.parametrize("n_poles,min_X", [(21, 3.0), (57, 10.0), (61, 12.0)])
+@pytest.mark.parametrize("n_poles,min_X", [(21, 3.0), (57, 10.0), (61, 12.0), (125, 20.0)])
 def test_library_fit_meets_contract(capi, n_poles, min_X):
     # the host fitter's output checked by the oracle's brute-force evaluation of
     # eqs. RM_prop1 / RM_prop2 (independent code)
@@ -65,6 +65,16 @@ def test_library_fit_meets_contract(capi, n_poles, min_X):
     assert band <= 1e-10 and mod <= 1.0 + 1e-12 and tail < 1.0
     assert np.array_equal(alpha[::-1], np.conj(alpha)) and np.array_equal(b[::-1], np.conj(b))
     assert np.abs(b).max() <= 100.0
+
+
+def test_every_odd_wide_pole_count_fits(capi):
+    # the 64-instance batch draws up to 201 poles; every odd count above 101 (the wide
+    # construction) must give an approximant: the last resort adds a zero-residue pair
+    # to the next smaller fit, as it does for the dense search below 101
+    import paper_1402_5168_gb300 as eo
+    for n in range(103, 203, 2):
+        alpha, b, X = eo.fit(n)
+        assert alpha.size == n and X > 5.0, n
 
 
 def test_library_fit_for_a_band(capi):
