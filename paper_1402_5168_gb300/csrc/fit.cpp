@@ -457,7 +457,7 @@ eo_status fit_for_band(double X, double delta, int nmax, Fit& out) {
   if (!(X > 0)) return fail(EO_ERR_INVALID_ARG, "band*tau must be positive");
   if (X > 40.0) return fit_wide(X, delta, out);
   std::vector<cplx> al, b;
-  for (int N = 5; N <= std::min(nmax, 301); N += 2) {
+  for (int N = 5; N <= std::min(nmax, 101); N += 2) {
     const int M = (N - 1) / 2;
     for (double s : kS)
       for (double ratio : kRatio) {
@@ -469,6 +469,9 @@ eo_status fit_for_band(double X, double delta, int nmax, Fit& out) {
         }
       }
   }
+  // no line of the search grid fits this band: the wide construction (trapezoidal
+  // centre, fitted ends) covers it with more poles
+  if (fit_wide(X, delta, out) == EO_OK) return EO_OK;
   return fail(EO_ERR_FIT, "band*tau too wide for the supported pole counts");
 }
 

@@ -33,19 +33,30 @@ __device__ __forceinline__ void cfma(float2& acc, float2 a, float2 b) {
 //              cross terms in a plain FP32 sum.  This runs on the FP32 pipe at
 //              near-FP64 accuracy (GB300's FP64 pipe is ~60x slower than FP32).
 // Vectors enter the products in the same type (Cv::from); Acc holds the sums
-// and returns them as FP64 (Cv::to).
+// and returns them as FP64 (Cv::to).  Part is a partial sum of one k group in the
+// cross-group reduction of cmv (16 bytes, the size of a cd): FP64 for double2 and
+// float2; for float4 the renormalised FP32 pair, so that the reduction stays on the
+// FP32 pipe and only the final sum is converted to FP64.
 template <typename TA> struct Cv;
 template <> struct Cv<double2> {
   typedef double2 Acc;
+  typedef cd Part;
   __device__ static double2 from(cd v) { return v; }
   __device__ static cd to(const Acc& v) { return v; }
+  __device__ static Part part(const Acc& v) { return v; }
+  __device__ static void part_add(Part& s, const Part& v) { s.x += v.x; s.y += v.y; }
+  __device__ static cd part_to(const Part& v) { return v; }
   __device__ static Acc zero() { return make_double2(0.0, 0.0); }
   __device__ static void mac(Acc& acc, const double2& a, const double2& b) { cfma(acc, a, b); }
 };
 template <> struct Cv<float2> {
   typedef float2 Acc;
+  typedef cd Part;
   __device__ static float2 from(cd v) { return make_float2((float)v.x, (float)v.y); }
   __device__ static cd to(const Acc& v) { return make_double2(v.x, v.y); }
+  __device__ static Part part(const Acc& v) { return to(v); }
+  __device__ static void part_add(Part& s, const Part& v) { s.x += v.x; s.y += v.y; }
+  __device__ static cd part_to(const Part& v) { return v; }
   __device__ static Acc zero() { return make_float2(0.f, 0.f); }
   __device__ static void mac(Acc& acc, const float2& a, const float2& b) { cfma(acc, a, b); }
 };
@@ -65,8 +76,22 @@ __device__ __forceinline__ void df_prod(float xh, float xl, float yh, float yl, 
   const float e = __fmaf_rn(xh, yh, -p);
   lo = __fmaf_rn(xh, yl, __fmaf_rn(xl, yh, e));
 }
+// (hi, lo) = a + b exactly (two-sum, no ordering assumption)
+__device__ __forceinline__ void df_renorm(float a, float b, float& hi, float& lo) {
+  hi = __fadd_rn(a, b);
+  const float bp = __fsub_rn(hi, a);
+  lo = __fadd_rn(__fsub_rn(a, __fsub_rn(hi, bp)), __fsub_rn(b, bp));
+}
+// s = s + v for FP32 pairs (hi, lo): the error of the hi sum and both lo parts join a
+// renormalised lo (about 2^-47 of the larger operand)
+__device__ __forceinline__ void df_pair_add(float& sh, float& sl, float vh, float vl) {
+  float c = 0.f;
+  df_two_sum(sh, c, vh);
+  df_renorm(sh, __fadd_rn(c, __fadd_rn(sl, vl)), sh, sl);
+}
 template <> struct Cv<float4> {
   typedef DFAcc Acc;
+  typedef float4 Part;   // (re_hi, im_hi, re_lo, im_lo)
   __device__ static float4 from(cd v) {
     const float rh = __double2float_rn(v.x), ih = __double2float_rn(v.y);
     return make_float4(rh, ih, __double2float_rn(v.x - (double)rh), __double2float_rn(v.y - (double)ih));
@@ -75,6 +100,19 @@ template <> struct Cv<float4> {
     return make_double2((double)a.sr + ((double)a.cr + (double)a.lr), (double)a.si + ((double)a.ci + (double)a.li));
   }
   __device__ static Acc zero() { return DFAcc{0.f, 0.f, 0.f, 0.f, 0.f, 0.f}; }
+  __device__ static Part part(const Acc& a) {
+    float rh, rl, ih, il;
+    df_renorm(a.sr, __fadd_rn(a.cr, a.lr), rh, rl);
+    df_renorm(a.si, __fadd_rn(a.ci, a.li), ih, il);
+    return make_float4(rh, ih, rl, il);
+  }
+  __device__ static void part_add(Part& s, const Part& v) {
+    df_pair_add(s.x, s.z, v.x, v.z);
+    df_pair_add(s.y, s.w, v.y, v.w);
+  }
+  __device__ static cd part_to(const Part& v) {
+    return make_double2((double)v.x + (double)v.z, (double)v.y + (double)v.w);
+  }
   // re += a_re b_re - a_im b_im ; im += a_re b_im + a_im b_re
   __device__ static void mac(Acc& acc, const float4& a, const float4& b) {
     float p, lo;
@@ -156,20 +194,19 @@ __device__ void cmv(const TA* __restrict__ A, int lda, int rows, int k, const TA
 #pragma unroll
         for (int c = 0; c < NC; ++c) Cs[c * rows + r] = Cv<TA>::to(acc[c]);
     } else {
+      typedef typename Cv<TA>::Part Part;
+      static_assert(sizeof(Part) == sizeof(cd), "a partial sum takes the slot of a cd");
+      Part* pr = reinterpret_cast<Part*>(red);
       if (kg < ks)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) red[(kg * NC + c) * rp + ri] = Cv<TA>::to(acc[c]);
+        for (int c = 0; c < NC; ++c) pr[(kg * NC + c) * rp + ri] = Cv<TA>::part(acc[c]);
       __syncthreads();
       if (kg == 0 && r < rows) {
 #pragma unroll
         for (int c = 0; c < NC; ++c) {
-          cd s = red[c * rp + ri];
-          for (int g = 1; g < ks; ++g) {
-            const cd v = red[(g * NC + c) * rp + ri];
-            s.x += v.x;
-            s.y += v.y;
-          }
-          Cs[c * rows + r] = s;
+          Part s = pr[c * rp + ri];
+          for (int g = 1; g < ks; ++g) Cv<TA>::part_add(s, pr[(g * NC + c) * rp + ri]);
+          Cs[c * rows + r] = Cv<TA>::part_to(s);
         }
       }
     }

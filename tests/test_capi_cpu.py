@@ -87,6 +87,17 @@ def test_library_fit_for_a_band(capi):
     assert alpha.size <= 41
 
 
+def test_band_between_the_dense_search_and_the_wide_construction(capi):
+    # X = 18: no line of the dense search grid up to 101 poles fits it; the wide
+    # construction takes over (with more poles) and the contract still holds
+    import paper_1402_5168_gb300 as eo
+    from oracle import rational
+    alpha, b, X = eo.fit(0, 18.0)
+    assert X == 18.0
+    band, mod, tail = rational.check_contract(alpha, b, X, 1e-10)
+    assert band <= 1e-10 and mod <= 1.0 + 1e-12 and tail < 1.0
+
+
 def test_wide_band_fit_meets_contract(capi):
     # wide band (X = 300): pole line with end corrections, checked by the oracle
     import paper_1402_5168_gb300 as eo
