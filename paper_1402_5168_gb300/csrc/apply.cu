@@ -18,6 +18,7 @@
 #include <cmath>
 #include <mutex>
 #include <string>
+#include <type_traits>
 #include <vector>
 
 #include "fused.cuh"
@@ -120,9 +121,13 @@ __global__ void __launch_bounds__(256) k_up_merge(Sweep s, MergeArgs m, const cd
 // [-Z; U] h3 = E [-Ze e - Zo o ...]: two products with the (n3/2 + nbd/4) x n3/2 blocks,
 // then w3[s] = ye[s] + yo[s], w3[J s] = ye[s] - yo[s] and, on the parent boundary,
 // dh[i] = ye[n3/2 + orb i] + osg[i] yo[n3/2 + orb i].
-template <int NC, typename TA>
+template <int NC, typename TA, int FMT>
 __global__ void __launch_bounds__(256) k_up_merge_sym(Sweep s, MergeArgs m, const cd* __restrict__ hin,
                                                       cd* __restrict__ hout) {
+  // FMT (FP32-pair blocks only): bit 0, the children's boundary data hin are complex FP32
+  // pairs (written so by the level below); bit 1, hout is written as pairs for the level
+  // above.  The sums around the block products then stay on the FP32 pipe.
+  constexpr bool PIN = (FMT & 1) != 0, POUT = (FMT & 2) != 0;
   extern __shared__ cd smem[];
   const int pl = blockIdx.y, p = s.p0 + pl;
   const int ncols = m.nbox * s.R;
@@ -133,49 +138,88 @@ __global__ void __launch_bounds__(256) k_up_merge_sym(Sweep s, MergeArgs m, cons
   cd* red = Cs + 2 * NC * rh;
   for (int e = threadIdx.x; e < NC * n3h; e += blockDim.x) {
     const int c = e / n3h, t = e - c * n3h;
-    cd ev = make_double2(0.0, 0.0), od = make_double2(0.0, 0.0);
-    if (c0 + c < ncols) {
-      int box, r, ca, cb;
-      col_box(c0 + c, s.R, box, r);
-      children(m, box, ca, cb);
-      const cd* hr = hin + ((long long)pl * s.R + r) * m.nbox_c * m.nbd_c;
-      const int tj = n3 - 1 - t;
-      const cd x1 = hr[(long long)ca * m.nbd_c + m.a3[t]], y1 = hr[(long long)cb * m.nbd_c + m.b3[t]];
-      const cd x2 = hr[(long long)ca * m.nbd_c + m.a3[tj]], y2 = hr[(long long)cb * m.nbd_c + m.b3[tj]];
-      const double ar = x1.x + y1.x, ai = x1.y + y1.y, br = x2.x + y2.x, bi = x2.y + y2.y;
-      ev = make_double2(0.5 * (ar + br), 0.5 * (ai + bi));
-      od = make_double2(0.5 * (ar - br), 0.5 * (ai - bi));
+    if constexpr (PIN) {
+      float4 ev = make_float4(0.f, 0.f, 0.f, 0.f), od = ev;
+      if (c0 + c < ncols) {
+        int box, r, ca, cb;
+        col_box(c0 + c, s.R, box, r);
+        children(m, box, ca, cb);
+        const float4* hr = reinterpret_cast<const float4*>(hin) + ((long long)pl * s.R + r) * m.nbox_c * m.nbd_c;
+        const int tj = n3 - 1 - t;
+        const float4 a = cp_add(hr[(long long)ca * m.nbd_c + m.a3[t]], hr[(long long)cb * m.nbd_c + m.b3[t]]);
+        const float4 b = cp_add(hr[(long long)ca * m.nbd_c + m.a3[tj]], hr[(long long)cb * m.nbd_c + m.b3[tj]]);
+        ev = cp_scale(cp_add(a, b), 0.5f);
+        od = cp_scale(cp_add(a, cp_scale(b, -1.0f)), 0.5f);
+      }
+      Bs[c * n3 + t] = ev;
+      Bs[c * n3 + n3h + t] = od;
+    } else {
+      cd ev = make_double2(0.0, 0.0), od = make_double2(0.0, 0.0);
+      if (c0 + c < ncols) {
+        int box, r, ca, cb;
+        col_box(c0 + c, s.R, box, r);
+        children(m, box, ca, cb);
+        const cd* hr = hin + ((long long)pl * s.R + r) * m.nbox_c * m.nbd_c;
+        const int tj = n3 - 1 - t;
+        const cd x1 = hr[(long long)ca * m.nbd_c + m.a3[t]], y1 = hr[(long long)cb * m.nbd_c + m.b3[t]];
+        const cd x2 = hr[(long long)ca * m.nbd_c + m.a3[tj]], y2 = hr[(long long)cb * m.nbd_c + m.b3[tj]];
+        const double ar = x1.x + y1.x, ai = x1.y + y1.y, br = x2.x + y2.x, bi = x2.y + y2.y;
+        ev = make_double2(0.5 * (ar + br), 0.5 * (ai + bi));
+        od = make_double2(0.5 * (ar - br), 0.5 * (ai - bi));
+      }
+      Bs[c * n3 + t] = Cv<TA>::from(ev);
+      Bs[c * n3 + n3h + t] = Cv<TA>::from(od);
     }
-    Bs[c * n3 + t] = Cv<TA>::from(ev);
-    Bs[c * n3 + n3h + t] = Cv<TA>::from(od);
   }
   __syncthreads();
   const TA* A = (const TA*)m.ZUs + (long long)p * m.zsps;
-  cmv<NC, TA>(A, rh, rh, n3h, Bs, n3, Cs, red);
-  cmv<NC, TA>(A + (long long)rh * n3h, rh, rh, n3h, Bs + n3h, n3, Cs + (size_t)NC * rh, red);
-  const cd* Ce = Cs;
-  const cd* Co = Cs + (size_t)NC * rh;
+  cmv<NC, TA, POUT>(A, rh, rh, n3h, Bs, n3, Cs, red);
+  cmv<NC, TA, POUT>(A + (long long)rh * n3h, rh, rh, n3h, Bs + n3h, n3, Cs + (size_t)NC * rh, red);
   for (int e = threadIdx.x; e < NC * m.zu_rows; e += blockDim.x) {
     const int c = e / m.zu_rows, row = e - c * m.zu_rows;
     if (c0 + c >= ncols) continue;
     int box, r;
     col_box(c0 + c, s.R, box, r);
-    if (row < n3) {
-      const int sr = row < n3h ? row : n3 - 1 - row;
-      const double sg = row < n3h ? 1.0 : -1.0;
-      const cd a = Ce[c * rh + sr], b = Co[c * rh + sr];
-      m.w3[(((long long)pl * s.R + r) * m.nbox + box) * n3 + row] = make_double2(a.x + sg * b.x, a.y + sg * b.y);
+    if constexpr (POUT) {
+      const float4* Ce = reinterpret_cast<const float4*>(Cs);
+      const float4* Co = Ce + (size_t)NC * rh;
+      if (row < n3) {
+        const int sr = row < n3h ? row : n3 - 1 - row;
+        const float4 b = row < n3h ? Co[c * rh + sr] : cp_scale(Co[c * rh + sr], -1.0f);
+        m.w3[(((long long)pl * s.R + r) * m.nbox + box) * n3 + row] = cp_to(cp_add(Ce[c * rh + sr], b));
+      } else {
+        const int i = row - n3;
+        const int k = n3h + m.orb[i];
+        const float4 b = cp_scale(Co[c * rh + k], (float)m.osg[i]);
+        int ca, cb;
+        children(m, box, ca, cb);
+        const long long xi = ((long long)pl * s.R + r) * m.nbox_c * m.nbd_c +
+                             (long long)(m.par_child[i] ? cb : ca) * m.nbd_c + m.par_idx[i];
+        const float4 x = PIN ? reinterpret_cast<const float4*>(hin)[xi] : Cv<float4>::from(hin[xi]);
+        reinterpret_cast<float4*>(hout)[(((long long)pl * s.R + r) * m.nbox + box) * m.nbd + i] =
+            cp_add(x, cp_add(Ce[c * rh + k], b));
+      }
     } else {
-      const int i = row - n3;
-      const int k = n3h + m.orb[i];
-      const double sg = (double)m.osg[i];
-      const cd a = Ce[c * rh + k], b = Co[c * rh + k];
-      int ca, cb;
-      children(m, box, ca, cb);
-      const cd* hr = hin + ((long long)pl * s.R + r) * m.nbox_c * m.nbd_c;
-      const cd x = hr[(long long)(m.par_child[i] ? cb : ca) * m.nbd_c + m.par_idx[i]];
-      hout[(((long long)pl * s.R + r) * m.nbox + box) * m.nbd + i] =
-          make_double2(x.x + a.x + sg * b.x, x.y + a.y + sg * b.y);
+      const cd* Ce = Cs;
+      const cd* Co = Cs + (size_t)NC * rh;
+      if (row < n3) {
+        const int sr = row < n3h ? row : n3 - 1 - row;
+        const double sg = row < n3h ? 1.0 : -1.0;
+        const cd a = Ce[c * rh + sr], b = Co[c * rh + sr];
+        m.w3[(((long long)pl * s.R + r) * m.nbox + box) * n3 + row] = make_double2(a.x + sg * b.x, a.y + sg * b.y);
+      } else {
+        const int i = row - n3;
+        const int k = n3h + m.orb[i];
+        const double sg = (double)m.osg[i];
+        const cd a = Ce[c * rh + k], b = Co[c * rh + k];
+        int ca, cb;
+        children(m, box, ca, cb);
+        const long long xi = ((long long)pl * s.R + r) * m.nbox_c * m.nbd_c +
+                             (long long)(m.par_child[i] ? cb : ca) * m.nbd_c + m.par_idx[i];
+        const cd x = PIN ? cp_to(reinterpret_cast<const float4*>(hin)[xi]) : hin[xi];
+        hout[(((long long)pl * s.R + r) * m.nbox + box) * m.nbd + i] =
+            make_double2(x.x + a.x + sg * b.x, x.y + a.y + sg * b.y);
+      }
     }
   }
 }
@@ -826,15 +870,36 @@ struct UpLeaf {
 
 template <int NC, typename TA>
 struct UpMerge {
-  static eo_status run(const Sweep& s, const MergeArgs& m, const cd* hin, cd* hout, int nt, cudaStream_t st) {
+  // fmt: formats of hin / hout for the FP32-pair symmetric kernel (k_up_merge_sym FMT)
+  static eo_status run(const Sweep& s, const MergeArgs& m, const cd* hin, cd* hout, int nt, int fmt,
+                       cudaStream_t st) {
     dim3 grid((m.nbox * s.R + NC - 1) / NC, s.P);
     const size_t smem = sizeof(cd) * ((size_t)NC * (m.n3 + m.zu_rows) + 256 * NC) + 64;
     if (m.sym) {
-      EO_SET_SMEM((k_up_merge_sym<NC, TA>), smem);
-      k_up_merge_sym<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(m.rh), smem, st>>>(s, m, hin, hout);
+      const int thr = nt > 0 ? nt : cmv_threads(m.rh);
+      if constexpr (std::is_same<TA, float4>::value) {
+        if (fmt == 1) {
+          EO_SET_SMEM((k_up_merge_sym<NC, TA, 1>), smem);
+          k_up_merge_sym<NC, TA, 1><<<grid, thr, smem, st>>>(s, m, hin, hout);
+        } else if (fmt == 2) {
+          EO_SET_SMEM((k_up_merge_sym<NC, TA, 2>), smem);
+          k_up_merge_sym<NC, TA, 2><<<grid, thr, smem, st>>>(s, m, hin, hout);
+        } else if (fmt == 3) {
+          EO_SET_SMEM((k_up_merge_sym<NC, TA, 3>), smem);
+          k_up_merge_sym<NC, TA, 3><<<grid, thr, smem, st>>>(s, m, hin, hout);
+        } else {
+          EO_SET_SMEM((k_up_merge_sym<NC, TA, 0>), smem);
+          k_up_merge_sym<NC, TA, 0><<<grid, thr, smem, st>>>(s, m, hin, hout);
+        }
+      } else {
+        if (fmt) return fail(EO_ERR_INVALID_ARG, "pair-format boundary data need FP32-pair blocks");
+        EO_SET_SMEM((k_up_merge_sym<NC, TA, 0>), smem);
+        k_up_merge_sym<NC, TA, 0><<<grid, thr, smem, st>>>(s, m, hin, hout);
+      }
       EO_CUDA_TRY(cudaGetLastError());
       return EO_OK;
     }
+    if (fmt) return fail(EO_ERR_INVALID_ARG, "pair-format boundary data need the symmetric merge kernel");
     EO_SET_SMEM((k_up_merge<NC, TA>), smem);
     k_up_merge<NC, TA><<<grid, nt > 0 ? nt : cmv_threads(m.zu_rows), smem, st>>>(s, m, hin, hout);
     EO_CUDA_TRY(cudaGetLastError());
@@ -983,6 +1048,18 @@ FusedLevels fused_plan(const Handle& h, int R) {
   return FusedLevels{};
 }
 
+// Formats of the boundary data around up level l (k_up_merge_sym FMT): a level run by the
+// FP32-pair symmetric kernel writes FP32 pairs when the level above is one too (not the
+// root's input, not a fused level); it reads pairs when the level below wrote them.
+static bool up_pairs_out(const Handle& h, int l, int Lf) {
+  const int L = h.plan.L();
+  auto pair_level = [&](int k) { return k > Lf && k <= L && h.lv[k].sym && h.lv[k].fp32 == 2; };
+  return l < L && pair_level(l) && pair_level(l + 1);
+}
+static int up_format(const Handle& h, int l, int Lf) {
+  return (l > 1 && up_pairs_out(h, l - 1, Lf) ? 1 : 0) | (up_pairs_out(h, l, Lf) ? 2 : 0);
+}
+
 template <typename TA>
 static eo_status run_up_fused(const Sweep& s, const FusedLevels& f, const cd* h0, cd* hout, size_t smem,
                               cudaStream_t st) {
@@ -1094,7 +1171,8 @@ eo_status sweep_to_edges(Handle& h, const double* uin, int R, int p0, int np, co
     if ((rc = h.trace_begin(st))) return rc;
     const Tuned tu = h.lv[l].up;
     const int nc = tu.nc ? tu.nc : pick_nc(h.shared, R, m.n3, m.zu_rows, m.nbox);
-    if ((rc = dispatch<UpMerge>(h.lv[l].fp32, nc, s, m, hcur, hnext, tu.nt, st))) return rc;
+    if ((rc = dispatch<UpMerge>(h.lv[l].fp32, nc, s, m, hcur, hnext, tu.nt, up_format(h, l, fl.Lf), st)))
+      return rc;
     if ((rc = h.trace_end(TR_UP_MERGE, st))) return rc;
     std::swap(hcur, hnext);
   }
@@ -1271,7 +1349,8 @@ eo_status autotune(Handle& h, int R, cudaStream_t st) {
     float best = 1e30f;
     for (int nc : nc_list(m.nbox, m.n3, m.zu_rows))
       for (int nt : nt_list(m.sym ? m.rh : m.zu_rows)) {
-        const float t = timeit([&] { return dispatch<UpMerge>(ld.fp32, nc, s, m, h.hA, h.hB, nt, st); });
+        const int fmt = up_format(h, l, fused_plan(h, R).Lf);
+        const float t = timeit([&] { return dispatch<UpMerge>(ld.fp32, nc, s, m, h.hA, h.hB, nt, fmt, st); });
         if (t < 0) return fail(EO_ERR_CUDA, "autotune: merge launch failed");
         if (t < best) { best = t; ld.up = Tuned{nc, nt}; }
       }

@@ -152,10 +152,26 @@ inline int cmv_threads(int rows) {
   return rp * (256 / rp);
 }
 
+// Complex FP32 pairs (re_hi, im_hi, re_lo, im_lo), the layout of Cv<float4>: sums on the
+// FP32 pipe (the FP64 pipe of GB300 runs at about 1/64 of its rate).
+__device__ __forceinline__ float4 cp_add(float4 a, const float4& b) {
+  df_pair_add(a.x, a.z, b.x, b.z);
+  df_pair_add(a.y, a.w, b.y, b.w);
+  return a;
+}
+__device__ __forceinline__ float4 cp_scale(const float4& a, float s) {   // s a power of two (exact)
+  return make_float4(s * a.x, s * a.y, s * a.z, s * a.w);
+}
+__device__ __forceinline__ cd cp_to(const float4& a) {
+  return make_double2((double)a.x + (double)a.z, (double)a.y + (double)a.w);
+}
+
 // C[c][r] = sum_{j<k} A[r + j*lda] B[c][j]  for r < rows, c < NC.
 // Bs: shared [NC][kb]; Cs: shared [NC][rows]; red: shared [256 * NC].
 // blockDim.x >= cmv_rp(rows); threads beyond rp * (blockDim.x / rp) idle.
-template <int NC, typename TA>
+// RAW: Cs receives Cv<TA>::Part values (for FP32 pairs the pair itself, no FP64
+// conversion) in the slots of the cd entries.
+template <int NC, typename TA, bool RAW = false>
 __device__ void cmv(const TA* __restrict__ A, int lda, int rows, int k, const TA* Bs, int kb,
                     cd* Cs, cd* red) {
   const int nt = blockDim.x, t = threadIdx.x;
@@ -189,13 +205,16 @@ __device__ void cmv(const TA* __restrict__ A, int lda, int rows, int k, const TA
         for (int c = 0; c < NC; ++c) Cv<TA>::mac(acc[c], a, Bs[c * kb + j]);
       }
     }
+    typedef typename Cv<TA>::Part Part;
+    static_assert(sizeof(Part) == sizeof(cd), "a partial sum takes the slot of a cd");
     if (ks == 1) {
       if (r < rows)
 #pragma unroll
-        for (int c = 0; c < NC; ++c) Cs[c * rows + r] = Cv<TA>::to(acc[c]);
+        for (int c = 0; c < NC; ++c) {
+          if (RAW) reinterpret_cast<Part*>(Cs)[c * rows + r] = Cv<TA>::part(acc[c]);
+          else Cs[c * rows + r] = Cv<TA>::to(acc[c]);
+        }
     } else {
-      typedef typename Cv<TA>::Part Part;
-      static_assert(sizeof(Part) == sizeof(cd), "a partial sum takes the slot of a cd");
       Part* pr = reinterpret_cast<Part*>(red);
       if (kg < ks)
 #pragma unroll
@@ -206,7 +225,8 @@ __device__ void cmv(const TA* __restrict__ A, int lda, int rows, int k, const TA
         for (int c = 0; c < NC; ++c) {
           Part s = pr[c * rp + ri];
           for (int g = 1; g < ks; ++g) Cv<TA>::part_add(s, pr[(g * NC + c) * rp + ri]);
-          Cs[c * rows + r] = Cv<TA>::part_to(s);
+          if (RAW) reinterpret_cast<Part*>(Cs)[c * rows + r] = s;
+          else Cs[c * rows + r] = Cv<TA>::part_to(s);
         }
       }
     }
