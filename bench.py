@@ -265,13 +265,14 @@ def class_work(op, w, R, prec, fd, root_c4=False, merge_sym=False, periodic=Fals
 
 # DRAM traffic (dram__bytes_read.sum + dram__bytes_write.sum) of one step's launches of a
 # kernel class, from an ncu capture of the shallow-water workload with 301 poles (151
-# distinct), FP32-pair precision, even/odd merge blocks and the four-block root.  Traffic
-# grows with the number of distinct poles (one block set per pole, read once), so a full
-# step scales it by P / 151.  Keys: (workload, precision, class).
+# distinct), FP32-pair precision, even/odd merge blocks (FP32-pair partial sums and
+# boundary data between up levels) and the four-block root.  Traffic grows with the number
+# of distinct poles (one block set per pole, read once), so a full step scales it by P / 151.
+# Keys: (workload, precision, class).
 NCU_TRAFFIC_151 = {
-    ("sw_walls_16x16_p16_tau20T", "df32", "up_merge"): 0.4365e9,
-    ("sw_walls_16x16_p16_tau20T", "df32", "down_merge"): 0.2945e9,
-    ("sw_walls_16x16_p16_tau20T", "df32", "root"): 0.4877e9,
+    ("sw_walls_16x16_p16_tau20T", "df32", "up_merge"): 0.4366e9,
+    ("sw_walls_16x16_p16_tau20T", "df32", "down_merge"): 0.2942e9,
+    ("sw_walls_16x16_p16_tau20T", "df32", "root"): 0.4872e9,
 }
 
 
