@@ -453,24 +453,53 @@ static eo_status fit_wide_poles(int N, double delta, Fit& out) {
   return fail(EO_ERR_FIT, "no admissible rational approximant for this pole count");
 }
 
+// Index (s-major over the spacings ss, then the sigma/s ratios rs) of the first grid
+// candidate whose N-pole line fits band X, or -1.  The candidates are evaluated in parallel
+// host threads; the first in grid order is kept, so the result does not depend on threads.
+static int first_accepted(int N, double X, double delta, const double* ss, int ns_, const double* rs, int nr) {
+  const int M = (N - 1) / 2;
+  const int nc = ns_ * nr;
+  std::vector<char> ok(nc, 0);
+  std::atomic<int> next(0);
+  auto work = [&] {
+    std::vector<cplx> al, b;
+    for (int ci = next++; ci < nc; ci = next++) {
+      const double sp = ss[ci / nr], ratio = rs[ci % nr];
+      double r;
+      if (sp * M >= X && residues(N, ratio * sp, sp, X, al, b) && accept(X, delta, al, b, &r)) ok[ci] = 1;
+    }
+  };
+  const unsigned nt = std::max(1u, std::min(32u, std::thread::hardware_concurrency()));
+  std::vector<std::thread> th;
+  for (unsigned t = 0; t < nt; ++t) th.emplace_back(work);
+  for (auto& x : th) x.join();
+  for (int ci = 0; ci < nc; ++ci)
+    if (ok[ci]) return ci;
+  return -1;
+}
+
 eo_status fit_for_band(double X, double delta, int nmax, Fit& out) {
   if (!(X > 0)) return fail(EO_ERR_INVALID_ARG, "band*tau must be positive");
   if (X > 40.0) return fit_wide(X, delta, out);
-  std::vector<cplx> al, b;
-  for (int N = 5; N <= std::min(nmax, 101); N += 2) {
-    const int M = (N - 1) / 2;
-    for (double s : kS)
-      for (double ratio : kRatio) {
-        if (s * M < X) continue;
-        double r;
-        if (residues(N, ratio * s, s, X, al, b) && accept(X, delta, al, b, &r)) {
-          store(al, b, r, X, ratio * s, s, out);
-          return EO_OK;
-        }
-      }
+  // fewest poles: the coarse search grid first, then the fine one, then the wide
+  // construction (trapezoidal centre, fitted ends), which needs more poles
+  const double* grids[2][2] = {{kS, kRatio}, {kSFine, kRatioFine}};
+  const int sizes[2][2] = {{(int)(sizeof(kS) / sizeof(kS[0])), (int)(sizeof(kRatio) / sizeof(kRatio[0]))},
+                           {(int)(sizeof(kSFine) / sizeof(kSFine[0])),
+                            (int)(sizeof(kRatioFine) / sizeof(kRatioFine[0]))}};
+  for (int gi = 0; gi < 2; ++gi) {
+    for (int N = 5; N <= std::min(nmax, 101); N += 2) {
+      const int ci = first_accepted(N, X, delta, grids[gi][0], sizes[gi][0], grids[gi][1], sizes[gi][1]);
+      if (ci < 0) continue;
+      const double sp = grids[gi][0][ci / sizes[gi][1]], ratio = grids[gi][1][ci % sizes[gi][1]];
+      std::vector<cplx> al, b;
+      double r;
+      residues(N, ratio * sp, sp, X, al, b);
+      accept(X, delta, al, b, &r);
+      store(al, b, r, X, ratio * sp, sp, out);
+      return EO_OK;
+    }
   }
-  // no line of the search grid fits this band: the wide construction (trapezoidal
-  // centre, fitted ends) covers it with more poles
   if (fit_wide(X, delta, out) == EO_OK) return EO_OK;
   return fail(EO_ERR_FIT, "band*tau too wide for the supported pole counts");
 }
